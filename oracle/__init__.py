@@ -1,0 +1,246 @@
+"""FP64 CPU oracle for Kaczmarz++ / CD++ -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg import this package.
+The product library (``paper_2501_11673_gb300``) never imports, links or runs anything here, and this
+package never imports the product library.  The C source (``kpp_oracle.c``) is the oracle proper;
+this module compiles it with gcc and marshals numpy arrays through ctypes.
+
+Paper: Derezinski, Needell, Rebrova, Yang, "Randomized Kaczmarz Methods with Beyond-Krylov
+Convergence" (arXiv 2501.11673).  Functions cite the passage they follow:
+
+* ``kpp_factor`` / ``cdpp_factor``: memoised Cholesky factor per block (Sec. 4, Sec. 5.2).
+* ``run``: the K++ iteration (Alg. 1 lines 6-11 with exact Cholesky projection, i.e. the
+  ``K++(Cholesky)`` variant of App. F; Alg. 5's adaptive rho and stopping rule) and the CD++
+  iteration (Eq. 5.1, Alg. 3 lines 10-20), both without the randomized Hadamard preprocessing.
+* ``cg``: plain conjugate gradients (context, Sec. 6).
+* ``philox4x32_10`` / ``sample_block``: Philox4x32-10 of Salmon et al. (SC'11).
+
+Parity of the adaptive-rho schedule and of the stopping rule is unpinned by the paper (it prints no
+worked values); they are pinned only by lockstep agreement with the CUDA path under the stated
+readings.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kpp_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libkpp_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, NO_CONVERGENCE, NOT_SPD, BAD_ARG = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FP contraction so x86 and Arm give the same bits)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int32), ("cd", ctypes.c_int32), ("lam", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("sys", ctypes.c_uint32), ("adaptive", ctypes.c_int32), ("eta", ctypes.c_double),
+                ("confirm", ctypes.c_int32)]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int64), ("ci", ctypes.c_int64), ("E0", ctypes.c_double),
+                ("E1", ctypes.c_double), ("rhat", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("rel_res_true", ctypes.c_double),
+                ("rel_res_est", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.orc_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                              ctypes.POINTER(ctypes.c_uint32)]
+            lib.orc_sample_block.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32]
+            lib.orc_sample_block.restype = ctypes.c_int32
+            lib.orc_cholesky.argtypes = [ctypes.c_int, dp]
+            lib.orc_cholesky.restype = ctypes.c_int
+            lib.orc_chol_solve.argtypes = [ctypes.c_int, dp, dp]
+            lib.orc_rel_residual.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, dp]
+            lib.orc_rel_residual.restype = ctypes.c_double
+            lib.orc_kpp_factor.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, ctypes.c_int, ctypes.c_double, dp]
+            lib.orc_kpp_factor.restype = ctypes.c_int
+            lib.orc_cdpp_factor.argtypes = [ctypes.c_int64, dp, ctypes.c_int, ctypes.c_double, dp]
+            lib.orc_cdpp_factor.restype = ctypes.c_int
+            lib.orc_run.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, dp, ctypes.POINTER(_Params),
+                                    ctypes.POINTER(_State), dp, dp, ctypes.POINTER(_Report), dp, ctypes.c_int64]
+            lib.orc_run.restype = ctypes.c_int
+            lib.orc_cg.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_double, ctypes.c_int64, dp]
+            lib.orc_cg.restype = ctypes.c_int64
+            _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11)
+# ----------------------------------------------------------------------------------------------
+
+def philox4x32_10(ctr, key) -> tuple:
+    lib = _load()
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return tuple(int(v) for v in o)
+
+
+def sample_block(seed: int, t: int, sys: int, nb: int) -> int:
+    """Block index drawn at step t of system `sys` (uniform over the nb partition blocks)."""
+    return int(_load().orc_sample_block(seed, t, sys, nb))
+
+
+# ----------------------------------------------------------------------------------------------
+# Dense pieces
+# ----------------------------------------------------------------------------------------------
+
+def cholesky(G: np.ndarray) -> np.ndarray:
+    """Lower Cholesky factor; raises ValueError on a non-positive pivot."""
+    L = _f64(G).copy()
+    rc = _load().orc_cholesky(L.shape[0], _dp(L))
+    if rc:
+        raise ValueError(f"not SPD at pivot {rc - 1}")
+    return L
+
+
+def chol_solve(L: np.ndarray, r: np.ndarray) -> np.ndarray:
+    y = _f64(r).copy()
+    _load().orc_chol_solve(L.shape[0], _dp(_f64(L)), _dp(y))
+    return y
+
+
+def rel_residual(A: np.ndarray, b: np.ndarray, x: np.ndarray) -> float:
+    A = _f64(A)
+    return float(_load().orc_rel_residual(A.shape[0], A.shape[1], _dp(A), _dp(_f64(b)), _dp(_f64(x))))
+
+
+def kpp_factor(A: np.ndarray, s: int, lam: float) -> np.ndarray:
+    """Per-block factors chol(A_S A_S^T + lam I) (Sec. 4); array of shape (nb, s, s)."""
+    A = _f64(A)
+    m, n = A.shape
+    nb = -(-m // s)
+    L = np.zeros((nb, s, s))
+    rc = _load().orc_kpp_factor(m, n, _dp(A), s, lam, _dp(L))
+    if rc:
+        raise ValueError(f"block {rc - 1} not SPD")
+    return L
+
+
+def cdpp_factor(A: np.ndarray, s: int, lam: float) -> np.ndarray:
+    """Per-block factors chol(A_SS + lam I) (Sec. 5.2); array of shape (nb, s, s)."""
+    A = _f64(A)
+    n = A.shape[0]
+    nb = -(-n // s)
+    L = np.zeros((nb, s, s))
+    rc = _load().orc_cdpp_factor(n, _dp(A), s, lam, _dp(L))
+    if rc:
+        raise ValueError(f"block {rc - 1} not SPD")
+    return L
+
+
+def factor_block(L: np.ndarray, j: int, rows: int, s: int) -> np.ndarray:
+    """The (len x len) factor of block j out of the packed (nb, s, s) array."""
+    ln = min(s, rows - j * s)
+    return L[j].reshape(-1)[: ln * ln].reshape(ln, ln)
+
+
+# ----------------------------------------------------------------------------------------------
+# The iteration
+# ----------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class State:
+    t: int = 0
+    ci: int = 0
+    E0: float = 0.0
+    E1: float = 0.0
+    rhat: float = 0.0
+    rho: float = 0.0
+
+
+@dataclasses.dataclass
+class Result:
+    x: np.ndarray
+    mom: np.ndarray
+    state: State
+    iters: int
+    rel_res_true: float
+    rel_res_est: float
+    status: int
+    trace: np.ndarray  # (n_checkpoints, 5): t, E0, E1, rho, true residual (NaN if not computed)
+
+
+def default_eta(rows: int, cols: int, s: int) -> float:
+    """eta = s / (2 min(rows, cols)) (Sec. 5.4; Alg. 3 and Alg. 5 print s/(2n))."""
+    return s / (2.0 * min(rows, cols))
+
+
+def run(A: np.ndarray, b: np.ndarray, L: np.ndarray, s: int, *, cd: bool = False, lam: float = 0.0,
+        tol: float = 1e-8, max_iters: int = 100000, seed: int = 0, sys: int = 0, adaptive: bool = True,
+        eta: float | None = None, rho: float = 0.0, confirm: bool = True, x0=None, mom0=None,
+        state: State | None = None, trace_cap: int = 4096) -> Result:
+    """Run K++ (cd=False) or CD++ (cd=True) iterations from a state until the stop rule or max_iters.
+
+    K++ step: Eq. 1.3 with the memoised factor L (Alg. 1 lines 6-10); CD++ step: Eq. 5.1.
+    Adaptive rho, residual estimate and stop: Eq. 5.2, Eq. 5.3, Alg. 3 lines 14-20 / Alg. 5 lines 13-19.
+    """
+    lib = _load()
+    A = _f64(A)
+    b = _f64(b)
+    rows, n = A.shape
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    mom = np.zeros(n) if mom0 is None else _f64(mom0).copy()
+    st = state or State(rho=rho)
+    p = _Params(s=s, cd=int(cd), lam=lam, tol=tol, max_iters=max_iters, seed=seed, sys=sys,
+                adaptive=int(adaptive), eta=default_eta(rows, n, s) if eta is None else eta,
+                confirm=int(confirm))
+    cst = _State(st.t, st.ci, st.E0, st.E1, st.rhat, st.rho)
+    rep = _Report()
+    tr = np.full((trace_cap, 5), np.nan)
+    Lc = _f64(L)
+    lib.orc_run(rows, n, _dp(A), _dp(b), _dp(Lc), ctypes.byref(p), ctypes.byref(cst), _dp(x), _dp(mom),
+                ctypes.byref(rep), _dp(tr), trace_cap)
+    nst = State(cst.t, cst.ci, cst.E0, cst.E1, cst.rhat, cst.rho)
+    ntr = min(nst.ci - (st.ci if state else 0), trace_cap)
+    return Result(x, mom, nst, rep.iters, rep.rel_res_true, rep.rel_res_est, rep.status, tr[:max(ntr, 0)])
+
+
+def cg(A: np.ndarray, b: np.ndarray, tol: float = 1e-8, max_iters: int = 100000, x0=None):
+    """Plain FP64 conjugate gradients (context only).  Returns (x, iterations, |Ax-b|/|b|)."""
+    A = _f64(A)
+    x = np.zeros(A.shape[0]) if x0 is None else _f64(x0).copy()
+    rr = ctypes.c_double()
+    it = _load().orc_cg(A.shape[0], _dp(A), _dp(_f64(b)), _dp(x), tol, max_iters, ctypes.byref(rr))
+    return x, int(it), rr.value

@@ -1,0 +1,338 @@
+/*
+ * kpp_oracle.c -- plain, slow, FP64 CPU oracle for Kaczmarz++ and CD++.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or calls this file; only
+ * the tests, the smoke check and the benchmark's CPU-baseline leg do.  It shares no code with the
+ * CUDA path (its own Philox, its own Cholesky, its own loops).
+ *
+ * Every loop is the textbook definition, summed left to right in FP64, with no blocking, fusion or
+ * reordering.  Build with -ffp-contract=off so that x86 and Arm hosts give identical bits.
+ *
+ * What it computes (paper: Derezinski, Needell, Rebrova, Yang, "Randomized Kaczmarz Methods with
+ * Beyond-Krylov Convergence", arXiv 2501.11673):
+ *   - regularised block projection           w = A_S^T (A_S A_S^T + lam I)^{-1} (A_S x - b_S)   (Eq. 1.3)
+ *   - Nesterov-style momentum                 m <- (1-rho)/(1+rho) (m - w),  x <- x - w + eta m     (Eq. 1.4, Alg. 1)
+ *   - CD++ coordinate step                    w = I_S^T (A_SS + lam I)^{-1} (A_S x - b_S)           (Eq. 5.1, Thm 5.1)
+ *   - residual estimate, adaptive rho, stop   E0/E1 windows of zeta steps, weighted ratio           (Eq. 5.2, Eq. 5.3, Alg. 3 / Alg. 5)
+ *   - memoised per-block Cholesky factors     one factor per block of a fixed partition             (Sec. 4, Sec. 5.2)
+ *   - plain conjugate gradients (context only; Sec. 6 compares against CG)
+ *   - Philox4x32-10 block sampling (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
+ *     1, 2, 3", SC'11): a counter-based generator, implemented here from its published definition.
+ *
+ * Readings where the paper is silent (shared with the GPU library by specification, not by code):
+ *   - blocks are the contiguous partition  S_j = [j s, min((j+1) s, rows)),  nb = ceil(rows / s);
+ *   - block draw at step t of system `sys`: out = Philox4x32-10(ctr = {t_lo, t_hi, sys, 0},
+ *     key = {seed_lo, seed_hi});  j = (out[0] * nb) >> 32   (uniform with replacement, Alg. 1);
+ *   - zeta = nb;  (t mod 2 zeta) < zeta adds |r|^2 to E0, otherwise to E1;
+ *   - at t = 2 zeta - 1 (mod 2 zeta), checkpoint i (1, 2, ...): if E1 <= eps^2 |b|^2 the true
+ *     residual |A x - b| / |b| is computed and the solve stops if it is <= eps; otherwise the ratio
+ *     q = E1 / E0 enters  rhat = q (i = 1),  rhat = (a_{i-1}/a_i) rhat + (1 - a_{i-1}/a_i) q (i >= 2)
+ *     with a_i = (i+1)^{ln(i+1)};  rho = 1 - rhat^{1/zeta} clamped to [0, 1 - 1e-12];  E0 = E1 = 0;
+ *   - eta defaults to s / (2 min(rows, cols)).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_NO_CONVERGENCE 1
+#define ORC_NOT_SPD 2
+#define ORC_BAD_ARG 3
+
+/* ------------------------------------------------------------------------------------------ */
+/* Philox4x32-10 (SC'11).  Round: (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2,                       */
+/* c' = {hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0};  the key is bumped by the Weyl constants     */
+/* between rounds.                                                                             */
+/* ------------------------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+int32_t orc_sample_block(uint64_t seed, int64_t t, uint32_t sys, int32_t nb) {
+    uint32_t ctr[4] = {(uint32_t)(uint64_t)t, (uint32_t)((uint64_t)t >> 32), sys, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return (int32_t)(((uint64_t)out[0] * (uint64_t)(uint32_t)nb) >> 32);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Dense linear algebra, row-major.                                                            */
+/* ------------------------------------------------------------------------------------------ */
+
+/* In place lower Cholesky of the s x s SPD matrix G (row-major, leading dimension s).
+ * Returns 0, or (j+1) if the j-th pivot is not positive / not finite.  The strict upper triangle
+ * is set to zero. */
+int orc_cholesky(int s, double *G) {
+    for (int j = 0; j < s; ++j) {
+        double d = G[(size_t)j * s + j];
+        for (int k = 0; k < j; ++k) d -= G[(size_t)j * s + k] * G[(size_t)j * s + k];
+        if (!(d > 0.0) || !isfinite(d)) return j + 1;
+        double ljj = sqrt(d);
+        G[(size_t)j * s + j] = ljj;
+        for (int i = j + 1; i < s; ++i) {
+            double v = G[(size_t)i * s + j];
+            for (int k = 0; k < j; ++k) v -= G[(size_t)i * s + k] * G[(size_t)j * s + k];
+            G[(size_t)i * s + j] = v / ljj;
+        }
+        for (int k = j + 1; k < s; ++k) G[(size_t)j * s + k] = 0.0;
+    }
+    return 0;
+}
+
+/* Solve (L L^T) y = r in place: forward substitution L z = r, then back substitution L^T y = z. */
+void orc_chol_solve(int s, const double *L, double *y) {
+    for (int i = 0; i < s; ++i) {
+        double v = y[i];
+        for (int k = 0; k < i; ++k) v -= L[(size_t)i * s + k] * y[k];
+        y[i] = v / L[(size_t)i * s + i];
+    }
+    for (int i = s - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < s; ++k) v -= L[(size_t)k * s + i] * y[k];
+        y[i] = v / L[(size_t)i * s + i];
+    }
+}
+
+static double dot(int64_t n, const double *a, const double *b) {
+    double acc = 0.0;
+    for (int64_t k = 0; k < n; ++k) acc += a[k] * b[k];
+    return acc;
+}
+
+/* |A x - b| / |b| in FP64. */
+double orc_rel_residual(int64_t m, int64_t n, const double *A, const double *b, const double *x) {
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double r = dot(n, A + (size_t)i * n, x) - b[i];
+        num += r * r;
+        den += b[i] * b[i];
+    }
+    return den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
+}
+
+static int64_t nblocks(int64_t rows, int s) { return (rows + s - 1) / s; }
+static int block_len(int64_t rows, int s, int64_t j) {
+    int64_t lo = j * s, hi = lo + s < rows ? lo + s : rows;
+    return (int)(hi - lo);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Memoised factors (Sec. 4 / Sec. 5.2): one s x s lower factor per block, stored at L + j*s*s  */
+/* (the last block may be shorter; its factor uses leading dimension equal to its length).      */
+/* ------------------------------------------------------------------------------------------ */
+
+/* K++: L_j = chol(A_{S_j} A_{S_j}^T + lam I).  Returns 0 or (block+1) of the first failure. */
+int orc_kpp_factor(int64_t m, int64_t n, const double *A, int s, double lam, double *L) {
+    int64_t nb = nblocks(m, s);
+    for (int64_t j = 0; j < nb; ++j) {
+        int len = block_len(m, s, j);
+        double *G = L + (size_t)j * s * s;
+        const double *As = A + (size_t)j * s * n;
+        for (int a = 0; a < len; ++a)
+            for (int c = 0; c < len; ++c)
+                G[(size_t)a * len + c] = dot(n, As + (size_t)a * n, As + (size_t)c * n) + (a == c ? lam : 0.0);
+        if (orc_cholesky(len, G) != 0) return (int)(j + 1);
+    }
+    return 0;
+}
+
+/* CD++: L_j = chol(A_{S_j,S_j} + lam I) for symmetric n x n A. */
+int orc_cdpp_factor(int64_t n, const double *A, int s, double lam, double *L) {
+    int64_t nb = nblocks(n, s);
+    for (int64_t j = 0; j < nb; ++j) {
+        int len = block_len(n, s, j);
+        double *G = L + (size_t)j * s * s;
+        int64_t r0 = j * s;
+        for (int a = 0; a < len; ++a)
+            for (int c = 0; c < len; ++c)
+                G[(size_t)a * len + c] = A[(size_t)(r0 + a) * n + (r0 + c)] + (a == c ? lam : 0.0);
+        if (orc_cholesky(len, G) != 0) return (int)(j + 1);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* The iteration.                                                                              */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t s;                 /* block size */
+    int32_t cd;                /* 0: K++ step (Eq. 1.3), 1: CD++ step (Eq. 5.1) */
+    double lam;                /* Tikhonov regulariser */
+    double tol;                /* eps; 0 disables stopping */
+    int64_t max_iters;         /* iteration cap (total, counting from state.t) */
+    uint64_t seed;             /* Philox key */
+    uint32_t sys;              /* Philox stream id (system / request) */
+    int32_t adaptive;          /* 1: adaptive rho (Eq. 5.3); 0: rho fixed at state.rho */
+    double eta;                /* momentum step (0: plain block Kaczmarz) */
+    int32_t confirm;           /* 1: stop only once the true residual is <= tol */
+} orc_params;
+
+typedef struct {
+    int64_t t;                 /* next iteration index */
+    int64_t ci;                /* checkpoints completed */
+    double E0, E1;             /* running window sums of |r_t|^2 */
+    double rhat, rho;          /* weighted ratio estimate and current rho */
+} orc_state;
+
+typedef struct {
+    int64_t iters;             /* iterations performed in this call */
+    double rel_res_true;       /* |A x - b| / |b| at return (always computed) */
+    double rel_res_est;        /* sqrt(E1)/|b| at the last checkpoint (NaN if none) */
+    int32_t status;            /* ORC_* */
+    int32_t pad;
+} orc_report;
+
+/* One block step on (x, mom), given the drawn block j and its factor.  Returns |r|^2. */
+static double step(int64_t rows, int64_t n, const double *A, const double *b, int s, int cd,
+                   const double *L, int64_t j, double beta, double eta, double *x, double *mom,
+                   double *r, double *w) {
+    int len = block_len(rows, s, j);
+    int64_t r0 = j * s;
+    const double *Lj = L + (size_t)j * s * s;
+    /* r = A_S x - b_S */
+    double rn2 = 0.0;
+    for (int a = 0; a < len; ++a) {
+        r[a] = dot(n, A + (size_t)(r0 + a) * n, x) - b[r0 + a];
+        rn2 += r[a] * r[a];
+    }
+    /* y = (G + lam I)^{-1} r through the memoised factor (r is overwritten by y) */
+    orc_chol_solve(len, Lj, r);
+    /* w = A_S^T y (K++) or I_S^T y (CD++) */
+    for (int64_t k = 0; k < n; ++k) w[k] = 0.0;
+    if (cd) {
+        for (int a = 0; a < len; ++a) w[r0 + a] = r[a];
+    } else {
+        for (int a = 0; a < len; ++a) {
+            const double *row = A + (size_t)(r0 + a) * n;
+            for (int64_t k = 0; k < n; ++k) w[k] += row[k] * r[a];
+        }
+    }
+    /* momentum, then the update (Alg. 1: m_{t+1} first, x_{t+1} uses m_{t+1}) */
+    for (int64_t k = 0; k < n; ++k) {
+        mom[k] = beta * (mom[k] - w[k]);
+        x[k] = x[k] - w[k] + eta * mom[k];
+    }
+    return rn2;
+}
+
+/* Run iterations from `st` until the stop rule fires or st->t reaches p->max_iters.
+ * rows x n matrix A (CD++: rows == n, A symmetric), factors from orc_*_factor.
+ * trace (optional, capacity trace_cap rows of 5 doubles): per checkpoint {t, E0, E1, rho, true_res or NaN}. */
+int orc_run(int64_t rows, int64_t n, const double *A, const double *b, const double *L,
+            const orc_params *p, orc_state *st, double *x, double *mom, orc_report *rep,
+            double *trace, int64_t trace_cap) {
+    if (p->s <= 0 || rows <= 0 || n <= 0 || (p->cd && rows != n)) return ORC_BAD_ARG;
+    int s = p->s;
+    int64_t nb = nblocks(rows, s);
+    int64_t zeta = nb;
+    double bn2 = dot(rows, b, b);
+    double *r = (double *)malloc(sizeof(double) * (size_t)s);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    int64_t it0 = st->t;
+    int status = ORC_NO_CONVERGENCE;
+    rep->rel_res_est = NAN;
+    int64_t ntrace = 0;
+    while (st->t < p->max_iters) {
+        int64_t t = st->t;
+        int64_t j = orc_sample_block(p->seed, t, p->sys, (int32_t)nb);
+        double beta = (1.0 - st->rho) / (1.0 + st->rho);
+        double rn2 = step(rows, n, A, b, s, p->cd, L, j, beta, p->eta, x, mom, r, w);
+        st->t = t + 1;
+        if ((t % (2 * zeta)) < zeta) st->E0 += rn2; else st->E1 += rn2;
+        if ((t % (2 * zeta)) == 2 * zeta - 1) {
+            st->ci += 1;
+            double tres = NAN;
+            rep->rel_res_est = bn2 > 0.0 ? sqrt(st->E1 / bn2) : sqrt(st->E1);
+            int stop = 0;
+            if (p->tol > 0.0 && st->E1 <= p->tol * p->tol * bn2) {
+                if (p->confirm) {
+                    tres = orc_rel_residual(rows, n, A, b, x);
+                    stop = tres <= p->tol;
+                } else {
+                    stop = 1;
+                }
+            }
+            if (trace && ntrace < trace_cap) {
+                double *tr = trace + 5 * ntrace;
+                tr[0] = (double)t; tr[1] = st->E0; tr[2] = st->E1; tr[3] = st->rho; tr[4] = tres;
+                ntrace++;
+            }
+            if (stop) { status = ORC_OK; break; }
+            if (p->adaptive) {
+                double q = st->E0 > 0.0 ? st->E1 / st->E0 : 0.0;
+                if (st->ci == 1) {
+                    st->rhat = q;
+                } else {
+                    double li = log((double)st->ci), li1 = log((double)st->ci + 1.0);
+                    double wgt = exp(li * li - li1 * li1); /* a_{i-1} / a_i,  a_i = (i+1)^{ln(i+1)} */
+                    st->rhat = wgt * st->rhat + (1.0 - wgt) * q;
+                }
+                double rho = 1.0 - pow(st->rhat, 1.0 / (double)zeta);
+                if (!(rho > 0.0)) rho = 0.0;
+                if (rho > 1.0 - 1e-12) rho = 1.0 - 1e-12;
+                st->rho = rho;
+            }
+            st->E0 = 0.0;
+            st->E1 = 0.0;
+        }
+    }
+    rep->iters = st->t - it0;
+    rep->rel_res_true = orc_rel_residual(rows, n, A, b, x);
+    rep->status = status;
+    free(r);
+    free(w);
+    return status;
+}
+
+/* Plain CG on SPD A (context only): x in/out, returns iterations; stops at |r|/|b| <= tol. */
+int64_t orc_cg(int64_t n, const double *A, const double *b, double *x, double tol, int64_t max_iters,
+               double *rel_res_out) {
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *pv = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Ap = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - dot(n, A + (size_t)i * n, x);
+    memcpy(pv, r, sizeof(double) * (size_t)n);
+    double bn = sqrt(dot(n, b, b));
+    double rr = dot(n, r, r);
+    int64_t it = 0;
+    while (it < max_iters && sqrt(rr) > tol * bn) {
+        for (int64_t i = 0; i < n; ++i) Ap[i] = dot(n, A + (size_t)i * n, pv);
+        double alpha = rr / dot(n, pv, Ap);
+        for (int64_t i = 0; i < n; ++i) {
+            x[i] += alpha * pv[i];
+            r[i] -= alpha * Ap[i];
+        }
+        double rr2 = dot(n, r, r);
+        double bta = rr2 / rr;
+        for (int64_t i = 0; i < n; ++i) pv[i] = r[i] + bta * pv[i];
+        rr = rr2;
+        ++it;
+    }
+    *rel_res_out = orc_rel_residual(n, n, A, b, x);
+    free(r);
+    free(pv);
+    free(Ap);
+    return it;
+}

@@ -1,0 +1,172 @@
+"""Seeded synthetic workloads for Kaczmarz++ / CD++ (inputs only, no solver arithmetic).
+
+The paper evaluates on matrices whose spectrum has a few large outlying singular values over a flat
+bulk (Sec. 6 and App. F: scikit-learn low-rank matrices and kernel matrices of public datasets).
+Those datasets are not used here; the planted-spectrum matrices below stand in for them:
+
+* ``lowrank_ls``: over-determined ``A = Z diag(d) V^T`` with ``Z`` i.i.d. Gaussian, ``V`` Haar
+  orthogonal, ``d`` = k log-spaced outliers plus a uniform bulk; consistent ``b = A x*`` (plus an
+  optional Gaussian noise term).
+* ``spd``: dense symmetric positive definite ``A = U diag(sigma) U^T`` with ``U`` Haar orthogonal.
+* ``gaussian_rows``: under-determined i.i.d. N(0,1) rows, some rows scaled up (row outliers).
+
+Haar matrices come from the QR factorisation of a Gaussian matrix with the signs of ``diag(R)`` moved
+into ``Q`` (Mezzadri, "How to generate random matrices from the classical compact groups", 2007).
+
+This module is shared by the tests and the benchmark so that both sides of a parity check see the
+same arrays; it never calls the solver, the oracle or the CUDA library.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+def haar_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-distributed n x n orthogonal matrix (QR of a Gaussian, sign-fixed)."""
+    g = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(g)
+    q *= np.sign(np.diag(r))[None, :]
+    return q
+
+
+def planted_spectrum(n_total: int, n_out: int, out_lo: float, out_hi: float,
+                     bulk_lo: float, bulk_hi: float, rng: np.random.Generator) -> np.ndarray:
+    """n_out log-spaced outliers in [out_lo, out_hi] (descending) followed by a uniform bulk."""
+    out = np.geomspace(out_hi, out_lo, n_out) if n_out > 0 else np.zeros(0)
+    bulk = rng.uniform(bulk_lo, bulk_hi, n_total - n_out)
+    return np.concatenate([out, np.sort(bulk)[::-1]])
+
+
+@dataclasses.dataclass
+class System:
+    """One linear system A x = b with its metadata (all arrays FP64, row-major, C-contiguous)."""
+    A: np.ndarray
+    b: np.ndarray
+    x_star: np.ndarray | None
+    s: int
+    lam: float
+    tol: float
+    name: str
+    spectrum: np.ndarray | None = None
+
+
+def lowrank_ls(m: int, n: int, n_out: int, out_lo: float, out_hi: float, bulk_lo: float,
+               bulk_hi: float, seed_A: int, seed_b: int, noise: float = 0.0) -> tuple:
+    """Over-determined A = Z diag(d) V^T (Z_ij ~ N(0, 1/m)), x* ~ N(0, I), b = A x* (+ noise)."""
+    rng = np.random.default_rng(seed_A)
+    z = rng.standard_normal((m, n)) * (1.0 / math.sqrt(m))
+    v = haar_orthogonal(n, rng)
+    d = planted_spectrum(n, n_out, out_lo, out_hi, bulk_lo, bulk_hi, rng)
+    A = np.ascontiguousarray(z @ (d[:, None] * v.T))
+    rb = np.random.default_rng(seed_b)
+    x_star = rb.standard_normal(n)
+    b = A @ x_star
+    if noise:
+        b = b + noise * rb.standard_normal(m)
+    return A, b, x_star, d
+
+
+def spd(n: int, n_out: int, out_lo: float, out_hi: float, bulk_lo: float, bulk_hi: float,
+        seed_A: int, seed_b: int) -> tuple:
+    """Exactly symmetric A = U diag(sigma) U^T with U Haar; b ~ N(0, I)."""
+    rng = np.random.default_rng(seed_A)
+    u = haar_orthogonal(n, rng)
+    sig = planted_spectrum(n, n_out, out_lo, out_hi, bulk_lo, bulk_hi, rng)
+    A = (u * sig[None, :]) @ u.T
+    A = np.ascontiguousarray(0.5 * (A + A.T))  # bitwise symmetric
+    b = np.random.default_rng(seed_b).standard_normal(n)
+    return A, b, sig
+
+
+def gaussian_rows(m: int, n: int, n_big: int, scale: float, seed_A: int, seed_b: int,
+                  k_rhs: int = 1) -> tuple:
+    """Under-determined A (m < n) with i.i.d. N(0,1) entries; n_big seeded rows scaled by `scale`."""
+    rng = np.random.default_rng(seed_A)
+    A = rng.standard_normal((m, n))
+    rows = rng.permutation(m)[:n_big]
+    A[rows] *= scale
+    B = np.random.default_rng(seed_b).standard_normal((m, k_rhs))
+    return np.ascontiguousarray(A), np.ascontiguousarray(B), np.sort(rows)
+
+
+# ---------------------------------------------------------------------------------------------
+# The five workloads (sizes as stated; `scale` shrinks the big ones for fast test variants).
+# ---------------------------------------------------------------------------------------------
+
+def kpp_fp64_2000x200() -> System:
+    """K++ FP64: 2000 x 200 consistent LS, 10 outliers 1e2..1e3 over U[1,2]; s=20, lambda=1e-3, seed 0."""
+    A, b, xs, d = lowrank_ls(2000, 200, 10, 1e2, 1e3, 1.0, 2.0, seed_A=0, seed_b=0)
+    return System(A, b, xs, s=20, lam=1e-3, tol=1e-8, name="kpp_fp64_2000x200", spectrum=d)
+
+
+def cdpp_fp64_spd(n: int = 4096, s: int = 64) -> System:
+    """CD++ FP64: n x n SPD, 50 outliers log-spaced 1e2..1e4 over U[1,10]; s=64, lambda=1e-4."""
+    n_out = 50 if n >= 1024 else max(1, n // 80)
+    A, b, sig = spd(n, n_out, 1e2, 1e4, 1.0, 10.0, seed_A=1, seed_b=102)
+    return System(A, b, None, s=s, lam=1e-4, tol=1e-8, name=f"cdpp_fp64_spd{n}", spectrum=sig)
+
+
+def kpp_mixed_lowrank(m: int = 262144, n: int = 4096, s: int = 512, n_out: int = 100,
+                      noise: float = 0.0) -> System:
+    """Mixed-precision K++: m x n LS, n_out outliers log-spaced 10..1000 over U[0.5,1]; s=512."""
+    A, b, xs, d = lowrank_ls(m, n, n_out, 10.0, 1000.0, 0.5, 1.0, seed_A=2, seed_b=103, noise=noise)
+    return System(A, b, xs, s=s, lam=1e-3, tol=1e-8, name=f"kpp_mixed_{m}x{n}", spectrum=d)
+
+
+def round_to_storage(A: np.ndarray, dtype: str) -> np.ndarray:
+    """Round FP64 entries to the storage type and widen back (the stored matrix is the system)."""
+    if dtype == "f64":
+        return A
+    if dtype == "f32":
+        return A.astype(np.float32).astype(np.float64)
+    if dtype == "bf16":
+        a32 = A.astype(np.float32)
+        u = a32.view(np.uint32).astype(np.uint64)
+        # round-to-nearest-even on the upper 16 bits (finite inputs only)
+        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    raise ValueError(dtype)
+
+
+def bf16_bits(A: np.ndarray) -> np.ndarray:
+    """The bf16 bit patterns (uint16) of A rounded to nearest-even."""
+    a32 = np.ascontiguousarray(A, dtype=np.float32)
+    u = a32.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return u.astype(np.uint16)
+
+
+def batched_minnorm(n_sys: int = 64, m: int = 2048, n: int = 65536, k_rhs: int = 8,
+                    n_big: int = 20) -> list:
+    """Batched under-determined min-norm K++ systems: A_i (m x n, FP32-stored) with row outliers."""
+    out = []
+    for i in range(n_sys):
+        A, B, rows = gaussian_rows(m, n, n_big, 100.0, seed_A=3000 + i, seed_b=4000 + i, k_rhs=k_rhs)
+        out.append((A, B, rows))
+    return out
+
+
+def row_outlier_lambda(A: np.ndarray) -> float:
+    """lambda = 1e-3 * median squared row norm (the regulariser used for the row-outlier systems)."""
+    return 1e-3 * float(np.median(np.einsum("ij,ij->i", A, A)))
+
+
+def serving_catalog(n_mats: int = 32, n_lo: int = 512, n_hi: int = 8192, seed: int = 5000) -> list:
+    """Sizes of the SPD matrices a serving run draws from (log-uniform in [n_lo, n_hi], multiple of 64)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), n_mats))
+    return [int(max(64, round(v / 64) * 64)) for v in sizes]
+
+
+def serving_requests(n_req: int = 1024, n_mats: int = 32, mean_gap_ms: float = 2.0,
+                     k_lo: int = 1, k_hi: int = 32, seed: int = 6000) -> list:
+    """Request stream: (arrival_ms, matrix_id, k_rhs, rhs_seed), Poisson arrivals."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(mean_gap_ms, n_req)
+    t = np.cumsum(gaps) - gaps[0]
+    mats = rng.integers(0, n_mats, n_req)
+    ks = rng.integers(k_lo, k_hi + 1, n_req)
+    return [(float(t[i]), int(mats[i]), int(ks[i]), 1000 + i) for i in range(n_req)]

@@ -1,0 +1,279 @@
+"""Pins for the FP64 oracle: each test checks it against something other than itself.
+
+Paper: arXiv 2501.11673.  What pins what:
+  * Philox4x32-10       -> published known-answer vectors (tests/golden/philox4x32_10_kat.txt)
+  * Cholesky / solve     -> LAPACK through numpy
+  * K++ step, lam > 0    -> the argmin definition of Eq. 1.3, solved through the n x n normal equations
+  * K++ step, lam = 0    -> the projection invariant A_S x = b_S (Sec. 1.1) and, for s = 1, the classical
+                            randomized Kaczmarz update; for one block = all rows, x = pinv(A) b
+  * momentum             -> the (x, y, v) recursion of Lemma 2.3 with alpha, beta, gamma of Lemma 2.3
+  * CD++ step            -> K++ on Phi with Phi Phi^T = A (Eq. 5.1 / the implicit form in the proof of Thm 5.1)
+  * whole solves         -> x*, numpy.linalg.solve / lstsq / the min-norm solution; range invariance (Thm 2.1)
+  * CG                   -> numpy.linalg.solve
+The adaptive-rho schedule and the stop rule have no printed values in the paper ("parity unpinned"):
+only their structural properties are checked here.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_11673_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _kat_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(t, 16) for t in line.split()]
+            rows.append((v[0:4], v[4:6], tuple(v[6:10])))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,expected", _kat_rows())
+def test_philox_known_answers(ctr, key, expected):
+    assert oracle.philox4x32_10(ctr, key) == expected
+
+
+def test_block_sampling_uniform_and_in_range():
+    nb = 7
+    draws = np.array([oracle.sample_block(1234, t, 3, nb) for t in range(14000)])
+    assert draws.min() >= 0 and draws.max() < nb
+    counts = np.bincount(draws, minlength=nb)
+    chi2 = float(((counts - 2000.0) ** 2 / 2000.0).sum())
+    assert chi2 < 30.0  # 6 dof; p ~ 4e-5
+    # different systems give different streams
+    other = np.array([oracle.sample_block(1234, t, 4, nb) for t in range(200)])
+    assert (other != draws[:200]).any()
+
+
+def _rand_spd(n, rng, cond=1e3):
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.geomspace(1.0, cond, n)
+    return (q * ev) @ q.T
+
+
+def test_cholesky_matches_lapack_and_flags_indefinite():
+    rng = np.random.default_rng(0)
+    for n in (1, 5, 20, 37):
+        G = _rand_spd(n, rng)
+        G = 0.5 * (G + G.T)
+        L = oracle.cholesky(G)
+        np.testing.assert_allclose(L, np.linalg.cholesky(G), rtol=1e-10, atol=1e-12)
+        r = rng.standard_normal(n)
+        np.testing.assert_allclose(oracle.chol_solve(L, r), np.linalg.solve(G, r), rtol=1e-9, atol=1e-12)
+    G = np.diag([1.0, 2.0, -1.0, 4.0])
+    with pytest.raises(ValueError, match="pivot 2"):
+        oracle.cholesky(G)
+
+
+def _one_step(A, b, s, lam, x0, seed=7, cd=False, mom0=None, eta=0.0, rho=0.0):
+    """One block step from x0 through the oracle; returns (x1, m1, j)."""
+    rows = A.shape[0]
+    L = oracle.cdpp_factor(A, s, lam) if cd else oracle.kpp_factor(A, s, lam)
+    nb = -(-rows // s)
+    j = oracle.sample_block(seed, 0, 0, nb)
+    res = oracle.run(A, b, L, s, cd=cd, lam=lam, tol=0.0, max_iters=1, seed=seed, adaptive=False,
+                     eta=eta, rho=rho, x0=x0, mom0=mom0)
+    assert res.iters == 1
+    return res.x, res.mom, j
+
+
+@pytest.mark.parametrize("m,n,s", [(50, 30, 8), (47, 60, 10), (23, 5, 4)])
+def test_kpp_step_is_regularised_argmin(m, n, s):
+    """Eq. 1.3: x1 = argmin |A_S x - b_S|^2 + lam |x - x0|^2 (normal equations, independent of the oracle)."""
+    rng = np.random.default_rng(m * n)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    x0 = rng.standard_normal(n)
+    lam = 0.37
+    for seed in range(6):  # several blocks, including the ragged last one
+        x1, _, j = _one_step(A, b, s, lam, x0, seed=seed)
+        S = slice(j * s, min((j + 1) * s, m))
+        As, bs = A[S], b[S]
+        ref = np.linalg.solve(As.T @ As + lam * np.eye(n), As.T @ bs + lam * x0)
+        np.testing.assert_allclose(x1, ref, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("m,n,s", [(40, 60, 8), (43, 30, 6)])
+def test_unregularised_step_is_a_projection(m, n, s):
+    """lam = 0, eta = 0: after the step A_S x = b_S exactly (Sec. 1.1), and x1 - x0 lies in range(A_S^T)."""
+    rng = np.random.default_rng(1 + m)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    x0 = rng.standard_normal(n)
+    for seed in range(5):
+        x1, _, j = _one_step(A, b, s, 0.0, x0, seed=seed)
+        S = slice(j * s, min((j + 1) * s, m))
+        assert np.linalg.norm(A[S] @ x1 - b[S]) <= 1e-10 * np.linalg.norm(b[S])
+        d = x1 - x0
+        coef, *_ = np.linalg.lstsq(A[S].T, d, rcond=None)
+        assert np.linalg.norm(A[S].T @ coef - d) <= 1e-10 * np.linalg.norm(d)
+
+
+def test_single_row_blocks_are_classical_randomized_kaczmarz():
+    """s = 1, lam = 0, eta = 0: x1 = x0 - (a_i^T x0 - b_i) / |a_i|^2 a_i (Strohmer-Vershynin update)."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((13, 9))
+    b = rng.standard_normal(13)
+    x0 = rng.standard_normal(9)
+    for seed in range(5):
+        x1, _, i = _one_step(A, b, 1, 0.0, x0, seed=seed)
+        a = A[i]
+        ref = x0 - (a @ x0 - b[i]) / (a @ a) * a
+        np.testing.assert_allclose(x1, ref, rtol=1e-12, atol=1e-13)
+
+
+def test_one_block_holding_all_rows_gives_min_norm_solution():
+    """s = m, lam = 0, eta = 0, x0 = 0 on an under-determined system: one step gives pinv(A) b."""
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((12, 40))
+    b = rng.standard_normal(12)
+    x1, _, j = _one_step(A, b, 12, 0.0, np.zeros(40))
+    assert j == 0
+    np.testing.assert_allclose(x1, np.linalg.pinv(A) @ b, rtol=1e-10, atol=1e-12)
+
+
+def test_momentum_matches_lemma_2_3_recursion():
+    """Lemma 2.3: with beta = 1 - rho, gamma = 1 + eta/rho - eta, alpha = rho/(1+rho) and v0 = y0 = x0,
+    the (x, y, v) recursion reproduces m <- (1-rho)/(1+rho)(m - w), x <- x - w + eta m (m0 = 0)."""
+    rng = np.random.default_rng(11)
+    m, n, s, lam = 60, 25, 6, 0.2
+    A = rng.standard_normal((m, n))
+    b = A @ rng.standard_normal(n)
+    x0 = rng.standard_normal(n)
+    rho, eta = 0.15, 0.2
+    T = 40
+    L = oracle.kpp_factor(A, s, lam)
+    res = oracle.run(A, b, L, s, lam=lam, tol=0.0, max_iters=T, seed=3, adaptive=False, eta=eta, rho=rho, x0=x0)
+    nb = -(-m // s)
+    alpha, beta, gamma = rho / (1 + rho), 1 - rho, 1 + eta / rho - eta
+    y = x0.copy()
+    v = x0.copy()
+    for t in range(T):
+        x = alpha * v + (1 - alpha) * y
+        j = oracle.sample_block(3, t, 0, nb)
+        S = slice(j * s, min((j + 1) * s, m))
+        As = A[S]
+        w = As.T @ np.linalg.solve(As @ As.T + lam * np.eye(As.shape[0]), As @ x - b[S])
+        y, v = x - w, beta * v + (1 - beta) * x - gamma * w
+    x_T = alpha * v + (1 - alpha) * y
+    np.testing.assert_allclose(res.x, x_T, rtol=1e-10, atol=1e-12)
+    # the momentum vector itself: m_t = beta (1 - alpha) / (gamma - 1) (v_t - y_t)
+    m_T = beta * (1 - alpha) / (gamma - 1) * (v - y)
+    np.testing.assert_allclose(res.mom, m_T, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_cdpp_is_kpp_on_a_square_root(adaptive):
+    """Eq. 5.1 / proof of Thm 5.1: CD++ on A = Phi Phi^T is K++ on Phi z = b with z_t = Phi^T x_t."""
+    rng = np.random.default_rng(21)
+    n, s, lam = 45, 7, 1e-3
+    A = _rand_spd(n, rng, cond=1e2)
+    A = 0.5 * (A + A.T)
+    b = rng.standard_normal(n)
+    Phi = np.linalg.cholesky(A)
+    T = 6 * (-(-n // s)) * 2  # six checkpoints
+    Lc = oracle.cdpp_factor(A, s, lam)
+    Lk = oracle.kpp_factor(Phi, s, lam)
+    kw = dict(lam=lam, tol=0.0, max_iters=T, seed=5, adaptive=adaptive, rho=0.0 if adaptive else 0.1,
+              eta=s / (2.0 * n))
+    rc = oracle.run(A, b, Lc, s, cd=True, **kw)
+    rk = oracle.run(Phi, b, Lk, s, cd=False, **kw)
+    np.testing.assert_allclose(rk.x, Phi.T @ rc.x, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(rk.trace[:, 1:4], rc.trace[:, 1:4], rtol=1e-9, atol=1e-14)
+
+
+def test_fixed_point_is_kept():
+    """x0 = x*, m0 = 0 on a consistent system: w = 0 up to rounding, so x stays at x*."""
+    sy = W.kpp_fp64_2000x200()
+    L = oracle.kpp_factor(sy.A, sy.s, sy.lam)
+    res = oracle.run(sy.A, sy.b, L, sy.s, lam=sy.lam, tol=0.0, max_iters=400, seed=0, x0=sy.x_star)
+    assert np.linalg.norm(res.x - sy.x_star) <= 1e-12 * np.linalg.norm(sy.x_star)
+
+
+def test_kpp_converges_to_consistent_solution():
+    """The 2000 x 200 consistent system: stop at |Ax-b|/|b| <= 1e-8 and x close to x*."""
+    sy = W.kpp_fp64_2000x200()
+    L = oracle.kpp_factor(sy.A, sy.s, sy.lam)
+    res = oracle.run(sy.A, sy.b, L, sy.s, lam=sy.lam, tol=1e-8, max_iters=20000, seed=0)
+    assert res.status == oracle.OK
+    assert res.rel_res_true <= 1e-8
+    x_ls = np.linalg.lstsq(sy.A, sy.b, rcond=None)[0]
+    kappa = sy.spectrum.max() / sy.spectrum.min() * 2
+    assert np.linalg.norm(res.x - x_ls) <= kappa * 1e-8 * np.linalg.norm(x_ls)
+    # stop happens at a checkpoint  t = 2 zeta - 1 (mod 2 zeta)
+    zeta = -(-sy.A.shape[0] // sy.s)
+    assert res.iters % (2 * zeta) == 0
+
+
+def test_underdetermined_stays_in_row_space_and_reaches_min_norm():
+    """Thm 2.1 (minimum-norm solution): from x0 = 0 every iterate lies in range(A^T)."""
+    rng = np.random.default_rng(31)
+    m, n, s = 40, 120, 8
+    A = rng.standard_normal((m, n))
+    A[3] *= 30.0
+    b = rng.standard_normal(m)
+    L = oracle.kpp_factor(A, s, 1e-2)
+    res = oracle.run(A, b, L, s, lam=1e-2, tol=1e-10, max_iters=50000, seed=2)
+    assert res.status == oracle.OK
+    q, _ = np.linalg.qr(A.T)
+    null_part = res.x - q @ (q.T @ res.x)
+    assert np.linalg.norm(null_part) <= 1e-12 * np.linalg.norm(res.x)
+    x_mn = np.linalg.pinv(A) @ b
+    assert np.linalg.norm(res.x - x_mn) <= 1e-7 * np.linalg.norm(x_mn)
+
+
+def test_cdpp_converges_to_spd_solution():
+    rng = np.random.default_rng(41)
+    n, s = 256, 16
+    A, b, _ = W.spd(n, 6, 1e2, 1e3, 1.0, 4.0, seed_A=41, seed_b=42)
+    L = oracle.cdpp_factor(A, s, 1e-4)
+    res = oracle.run(A, b, L, s, cd=True, lam=1e-4, tol=1e-9, max_iters=200000, seed=4)
+    assert res.status == oracle.OK and res.rel_res_true <= 1e-9
+    x = np.linalg.solve(A, b)
+    assert np.linalg.norm(res.x - x) <= 1e-9 * 1e3 * np.linalg.norm(x)
+
+
+def test_adaptive_rho_schedule_structure():
+    """Alg. 3 lines 14-20 (parity unpinned): checkpoints every 2 zeta steps; rho in [0, 1); the first
+    rho follows from the first ratio as 1 - (E1/E0)^(1/zeta)."""
+    sy = W.kpp_fp64_2000x200()
+    L = oracle.kpp_factor(sy.A, sy.s, sy.lam)
+    res = oracle.run(sy.A, sy.b, L, sy.s, lam=sy.lam, tol=0.0, max_iters=2000, seed=0)
+    zeta = 100
+    tr = res.trace
+    assert len(tr) == 10
+    np.testing.assert_array_equal(tr[:, 0], np.arange(1, 11) * 2 * zeta - 1)
+    assert tr[0, 3] == 0.0  # rho_0 = 0 (Alg. 3 line 4)
+    rho1 = 1.0 - (tr[0, 2] / tr[0, 1]) ** (1.0 / zeta)
+    assert tr[1, 3] == pytest.approx(max(rho1, 0.0), rel=1e-12)
+    assert np.all((res.trace[:, 3] >= 0) & (res.trace[:, 3] < 1))
+
+
+def test_cg_matches_direct_solve():
+    rng = np.random.default_rng(51)
+    A = _rand_spd(80, rng, cond=1e3)
+    A = 0.5 * (A + A.T)
+    b = rng.standard_normal(80)
+    x, it, rr = oracle.cg(A, b, tol=1e-12)
+    assert rr <= 1e-12
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-8)
+
+
+def test_storage_rounding_is_exact_widening():
+    rng = np.random.default_rng(61)
+    A = rng.standard_normal((5, 7))
+    Ab = W.round_to_storage(A, "bf16")
+    # every bf16 value has at most 8 significant bits
+    m, e = np.frexp(Ab)
+    assert np.all(np.abs(m * 256 - np.round(m * 256)) == 0)
+    assert np.all(np.abs(Ab - A) <= 2.0 ** -8 * np.abs(A))
+    bits = W.bf16_bits(A).astype(np.uint32) << 16
+    np.testing.assert_array_equal(bits.view(np.float32).astype(np.float64), Ab)
