@@ -1,0 +1,198 @@
+/*
+ * kpp.h -- C ABI of the GB300 (sm_103a) Kaczmarz++ / CD++ block-step library (libkpp.so).
+ *
+ * Method: Derezinski, Needell, Rebrova, Yang, "Randomized Kaczmarz Methods with Beyond-Krylov
+ * Convergence" (arXiv 2501.11673).  Each solver iteration is one block step:
+ *   1. draw a block S of a fixed contiguous row partition (Alg. 1, "draw a random S from B");
+ *   2. block residual r = A_S x - b_S (Alg. 5) -- for CD++ the residual is kept up to date;
+ *   3. regularised projection y = (A_S A_S^T + lam I)^{-1} r (Eq. 1.3), or (A_SS + lam I)^{-1} r for
+ *      CD++ (Eq. 5.1), applied through a per-block factor memoised once (Sec. 4, Sec. 5.2);
+ *   4. w = A_S^T y (CD++: w = I_S^T y), m <- (1-rho)/(1+rho) (m - w), x <- x - w + eta m (Eq. 1.4);
+ *   5. residual estimate, adaptive rho and the stopping rule every 2 zeta steps (Eq. 5.2, Eq. 5.3,
+ *      Alg. 3 lines 14-20, Alg. 5 lines 13-19), confirmed by the true FP64 residual |Ax - b|/|b|.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are row-major with a leading dimension `ld` (elements).  A `kpp_matrix` names memory
+ *     the caller owns; the library never frees it.  Unless an entry point says otherwise, matrix and
+ *     vector pointers are DEVICE pointers on the current CUDA device.
+ *   - b and x are FP64 whatever the storage type of A.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is
+ *     stream-ordered.  Calls that fill a host `kpp_report` synchronise that stream before returning.
+ *   - Every call returns a kpp_status.  KPP_OK is 0.  On failure, kpp_last_error() returns a
+ *     thread-local message.  No entry point aborts the process or traps the GPU.  Device-side waits
+ *     are bounded; when the bound is hit the call returns KPP_ERR_TIMEOUT.
+ *   - Block partition: block j holds rows [j s, min((j+1) s, rows)), and nb = ceil(rows / s).
+ *   - Block draw at step t of system `sys_id`: out = Philox4x32-10(counter = {t_lo, t_hi, sys_id, 0},
+ *     key = {seed_lo, seed_hi}) (Salmon et al., SC'11).  j = (out[0] * nb) >> 32.
+ */
+#ifndef KPP_H
+#define KPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Storage type of the matrix entries. */
+typedef enum { KPP_F64 = 0, KPP_F32 = 1, KPP_BF16 = 2 } kpp_dtype;
+
+typedef enum {
+    KPP_OK = 0,
+    KPP_ERR_ARG = 1,            /* invalid argument: null pointer, bad size, dtype or partition mismatch */
+    KPP_ERR_CUDA = 2,           /* a CUDA runtime call failed (message in kpp_last_error) */
+    KPP_ERR_OOM = 3,            /* device allocation failed */
+    KPP_ERR_NOT_SPD = 4,        /* a block matrix had a non-positive Cholesky pivot (report.bad_block) */
+    KPP_ERR_NUMERIC = 5,        /* NaN or Inf appeared in the iterate or in a scalar */
+    KPP_ERR_NO_CONVERGENCE = 6, /* max_iters (or max_outer) reached; x holds the last iterate */
+    KPP_ERR_TIMEOUT = 7,        /* a bounded device-side wait expired; x holds the last iterate */
+    KPP_ERR_BUDGET = 8,         /* a serving request does not fit the memory budget */
+    KPP_ERR_UNSUPPORTED = 9     /* a combination this build does not implement */
+} kpp_status;
+
+/* A dense row-major matrix in caller-owned memory. */
+typedef struct {
+    const void *data;  /* first entry */
+    int32_t dtype;     /* kpp_dtype */
+    int32_t reserved;
+    int64_t rows;
+    int64_t cols;
+    int64_t ld;        /* leading dimension in elements, >= cols */
+} kpp_matrix;
+
+/* Library-owned handles. */
+typedef struct kpp_partition_s *kpp_partition_t;
+typedef struct kpp_factors_s *kpp_factors_t;
+
+/* Solver parameters.  Fill with kpp_params_default() and override fields as needed. */
+typedef struct {
+    double lambda;         /* Tikhonov regulariser (Eq. 1.3); must equal the factors' lambda */
+    double tol;            /* eps: stop when |Ax-b|/|b| <= eps (Alg. 3 line 16) */
+    int64_t max_iters;     /* cap on block iterations (per inner solve when refining) */
+    uint64_t seed;         /* Philox key */
+    uint32_t sys_id;       /* Philox stream id (system / request index) */
+    int32_t adaptive_rho;  /* 1: adaptive rho (Eq. 5.3); 0: rho fixed at rho0 */
+    double rho0;           /* initial rho (the paper starts from 0) or the fixed rho */
+    double eta;            /* momentum step; NaN selects s / (2 min(rows, cols)) (Sec. 5.4) */
+    int32_t grid;          /* CTAs per system; 0 selects automatically */
+    int32_t refine;        /* mixed precision: outer FP64 iterative refinement (F32/BF16 storage) */
+    int32_t max_outer;     /* cap on refinement steps */
+    int32_t reserved0;
+    double inner_tol;      /* relative tolerance of each inner (FP32) solve */
+    int64_t reserved1[4];
+} kpp_params;
+
+/* What a solve did. */
+typedef struct {
+    int64_t iters;         /* block iterations performed (all inner solves together) */
+    int64_t outer;         /* refinement steps (0 without refinement) */
+    double rel_res_true;   /* |A x - b| / |b| in FP64 at return */
+    double rel_res_est;    /* sqrt(E1) / |b| at the last checkpoint (NaN if none) */
+    double rho_final;      /* rho at return */
+    int32_t status;        /* kpp_status of the solve */
+    int32_t bad_block;     /* first block whose factorisation failed, else -1 */
+    double device_ms;      /* device time of the solve (CUDA events on `stream`) */
+    int64_t reserved[4];
+} kpp_report;
+
+/* Defaults: lambda 0, tol 1e-8, max_iters 10^6, seed 0, adaptive rho from 0, eta NaN (s/(2 min)),
+ * grid 0 (auto), refine 0, max_outer 20, inner_tol 1e-3. */
+kpp_params kpp_params_default(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *kpp_status_string(kpp_status st);
+
+/* Message of the last failing call on this thread (empty string if none). */
+const char *kpp_last_error(void);
+
+/* Fixed contiguous partition of `rows` rows into blocks of `s` rows: the block collection B of
+ * Alg. 1 line 4, held fixed so that every block's factor is memoised up front (Sec. 4).  The last
+ * block holds rows mod s rows when s does not divide rows.  Errors: KPP_ERR_ARG if rows < 1, s < 1
+ * or s > 1024.  Host-only; no device memory is used.  Free with kpp_partition_destroy. */
+kpp_status kpp_partition(int64_t rows, int32_t s, kpp_partition_t *out);
+void kpp_partition_destroy(kpp_partition_t p);
+/* Number of blocks nb = ceil(rows / s) of a partition (0 for a null handle). */
+int64_t kpp_partition_blocks(kpp_partition_t p);
+
+/* Memoised per-block factors (Sec. 4; Sec. 5.2; Alg. 1 line 7; Alg. 3 line 8).
+ *   mode 0 (K++):  G_j = A_{S_j} A_{S_j}^T + lambda I  (the block Gram; for F32/BF16 storage it is
+ *                  built on the tensor cores with FP32 accumulation, then widened to FP64);
+ *   mode 1 (CD++): G_j = A_{S_j S_j} + lambda I  (the principal block; A must be square and symmetric).
+ * For every block the library stores the FP64 lower Cholesky factor L_j (G_j = L_j L_j^T) and the
+ * inverse G_j^{-1} = L_j^{-T} L_j^{-1} formed from it.  The inverse turns each per-step projection
+ * into a parallel s x s matrix-vector product instead of two depth-s substitutions.  With F32/BF16
+ * storage it also keeps an FP32 copy of G_j^{-1} for the inner solves.
+ * A: device matrix, rows x cols (K++), or n x n symmetric (CD++).  Its rows must equal the
+ * partition's rows.  The factors are device memory owned by the handle.  They stay valid while A is
+ * unchanged.  Errors: KPP_ERR_ARG, KPP_ERR_OOM, KPP_ERR_CUDA, and KPP_ERR_NOT_SPD when a pivot is
+ * <= 0 or not finite.  On NOT_SPD, *out is still created and kpp_factors_bad_block names the block.
+ * Synchronises `stream`. */
+kpp_status kpp_factor_blocks(const kpp_matrix *A, kpp_partition_t P, double lambda, int32_t mode,
+                             kpp_factors_t *out, void *stream);
+void kpp_factors_destroy(kpp_factors_t f);
+/* First block whose factorisation failed, or -1. */
+int64_t kpp_factors_bad_block(kpp_factors_t f);
+/* Copy the FP64 factor L_j (len x len, row-major, lower; len = length of block j) to host memory
+ * `out` (len*len doubles).  For tests and inspection.  Errors: KPP_ERR_ARG for a bad j. */
+kpp_status kpp_factors_get_block(kpp_factors_t f, int64_t j, double *out_host);
+
+/* Kaczmarz++ solve of A x = b: Alg. 5 with exact memoised projections (the K++(Cholesky) variant of
+ * App. F), a fixed partition, no randomised Hadamard preprocessing.
+ * A: device rows x cols, any dtype.  b: device FP64 [rows].  x: device FP64 [cols], holding x0 on
+ * entry and the last iterate on return.  F: from kpp_factor_blocks(mode 0) on the same A and P.
+ * With F32/BF16 storage and p->refine = 1, each outer step computes r = b - A x in FP64, solves
+ * A d = r with FP32 K++ to p->inner_tol, and updates x += d in FP64.  Without refinement the
+ * iteration runs in the storage precision of A (FP64 or FP32 arithmetic).
+ * rep (host, may be NULL): filled on return.  Errors: KPP_ERR_ARG on shape, dtype or lambda
+ * mismatch; KPP_ERR_NO_CONVERGENCE; KPP_ERR_NUMERIC; KPP_ERR_TIMEOUT; KPP_ERR_CUDA.
+ * Synchronises `stream`. */
+kpp_status kpp_solve(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P,
+                     kpp_factors_t F, const kpp_params *p, kpp_report *rep, void *stream);
+
+/* CD++ solve of A x = b for symmetric positive (semi)definite A (Eq. 5.1; Alg. 3 without the
+ * randomised Hadamard transform).  The residual R_x = A x - b and R_m = A m are kept up to date
+ * (R_m <- beta (R_m - u), R_x <- R_x - u + eta R_m with u = A_{:,S} y), so a step reads the block
+ * rows of A once and gathers r = R_x[S].  At each checkpoint that passes the estimate, the residual is
+ * recomputed from A and replaces R_x.  Arguments and errors are as for kpp_solve; F must come from
+ * kpp_factor_blocks(mode 1); A is n x n. */
+kpp_status cdpp_solve(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P,
+                      kpp_factors_t F, const kpp_params *p, kpp_report *rep, void *stream);
+
+/* End-to-end host variants: A (rows x cols, dtype per A->dtype, row-major), b and x are HOST
+ * pointers.  The call copies A and b to the device, factors, solves and copies x back.  Device
+ * buffers are allocated and freed inside the call.  mode 0 = K++, 1 = CD++. */
+kpp_status kpp_solve_host(const kpp_matrix *A_host, const double *b_host, double *x_host, int32_t s,
+                          int32_t mode, const kpp_params *p, kpp_report *rep, void *stream);
+
+/* |A x - b|_2 / |b|_2 with FP64 accumulation (stored entries widened exactly) -- the stopping
+ * rule's confirmation (Alg. 3 line 16).  A, b, x: device.  Result to *out_host.  Synchronises. */
+kpp_status kpp_rel_residual(const kpp_matrix *A, const double *b, const double *x, double *out_host,
+                            void *stream);
+
+/* Batched K++ over `nsys` independent systems that share shape, dtype and block size, each with a
+ * panel of k right-hand sides: system i has matrix A[i] (device,
+ * rows x cols), right-hand sides B[i] (device FP64, rows x k, row-major) and iterates X[i] (device
+ * FP64, cols x k, row-major, x0 on entry).  Factors F[i] come from kpp_factor_blocks(mode 0).
+ * Every RHS column runs its own rho, residual estimate and stopping rule, and the k columns of a
+ * system share the block sequence of Philox stream sys_id = p->sys_id + i.  All systems advance in
+ * one persistent launch (p->grid CTAs per system).  reps (host, may be NULL): nsys * k reports in
+ * system-major order.  Errors are as for kpp_solve.  The worst status is returned. */
+kpp_status kpp_solve_batched(int32_t nsys, const kpp_matrix *A, const double *const *B, double *const *X,
+                             int32_t k, kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p,
+                             kpp_report *reps, void *stream);
+
+/* The block indices the solver draws at steps t0 .. t0+count-1 of Philox stream `sys_id` (see the
+ * draw rule above), computed on the device by the same code the solve kernel uses.  out: device
+ * int32[count].  Errors: KPP_ERR_ARG for count < 0, nb < 1 or a null pointer.  Stream-ordered. */
+kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t count, int32_t nb, int32_t *out,
+                             void *stream);
+
+/* Library build information: "sm_103a; <compiler>; <date>". */
+const char *kpp_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KPP_H */

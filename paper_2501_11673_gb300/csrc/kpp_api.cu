@@ -1,0 +1,656 @@
+// kpp_api.cu -- the extern "C" boundary of libkpp (declared in include/kpp.h).
+//
+// Host-side orchestration only: argument checks, device buffers of a solve, the launch of the
+// persistent solve kernel, the FP64 iterative-refinement loop of the mixed-precision form, and the
+// report.  Every arithmetic step of the method runs in the kernels of kpp_solve.cu / kpp_factor.cu /
+// kpp_gram_tc.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kpp_internal.cuh"
+#include "kpp_runtime.h"
+#include "kpp_solve.h"
+
+struct kpp_partition_s {
+    int64_t rows;
+    int32_t s;
+    int64_t nb;
+};
+
+struct kpp_factors_s {
+    kpp::FactorSet f;
+};
+
+namespace kpp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+void clear_error() { g_last_error.clear(); }
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+void FactorSet::release() {
+    if (L) cudaFree(L);
+    if (Ginv) cudaFree(Ginv);
+    if (Ginv32) cudaFree(Ginv32);
+    L = nullptr;
+    Ginv = nullptr;
+    Ginv32 = nullptr;
+}
+
+static size_t dtype_size(int dt) { return dt == KPP_F64 ? 8 : (dt == KPP_F32 ? 4 : 2); }
+
+static bool matrix_ok(const kpp_matrix *A) {
+    return A && A->data && A->rows > 0 && A->cols > 0 && A->ld >= A->cols &&
+           (A->dtype == KPP_F64 || A->dtype == KPP_F32 || A->dtype == KPP_BF16);
+}
+
+#define CUDA_OR(call, code)                                                    \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            set_error("%s: %s", #call, cudaGetErrorString(e_));                \
+            rc = (e_ == cudaErrorMemoryAllocation) ? KPP_ERR_OOM : (code);     \
+            goto cleanup;                                                      \
+        }                                                                      \
+    } while (0)
+
+// Stream-ordered scratch that is freed when the object goes out of scope.
+struct Scratch {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    cudaError_t alloc(void **p, size_t bytes) {
+        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    ~Scratch() {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+// |A x - b|^2 and |b|^2 per column (deterministic: fixed grid, host sums in a fixed order).
+static kpp_status residual_norms(const kpp_matrix &A, int k, const double *b, const double *x, float *r32,
+                                 std::vector<double> &res2, std::vector<double> *bn2, cudaStream_t st) {
+    kpp_status rc = KPP_OK;
+    const int grid = residual_grid();
+    std::vector<double> h((size_t)grid * k);
+    Scratch scr(st);
+    double *part = nullptr;
+    CUDA_OR(scr.alloc((void **)&part, (size_t)grid * k * sizeof(double)), KPP_ERR_CUDA);
+    res2.assign(k, 0.0);
+    CUDA_OR(launch_residual(A, k, b, x, r32, part, st), KPP_ERR_CUDA);
+    CUDA_OR(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), KPP_ERR_CUDA);
+    CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
+    for (int gi = 0; gi < grid; ++gi)
+        for (int c = 0; c < k; ++c) res2[c] += h[(size_t)gi * k + c];
+    if (bn2) {
+        bn2->assign(k, 0.0);
+        CUDA_OR(launch_residual(A, k, b, nullptr, nullptr, part, st), KPP_ERR_CUDA);
+        CUDA_OR(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), KPP_ERR_CUDA);
+        CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
+        for (int gi = 0; gi < grid; ++gi)
+            for (int c = 0; c < k; ++c) (*bn2)[c] += h[(size_t)gi * k + c];
+    }
+cleanup:
+    return rc;
+}
+
+// One system's buffers for a launch of the persistent kernel.
+struct SysInput {
+    const kpp_matrix *A;
+    const void *b;        // TC, rows x k
+    void *x;              // TC, cols x k
+    const FactorSet *F;
+    uint32_t sys_id;
+    SolveScalars *sc_host; // k entries, in/out
+};
+
+static int auto_grid(int64_t cols, int nsys) {
+    // enough CTAs to spread the block rows, at most one CTA per SM for the whole launch
+    int per = (int)std::min<int64_t>((cols + 31) / 32, 1024);
+    int cap = std::max(1, sm_count() / std::max(1, nsys));
+    return std::max(1, std::min(per, cap));
+}
+
+// Run the persistent kernel over nsys systems that share shape, dtype, s and k.
+static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd, int k, int s, double eta,
+                                 double tol, int adaptive, int confirm, int64_t max_iters, uint64_t seed, int grid,
+                                 bool init_residual, int64_t t0, cudaStream_t st, float *ms_out, int *err_out) {
+    kpp_status rc = KPP_OK;
+    const int nsys = (int)sys.size();
+    const kpp_matrix &A0 = *sys[0].A;
+    const bool f64 = dtype == KPP_F64;
+    const size_t tcs = f64 ? 8 : 4;
+    const int KP = pick_kp(k);
+    const int G = grid > 0 ? grid : auto_grid(A0.cols, nsys);
+    const int64_t sector = 32 / (int64_t)dtype_size(dtype);
+    int64_t CW = (A0.cols + G - 1) / G;
+    CW = (CW + sector - 1) / sector * sector;
+    const int nb = (int)((A0.rows + s - 1) / s);
+    Common cm{};
+    cm.rows = A0.rows;
+    cm.cols = A0.cols;
+    cm.s = s;
+    cm.nb = nb;
+    cm.k = k;
+    cm.CW = CW;
+    cm.G = G;
+    cm.eta = eta;
+    cm.tol = tol;
+    cm.adaptive = adaptive;
+    cm.confirm = confirm;
+    cm.reduce_redundant = ((int64_t)G * s * KP <= 8192) ? 1 : 0;
+    cm.init_residual = init_residual ? 1 : 0;
+    cm.max_iters = max_iters;
+    cm.seed = seed;
+    cm.timeout_ns = 2000000000ull;
+
+    const size_t smem = solve_smem_bytes(s, KP, CW, tcs);
+    if (smem > 220 * 1024) {
+        set_error("shared memory %zu B exceeds the per-CTA limit (s=%d, k=%d, chunk=%lld)", smem, s, k, (long long)CW);
+        return KPP_ERR_UNSUPPORTED;
+    }
+    Scratch scr(st);
+    std::vector<SysArgs> args(nsys);
+    SysArgs *d_args = nullptr;
+    unsigned *bars = nullptr;
+    int *errs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<int> herr(nsys, 0);
+    const size_t vec_n = (size_t)A0.cols * k, vec_r = (size_t)A0.rows * k;
+    CUDA_OR(scr.alloc((void **)&bars, nsys * sizeof(unsigned)), KPP_ERR_CUDA);
+    CUDA_OR(scr.alloc((void **)&errs, nsys * sizeof(int)), KPP_ERR_CUDA);
+    CUDA_OR(cudaMemsetAsync(bars, 0, nsys * sizeof(unsigned), st), KPP_ERR_CUDA);
+    CUDA_OR(cudaMemsetAsync(errs, 0, nsys * sizeof(int), st), KPP_ERR_CUDA);
+    for (int i = 0; i < nsys; ++i) {
+        SysArgs &a = args[i];
+        a.A = sys[i].A->data;
+        a.lda = sys[i].A->ld;
+        a.b = sys[i].b;
+        a.x = sys[i].x;
+        a.Ginv = f64 ? (const void *)sys[i].F->Ginv : (const void *)sys[i].F->Ginv32;
+        CUDA_OR(scr.alloc(&a.m, vec_n * tcs), KPP_ERR_CUDA);
+        CUDA_OR(cudaMemsetAsync(a.m, 0, vec_n * tcs, st), KPP_ERR_CUDA);
+        if (cd) {
+            CUDA_OR(scr.alloc(&a.Rx, vec_r * tcs), KPP_ERR_CUDA);
+            CUDA_OR(scr.alloc(&a.Rm, vec_r * tcs), KPP_ERR_CUDA);
+            CUDA_OR(cudaMemsetAsync(a.Rm, 0, vec_r * tcs, st), KPP_ERR_CUDA);
+            if (!init_residual) {  // x0 = 0: R_x = -b
+                CUDA_OR(launch_negate_copy(vec_r, a.b, a.Rx, f64, st), KPP_ERR_CUDA);
+            }
+        } else {
+            a.Rx = a.Rm = nullptr;
+        }
+        CUDA_OR(scr.alloc(&a.part, (size_t)G * s * KP * tcs), KPP_ERR_CUDA);
+        CUDA_OR(scr.alloc(&a.rbuf, (size_t)s * KP * tcs), KPP_ERR_CUDA);
+        CUDA_OR(scr.alloc(&a.ybuf, (size_t)s * KP * tcs), KPP_ERR_CUDA);
+        CUDA_OR(scr.alloc((void **)&a.rpart, (size_t)G * KP * sizeof(double)), KPP_ERR_CUDA);
+        CUDA_OR(scr.alloc((void **)&a.sc, (size_t)k * sizeof(SolveScalars)), KPP_ERR_CUDA);
+        CUDA_OR(cudaMemcpyAsync(a.sc, sys[i].sc_host, (size_t)k * sizeof(SolveScalars), cudaMemcpyHostToDevice, st),
+                KPP_ERR_CUDA);
+        a.bar = bars + i;
+        a.err = errs + i;
+        a.sys_id = sys[i].sys_id;
+        a.t0 = t0;
+    }
+    CUDA_OR(scr.alloc((void **)&d_args, nsys * sizeof(SysArgs)), KPP_ERR_CUDA);
+    CUDA_OR(cudaMemcpyAsync(d_args, args.data(), nsys * sizeof(SysArgs), cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
+    CUDA_OR(cudaEventCreate(&e0), KPP_ERR_CUDA);
+    CUDA_OR(cudaEventCreate(&e1), KPP_ERR_CUDA);
+    CUDA_OR(cudaEventRecord(e0, st), KPP_ERR_CUDA);
+    {
+        cudaError_t le = launch_solve(dtype, f64, cd, d_args, nsys, cm, KP, st);
+        if (le == cudaErrorCooperativeLaunchTooLarge) {
+            set_error("%d systems x %d CTAs do not fit co-resident on this GPU", nsys, G);
+            rc = KPP_ERR_UNSUPPORTED;
+            goto cleanup;
+        }
+        CUDA_OR(le, KPP_ERR_CUDA);
+    }
+    CUDA_OR(cudaEventRecord(e1, st), KPP_ERR_CUDA);
+    for (int i = 0; i < nsys; ++i)
+        CUDA_OR(cudaMemcpyAsync(sys[i].sc_host, args[i].sc, (size_t)k * sizeof(SolveScalars), cudaMemcpyDeviceToHost, st),
+                KPP_ERR_CUDA);
+    CUDA_OR(cudaMemcpyAsync(herr.data(), errs, nsys * sizeof(int), cudaMemcpyDeviceToHost, st), KPP_ERR_CUDA);
+    CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
+    if (ms_out) cudaEventElapsedTime(ms_out, e0, e1);
+    for (int i = 0; i < nsys; ++i) {
+        err_out[i] = herr[i];
+        if (herr[i]) {
+            set_error("system %d: device error %d (%s)", i, herr[i], kpp_status_string((kpp_status)herr[i]));
+            if (rc == KPP_OK) rc = (kpp_status)herr[i];
+        }
+    }
+cleanup:
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}
+
+static void init_scalars(std::vector<SolveScalars> &sc, int k, double rho0) {
+    sc.assign(k, SolveScalars{});
+    for (int c = 0; c < k; ++c) {
+        sc[c].rho = rho0;
+        sc[c].active = 1;
+        sc[c].status = KPP_ERR_NO_CONVERGENCE;
+        sc[c].res_est = NAN;
+    }
+}
+
+static double default_eta(const kpp_params &p, int s, int64_t rows, int64_t cols) {
+    if (!std::isnan(p.eta)) return p.eta;
+    return (double)s / (2.0 * (double)std::min(rows, cols));
+}
+
+static kpp_status worse(kpp_status a, kpp_status b) { return a != KPP_OK ? a : b; }
+
+// The solve of `nsys` systems with k right-hand sides each (FP64 b/x on the device).
+static kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
+                                kpp_partition_t P, const kpp_factors_t *F, const kpp_params *pp, kpp_report *reps,
+                                cudaStream_t st, bool cd) {
+    clear_error();
+    if (nsys < 1 || !A || !B || !X || !P || !F || !pp || k < 1 || k > 32) {
+        set_error("invalid argument (nsys=%d, k=%d)", nsys, k);
+        return KPP_ERR_ARG;
+    }
+    const kpp_params p = *pp;
+    const int s = P->s;
+    for (int i = 0; i < nsys; ++i) {
+        if (!matrix_ok(&A[i]) || !B[i] || !X[i] || !F[i]) {
+            set_error("system %d: null or malformed argument", i);
+            return KPP_ERR_ARG;
+        }
+        if (A[i].rows != P->rows || A[i].rows != A[0].rows || A[i].cols != A[0].cols || A[i].dtype != A[0].dtype) {
+            set_error("system %d: shape/dtype differs from the partition or from system 0", i);
+            return KPP_ERR_ARG;
+        }
+        const FactorSet &f = F[i]->f;
+        if (f.rows != A[i].rows || f.s != s || f.mode != (cd ? 1 : 0) || f.dtype != A[i].dtype || f.bad_block >= 0 ||
+            std::fabs(f.lambda - p.lambda) > 1e-15 * std::max(1.0, std::fabs(p.lambda))) {
+            set_error("system %d: factors do not match (mode, s, dtype, lambda or a failed block)", i);
+            return KPP_ERR_ARG;
+        }
+        if (cd && A[i].rows != A[i].cols) {
+            set_error("CD++ needs a square matrix");
+            return KPP_ERR_ARG;
+        }
+    }
+    const int dtype = A[0].dtype;
+    const int64_t rows = A[0].rows, cols = A[0].cols;
+    const double eta = default_eta(p, s, rows, cols);
+    kpp_status rc = KPP_OK;
+    std::vector<std::vector<SolveScalars>> sc(nsys);
+    std::vector<int> errs(nsys, 0);
+    std::vector<SysInput> in(nsys);
+    std::vector<double> dev_ms(nsys, 0.0);
+    std::vector<int64_t> iters(nsys, 0), outer(nsys, 0);
+    for (int i = 0; i < nsys; ++i) init_scalars(sc[i], k, p.rho0);
+    float ms = 0.f;
+
+    if (dtype == KPP_F64) {
+        // plain FP64 path: the kernel iterates directly on the caller's b and x
+        for (int i = 0; i < nsys; ++i) in[i] = SysInput{&A[i], B[i], X[i], &F[i]->f, p.sys_id + (uint32_t)i, sc[i].data()};
+        rc = run_persistent(in, dtype, cd, k, s, eta, p.tol, p.adaptive_rho, 1, p.max_iters, p.seed, p.grid,
+                            /*init_residual=*/true, 0, st, &ms, errs.data());
+        for (int i = 0; i < nsys; ++i) {
+            dev_ms[i] = ms;
+            iters[i] = sc[i][0].t;
+        }
+    } else {
+        // FP32 / BF16 storage: FP32 iterations, FP64 outer refinement (or a single FP32 solve)
+        Scratch scr(st);
+        std::vector<float *> b32(nsys), d32(nsys);
+        std::vector<std::vector<double>> bn2(nsys), res2(nsys);
+        std::vector<int> done(nsys, 0);
+        const size_t nr = (size_t)rows * k, nc = (size_t)cols * k;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int64_t t_global = 0;
+        CUDA_OR(cudaEventCreate(&e0), KPP_ERR_CUDA);
+        CUDA_OR(cudaEventCreate(&e1), KPP_ERR_CUDA);
+        CUDA_OR(cudaEventRecord(e0, st), KPP_ERR_CUDA);
+        for (int i = 0; i < nsys; ++i) {
+            CUDA_OR(scr.alloc((void **)&b32[i], nr * sizeof(float)), KPP_ERR_CUDA);
+            CUDA_OR(scr.alloc((void **)&d32[i], nc * sizeof(float)), KPP_ERR_CUDA);
+        }
+        if (!p.refine) {
+            for (int i = 0; i < nsys; ++i) {
+                CUDA_OR(launch_f64_to_f32(nr, B[i], b32[i], st), KPP_ERR_CUDA);
+                CUDA_OR(launch_f64_to_f32(nc, X[i], d32[i], st), KPP_ERR_CUDA);
+                in[i] = SysInput{&A[i], b32[i], d32[i], &F[i]->f, p.sys_id + (uint32_t)i, sc[i].data()};
+            }
+            rc = run_persistent(in, dtype, cd, k, s, eta, p.tol, p.adaptive_rho, 0, p.max_iters, p.seed, p.grid,
+                                true, 0, st, &ms, errs.data());
+            for (int i = 0; i < nsys; ++i) {
+                // x = double(x32): overwrite through the axpy of (x32 - x) is not exact; copy via zero + axpy
+                CUDA_OR(cudaMemsetAsync(X[i], 0, nc * sizeof(double), st), KPP_ERR_CUDA);
+                CUDA_OR(launch_axpy(nc, d32[i], X[i], st), KPP_ERR_CUDA);
+                iters[i] = sc[i][0].t;
+            }
+        } else {
+            for (int outer_it = 0; outer_it <= p.max_outer; ++outer_it) {
+                // r = b - A x in FP64 (rounded copy to FP32 as the inner right-hand side)
+                bool any = false;
+                for (int i = 0; i < nsys; ++i) {
+                    if (done[i]) continue;
+                    kpp_status r2 = residual_norms(A[i], k, B[i], X[i], b32[i], res2[i], outer_it == 0 ? &bn2[i] : nullptr, st);
+                    if (r2 != KPP_OK) {
+                        rc = r2;
+                        goto cleanup;
+                    }
+                    int active = 0;
+                    for (int c = 0; c < k; ++c) {
+                        const double rel = bn2[i][c] > 0 ? std::sqrt(res2[i][c] / bn2[i][c]) : std::sqrt(res2[i][c]);
+                        const bool conv = rel <= p.tol;
+                        sc[i][c].active = conv ? 0 : 1;
+                        sc[i][c].status = conv ? KPP_OK : KPP_ERR_NO_CONVERGENCE;
+                        sc[i][c].E0 = sc[i][c].E1 = 0.0;
+                        active += !conv;
+                    }
+                    if (!active) done[i] = 1;
+                    else any = true;
+                }
+                if (!any || outer_it == p.max_outer) break;
+                // inner FP32 solve of A d = r from d = 0 (momentum restarts, rho carries over)
+                std::vector<SysInput> act;
+                std::vector<int> idx;
+                for (int i = 0; i < nsys; ++i) {
+                    if (done[i]) continue;
+                    CUDA_OR(cudaMemsetAsync(d32[i], 0, nc * sizeof(float), st), KPP_ERR_CUDA);
+                    act.push_back(SysInput{&A[i], b32[i], d32[i], &F[i]->f, p.sys_id + (uint32_t)i, sc[i].data()});
+                    idx.push_back(i);
+                    outer[i] += 1;
+                }
+                std::vector<int> e2(act.size(), 0);
+                kpp_status ri = run_persistent(act, dtype, cd, k, s, eta, p.inner_tol, p.adaptive_rho, 0,
+                                               t_global + p.max_iters, p.seed, p.grid, false, t_global, st, nullptr,
+                                               e2.data());
+                int64_t tmax = t_global;
+                for (size_t q = 0; q < act.size(); ++q) {
+                    const int i = idx[q];
+                    errs[i] = e2[q];
+                    iters[i] += sc[i][0].t - t_global;
+                    tmax = std::max<int64_t>(tmax, sc[i][0].t);
+                    CUDA_OR(launch_axpy(nc, d32[i], X[i], st), KPP_ERR_CUDA);
+                }
+                // keep the Philox counter moving so that inner solves do not replay one block sequence
+                t_global = tmax;
+                if (ri != KPP_OK && ri != KPP_ERR_NO_CONVERGENCE) {
+                    rc = ri;
+                    goto cleanup;
+                }
+            }
+        }
+        CUDA_OR(cudaEventRecord(e1, st), KPP_ERR_CUDA);
+        CUDA_OR(cudaEventSynchronize(e1), KPP_ERR_CUDA);
+        cudaEventElapsedTime(&ms, e0, e1);
+        for (int i = 0; i < nsys; ++i) dev_ms[i] = ms;
+    cleanup:
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (rc != KPP_OK && rc != KPP_ERR_NO_CONVERGENCE) return rc;
+    }
+    if (rc != KPP_OK && rc != KPP_ERR_NO_CONVERGENCE && rc != KPP_ERR_TIMEOUT && rc != KPP_ERR_NUMERIC) return rc;
+
+    // final report: true FP64 residual of every column
+    kpp_status worst = rc;
+    for (int i = 0; i < nsys; ++i) {
+        std::vector<double> r2, b2;
+        kpp_status r3 = residual_norms(A[i], k, B[i], X[i], nullptr, r2, &b2, st);
+        if (r3 != KPP_OK) return r3;
+        for (int c = 0; c < k; ++c) {
+            const double rel = b2[c] > 0 ? std::sqrt(r2[c] / b2[c]) : std::sqrt(r2[c]);
+            kpp_status cs = (kpp_status)sc[i][c].status;
+            if (errs[i]) cs = (kpp_status)errs[i];
+            else if (!std::isfinite(rel)) cs = KPP_ERR_NUMERIC;
+            else if (dtype != KPP_F64 && p.refine) cs = rel <= p.tol ? KPP_OK : KPP_ERR_NO_CONVERGENCE;
+            worst = worse(worst, cs);
+            if (reps) {
+                kpp_report &r = reps[(size_t)i * k + c];
+                memset(&r, 0, sizeof(r));
+                r.iters = iters[i];
+                r.outer = outer[i];
+                r.rel_res_true = rel;
+                r.rel_res_est = sc[i][c].res_est;
+                r.rho_final = sc[i][c].rho;
+                r.status = cs;
+                r.bad_block = -1;
+                r.device_ms = dev_ms[i];
+            }
+        }
+    }
+    if (worst != KPP_OK && g_last_error.empty()) set_error("solve ended with %s", kpp_status_string(worst));
+    return worst;
+}
+
+}  // namespace kpp
+
+using namespace kpp;
+
+extern "C" {
+
+kpp_params kpp_params_default(void) {
+    kpp_params p;
+    memset(&p, 0, sizeof(p));
+    p.lambda = 0.0;
+    p.tol = 1e-8;
+    p.max_iters = 1000000;
+    p.seed = 0;
+    p.sys_id = 0;
+    p.adaptive_rho = 1;
+    p.rho0 = 0.0;
+    p.eta = NAN;
+    p.grid = 0;
+    p.refine = 0;
+    p.max_outer = 20;
+    p.inner_tol = 1e-3;
+    return p;
+}
+
+const char *kpp_status_string(kpp_status st) {
+    switch (st) {
+        case KPP_OK: return "KPP_OK";
+        case KPP_ERR_ARG: return "KPP_ERR_ARG";
+        case KPP_ERR_CUDA: return "KPP_ERR_CUDA";
+        case KPP_ERR_OOM: return "KPP_ERR_OOM";
+        case KPP_ERR_NOT_SPD: return "KPP_ERR_NOT_SPD";
+        case KPP_ERR_NUMERIC: return "KPP_ERR_NUMERIC";
+        case KPP_ERR_NO_CONVERGENCE: return "KPP_ERR_NO_CONVERGENCE";
+        case KPP_ERR_TIMEOUT: return "KPP_ERR_TIMEOUT";
+        case KPP_ERR_BUDGET: return "KPP_ERR_BUDGET";
+        case KPP_ERR_UNSUPPORTED: return "KPP_ERR_UNSUPPORTED";
+    }
+    return "KPP_ERR_UNKNOWN";
+}
+
+const char *kpp_last_error(void) { return g_last_error.c_str(); }
+
+#define KPP_STR2(x) #x
+#define KPP_STR(x) KPP_STR2(x)
+const char *kpp_build_info(void) {
+    return "sm_103a; nvcc " KPP_STR(__CUDACC_VER_MAJOR__) "." KPP_STR(__CUDACC_VER_MINOR__) "; " __DATE__;
+}
+
+kpp_status kpp_partition(int64_t rows, int32_t s, kpp_partition_t *out) {
+    clear_error();
+    if (!out || rows < 1 || s < 1 || s > 1024) {
+        set_error("kpp_partition: rows=%lld s=%d", (long long)rows, s);
+        return KPP_ERR_ARG;
+    }
+    kpp_partition_t p = new kpp_partition_s;
+    p->rows = rows;
+    p->s = s;
+    p->nb = (rows + s - 1) / s;
+    *out = p;
+    return KPP_OK;
+}
+
+void kpp_partition_destroy(kpp_partition_t p) { delete p; }
+
+int64_t kpp_partition_blocks(kpp_partition_t p) { return p ? p->nb : 0; }
+
+kpp_status kpp_factor_blocks(const kpp_matrix *A, kpp_partition_t P, double lambda, int32_t mode, kpp_factors_t *out,
+                             void *stream) {
+    clear_error();
+    if (!out || !P || !matrix_ok(A) || (mode != 0 && mode != 1) || !(lambda >= 0.0) || A->rows != P->rows ||
+        (mode == 1 && A->rows != A->cols)) {
+        set_error("kpp_factor_blocks: invalid argument");
+        return KPP_ERR_ARG;
+    }
+    kpp_factors_t f = new kpp_factors_s;
+    kpp_status rc = factor_blocks_impl(*A, P->s, lambda, mode, f->f, (cudaStream_t)stream);
+    if (rc != KPP_OK && rc != KPP_ERR_NOT_SPD) {
+        f->f.release();
+        delete f;
+        *out = nullptr;
+        return rc;
+    }
+    *out = f;
+    return rc;
+}
+
+void kpp_factors_destroy(kpp_factors_t f) {
+    if (!f) return;
+    f->f.release();
+    delete f;
+}
+
+int64_t kpp_factors_bad_block(kpp_factors_t f) { return f ? f->f.bad_block : -1; }
+
+kpp_status kpp_factors_get_block(kpp_factors_t f, int64_t j, double *out_host) {
+    clear_error();
+    if (!f || !out_host || j < 0 || j >= f->f.nb) {
+        set_error("kpp_factors_get_block: bad handle or block index");
+        return KPP_ERR_ARG;
+    }
+    const int64_t len = std::min<int64_t>(f->f.s, f->f.rows - j * f->f.s);
+    cudaError_t e = cudaMemcpy(out_host, f->f.L + (size_t)j * f->f.s * f->f.s, (size_t)len * len * sizeof(double),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_error("cudaMemcpy: %s", cudaGetErrorString(e));
+        return KPP_ERR_CUDA;
+    }
+    return KPP_OK;
+}
+
+kpp_status kpp_solve(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
+                     const kpp_params *p, kpp_report *rep, void *stream) {
+    const double *B[1] = {b};
+    double *X[1] = {x};
+    return solve_systems(1, A, B, X, 1, P, &F, p, rep, (cudaStream_t)stream, false);
+}
+
+kpp_status cdpp_solve(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
+                      const kpp_params *p, kpp_report *rep, void *stream) {
+    const double *B[1] = {b};
+    double *X[1] = {x};
+    return solve_systems(1, A, B, X, 1, P, &F, p, rep, (cudaStream_t)stream, true);
+}
+
+kpp_status kpp_solve_batched(int32_t nsys, const kpp_matrix *A, const double *const *B, double *const *X, int32_t k,
+                             kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p, kpp_report *reps,
+                             void *stream) {
+    return solve_systems(nsys, A, B, X, k, P, F, p, reps, (cudaStream_t)stream, false);
+}
+
+kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t count, int32_t nb, int32_t *out,
+                             void *stream) {
+    clear_error();
+    if (count < 0 || nb < 1 || (count > 0 && !out)) {
+        set_error("kpp_sample_blocks: invalid argument");
+        return KPP_ERR_ARG;
+    }
+    cudaError_t e = launch_sample_blocks(seed, sys_id, t0, count, nb, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error("sample kernel: %s", cudaGetErrorString(e));
+        return KPP_ERR_CUDA;
+    }
+    return KPP_OK;
+}
+
+kpp_status kpp_rel_residual(const kpp_matrix *A, const double *b, const double *x, double *out_host, void *stream) {
+    clear_error();
+    if (!matrix_ok(A) || !b || !x || !out_host) {
+        set_error("kpp_rel_residual: invalid argument");
+        return KPP_ERR_ARG;
+    }
+    std::vector<double> r2, b2;
+    kpp_status rc = residual_norms(*A, 1, b, x, nullptr, r2, &b2, (cudaStream_t)stream);
+    if (rc != KPP_OK) return rc;
+    *out_host = b2[0] > 0 ? std::sqrt(r2[0] / b2[0]) : std::sqrt(r2[0]);
+    return KPP_OK;
+}
+
+kpp_status kpp_solve_host(const kpp_matrix *A_host, const double *b_host, double *x_host, int32_t s, int32_t mode,
+                          const kpp_params *p, kpp_report *rep, void *stream) {
+    clear_error();
+    if (!matrix_ok(A_host) || !b_host || !x_host || !p || (mode != 0 && mode != 1)) {
+        set_error("kpp_solve_host: invalid argument");
+        return KPP_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    kpp_status rc = KPP_OK;
+    const size_t es = dtype_size(A_host->dtype);
+    const size_t abytes = (size_t)A_host->rows * A_host->cols * es;
+    void *dA = nullptr;
+    double *db = nullptr, *dx = nullptr;
+    kpp_partition_t P = nullptr;
+    kpp_factors_t F = nullptr;
+    kpp_matrix Ad = *A_host;
+    CUDA_OR(cudaMalloc(&dA, abytes), KPP_ERR_CUDA);
+    CUDA_OR(cudaMalloc((void **)&db, A_host->rows * sizeof(double)), KPP_ERR_CUDA);
+    CUDA_OR(cudaMalloc((void **)&dx, A_host->cols * sizeof(double)), KPP_ERR_CUDA);
+    CUDA_OR(cudaMemcpy2DAsync(dA, A_host->cols * es, A_host->data, A_host->ld * es, A_host->cols * es, A_host->rows,
+                              cudaMemcpyHostToDevice, st),
+            KPP_ERR_CUDA);
+    CUDA_OR(cudaMemcpyAsync(db, b_host, A_host->rows * sizeof(double), cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
+    CUDA_OR(cudaMemcpyAsync(dx, x_host, A_host->cols * sizeof(double), cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
+    Ad.data = dA;
+    Ad.ld = A_host->cols;
+    rc = kpp_partition(A_host->rows, s, &P);
+    if (rc != KPP_OK) goto cleanup;
+    rc = kpp_factor_blocks(&Ad, P, p->lambda, mode, &F, stream);
+    if (rc != KPP_OK) goto cleanup;
+    rc = mode == 0 ? kpp_solve(&Ad, db, dx, P, F, p, rep, stream) : cdpp_solve(&Ad, db, dx, P, F, p, rep, stream);
+    {
+        cudaError_t e = cudaMemcpyAsync(x_host, dx, A_host->cols * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess && rc == KPP_OK) {
+            set_error("copy back: %s", cudaGetErrorString(e));
+            rc = KPP_ERR_CUDA;
+        }
+    }
+cleanup:
+    if (F) kpp_factors_destroy(F);
+    if (P) kpp_partition_destroy(P);
+    if (dA) cudaFree(dA);
+    if (db) cudaFree(db);
+    if (dx) cudaFree(dx);
+    return rc;
+}
+
+}  // extern "C"

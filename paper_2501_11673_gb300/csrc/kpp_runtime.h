@@ -1,0 +1,39 @@
+// kpp_runtime.h -- host-side internals of libkpp shared between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kpp.h"
+
+namespace kpp {
+
+// Thread-local last-error message (kpp_last_error).
+void set_error(const char *fmt, ...);
+void clear_error();
+
+// Memoised factors of one matrix (Sec. 4 / Sec. 5.2), device memory owned by this struct.
+struct FactorSet {
+    int64_t nb = 0, rows = 0;
+    int s = 0;
+    int mode = 0;        // 0: K++ block Gram, 1: CD++ principal block
+    int dtype = 0;       // storage dtype of the matrix the factors came from
+    double lambda = 0.0;
+    int64_t bad_block = -1;
+    double *L = nullptr;      // nb x s x s, FP64 lower Cholesky factors (block j: len x len, ld len)
+    double *Ginv = nullptr;   // nb x s x s, FP64 (G_j)^{-1}
+    float *Ginv32 = nullptr;  // nb x s x s, FP32 copy (FP32/BF16 storage only)
+    void release();
+};
+
+kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, FactorSet &F, cudaStream_t st);
+
+// Tensor-core block Gram for FP32/BF16 storage (kpp_gram_tc.cu).  Writes G (nb x s x s, FP64,
+// block j packed with leading dimension len) and returns true, or returns false when the shape is
+// not supported by the tensor-core kernel (the caller then uses the CUDA-core kernel).
+bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st);
+
+// Number of SMs of the current device (cached).
+int sm_count();
+
+}  // namespace kpp

@@ -1,0 +1,68 @@
+// kpp_solve.h -- launch descriptors of the persistent solve kernel (host and device view).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kpp.h"
+
+namespace kpp {
+
+// Per right-hand-side column state, kept in device memory between launches (resume, refinement).
+struct SolveScalars {
+    double E0, E1, rhat, rho, bn2, res_est;
+    long long ci;   // checkpoints completed
+    long long t;    // next iteration index (written back by the kernel)
+    int active;     // 1 while the column iterates
+    int status;     // kpp_status of the column
+};
+
+// One system of a launch.
+struct SysArgs {
+    const void *A;       // rows x cols, storage type
+    int64_t lda;
+    const void *b;       // rows x k, compute type (TC)
+    void *x;             // cols x k, TC
+    void *m;             // cols x k, TC
+    void *Rx, *Rm;       // CD++: n x k, TC (maintained residual and A m)
+    const void *Ginv;    // nb x s x s, TC
+    void *part;          // G x s x KP, TC (K++ partial residuals)
+    void *rbuf;          // s x KP, TC
+    void *ybuf;          // s x KP, TC
+    double *rpart;       // G x KP
+    SolveScalars *sc;    // k
+    unsigned *bar;       // group barrier counter
+    int *err;            // group error word
+    uint32_t sys_id;
+    int64_t t0;
+};
+
+// Shared by every system of a launch.
+struct Common {
+    int64_t rows, cols;
+    int s, nb, k;
+    int64_t CW;          // columns per CTA (multiple of the 32-byte sector)
+    int G;               // CTAs per system
+    double eta, tol;
+    int adaptive, confirm;
+    int reduce_redundant;  // K++: every CTA reduces the partial residuals itself (small G * s * k)
+    int init_residual;     // CD++: compute R_x = A x0 - b at start
+    int64_t max_iters;
+    uint64_t seed;
+    uint64_t timeout_ns;
+};
+
+size_t solve_smem_bytes(int s, int KP, int64_t CW, size_t tc_size);
+int pick_kp(int k);
+cudaError_t launch_solve(int dtype, bool fp64_compute, bool cd, const SysArgs *d_sys, int nsys, const Common &cm,
+                         int KP, cudaStream_t st);
+int residual_grid();
+cudaError_t launch_sample_blocks(uint64_t seed, uint32_t sys, int64_t t0, int64_t count, int32_t nb, int32_t *out,
+                                 cudaStream_t st);
+cudaError_t launch_residual(const kpp_matrix &A, int k, const double *b, const double *x, float *r32, double *part,
+                            cudaStream_t st);
+cudaError_t launch_axpy(int64_t n, const float *d, double *x, cudaStream_t st);
+cudaError_t launch_f64_to_f32(int64_t n, const double *a, float *o, cudaStream_t st);
+cudaError_t launch_negate_copy(size_t n, const void *src, void *dst, bool f64, cudaStream_t st);
+
+}  // namespace kpp

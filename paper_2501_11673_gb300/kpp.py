@@ -1,0 +1,295 @@
+"""Python binding of libkpp (include/kpp.h): argument marshalling through ctypes, nothing else.
+
+Every step of the solver runs in the CUDA library.  There is no CPU fallback: if ``libkpp.so`` is
+missing or cannot be loaded, every call raises ``RuntimeError``.  PyTorch tensors provide device
+memory and streams; their data pointers are passed straight through the C ABI.
+
+Paper: Derezinski, Needell, Rebrova, Yang, "Randomized Kaczmarz Methods with Beyond-Krylov
+Convergence" (arXiv 2501.11673).  ``kpp_solve`` is Kaczmarz++ (Alg. 1 / Alg. 5 with exact memoised
+projections); ``cdpp_solve`` is CD++ (Eq. 5.1, Alg. 3); ``kpp_factor_blocks`` memoises the block
+factors (Sec. 4, Sec. 5.2).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libkpp.so")
+
+KPP_F64, KPP_F32, KPP_BF16 = 0, 1, 2
+STATUS = {0: "KPP_OK", 1: "KPP_ERR_ARG", 2: "KPP_ERR_CUDA", 3: "KPP_ERR_OOM", 4: "KPP_ERR_NOT_SPD",
+          5: "KPP_ERR_NUMERIC", 6: "KPP_ERR_NO_CONVERGENCE", 7: "KPP_ERR_TIMEOUT", 8: "KPP_ERR_BUDGET",
+          9: "KPP_ERR_UNSUPPORTED"}
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NUMERIC, ERR_NO_CONVERGENCE, ERR_TIMEOUT, ERR_BUDGET, \
+    ERR_UNSUPPORTED = range(10)
+
+# Every symbol include/kpp.h declares (checked by the CPU test suite against the built library).
+EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_partition", "kpp_partition_destroy",
+           "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block",
+           "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
+           "kpp_solve_batched", "kpp_sample_blocks", "kpp_build_info"]
+
+
+class KppError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("ld", ctypes.c_int64)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("sys_id", ctypes.c_uint32), ("adaptive_rho", ctypes.c_int32),
+                ("rho0", ctypes.c_double), ("eta", ctypes.c_double), ("grid", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double), ("reserved1", ctypes.c_int64 * 4)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("outer", ctypes.c_int64), ("rel_res_true", ctypes.c_double),
+                ("rel_res_est", ctypes.c_double), ("rho_final", ctypes.c_double), ("status", ctypes.c_int32),
+                ("bad_block", ctypes.c_int32), ("device_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libkpp.so (built by ``paper_2501_11673_gb300.build``).  Raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libkpp.so not found at {p}: build it with paper_2501_11673_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.kpp_params_default.restype = Params
+        lib.kpp_status_string.argtypes = [ctypes.c_int]
+        lib.kpp_status_string.restype = ctypes.c_char_p
+        lib.kpp_last_error.restype = ctypes.c_char_p
+        lib.kpp_build_info.restype = ctypes.c_char_p
+        lib.kpp_partition.argtypes = [i64, i32, ctypes.POINTER(vp)]
+        lib.kpp_partition_destroy.argtypes = [vp]
+        lib.kpp_partition_blocks.argtypes = [vp]
+        lib.kpp_partition_blocks.restype = i64
+        lib.kpp_factor_blocks.argtypes = [ctypes.POINTER(Matrix), vp, dbl, i32, ctypes.POINTER(vp), vp]
+        lib.kpp_factors_destroy.argtypes = [vp]
+        lib.kpp_factors_bad_block.argtypes = [vp]
+        lib.kpp_factors_bad_block.restype = i64
+        lib.kpp_factors_get_block.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
+        for name in ("kpp_solve", "cdpp_solve"):
+            f = getattr(lib, name)
+            f.argtypes = [ctypes.POINTER(Matrix), vp, vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
+        lib.kpp_solve_host.argtypes = [ctypes.POINTER(Matrix), vp, vp, i32, i32, ctypes.POINTER(Params),
+                                       ctypes.POINTER(Report), vp]
+        lib.kpp_rel_residual.argtypes = [ctypes.POINTER(Matrix), vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+        lib.kpp_solve_batched.argtypes = [i32, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
+                                          vp, ctypes.POINTER(vp), ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
+        lib.kpp_sample_blocks.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i64, i64, i32, vp, vp]
+        for name in ("kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
+                     "kpp_solve_host", "kpp_rel_residual", "kpp_solve_batched"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().kpp_last_error().decode()
+
+
+def _check(rc: int, allow=()):
+    if rc != OK and rc not in allow:
+        raise KppError(rc, last_error())
+    return rc
+
+
+# ---------------------------------------------------------------------------------------------
+# torch <-> C structs
+# ---------------------------------------------------------------------------------------------
+
+def _dtype_code(t) -> int:
+    import torch
+    m = {torch.float64: KPP_F64, torch.float32: KPP_F32, torch.bfloat16: KPP_BF16}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported matrix dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def matrix(A) -> Matrix:
+    """Describe a 2-D torch tensor (row-major, unit column stride) as a kpp_matrix."""
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a 2-D row-major tensor with unit column stride")
+    return Matrix(ctypes.c_void_p(A.data_ptr()), _dtype_code(A), 0, A.shape[0], A.shape[1], A.stride(0))
+
+
+def host_matrix(A) -> Matrix:
+    """Describe a C-contiguous numpy array (float64 / float32, or uint16 holding bf16 bits)."""
+    import numpy as np
+    codes = {np.dtype(np.float64): KPP_F64, np.dtype(np.float32): KPP_F32, np.dtype(np.uint16): KPP_BF16}
+    if A.ndim != 2 or not A.flags.c_contiguous or A.dtype not in codes:
+        raise ValueError("host matrix must be a C-contiguous 2-D float64/float32/uint16(bf16) array")
+    return Matrix(ctypes.c_void_p(A.ctypes.data), codes[A.dtype], 0, A.shape[0], A.shape[1], A.shape[1])
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def params(**kw) -> Params:
+    """kpp_params_default() with fields overridden (use ``lam`` for lambda)."""
+    p = load().kpp_params_default()
+    for k, v in kw.items():
+        if k in ("lam", "lambda_"):
+            p.lambda_ = float(v)
+        elif k == "eta" and v is None:
+            p.eta = math.nan
+        else:
+            if not hasattr(p, k):
+                raise AttributeError(k)
+            setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------------------------------------
+# Handles
+# ---------------------------------------------------------------------------------------------
+
+class Partition:
+    """Fixed contiguous row partition into blocks of s rows (kpp_partition)."""
+
+    def __init__(self, rows: int, s: int):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.kpp_partition(rows, s, ctypes.byref(h)))
+        self.handle, self.rows, self.s = h, rows, s
+
+    @property
+    def nb(self) -> int:
+        return int(self._lib.kpp_partition_blocks(self.handle))
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self._lib.kpp_partition_destroy(self.handle)
+            self.handle = None
+
+
+class Factors:
+    """Memoised per-block factors (kpp_factor_blocks).  mode 0: K++ Gram, 1: CD++ principal block."""
+
+    def __init__(self, A, P: Partition, lam: float, mode: int, stream=None, allow_not_spd: bool = False):
+        self._lib = load()
+        self._A = A  # keep the matrix alive while the factors are
+        h = ctypes.c_void_p()
+        m = matrix(A)
+        rc = self._lib.kpp_factor_blocks(ctypes.byref(m), P.handle, float(lam), int(mode), ctypes.byref(h),
+                                         _stream_ptr(stream))
+        self.handle = h if h.value else None
+        self.status = rc
+        _check(rc, allow=(ERR_NOT_SPD,) if allow_not_spd else ())
+        self.lam, self.mode, self.P = lam, mode, P
+
+    @property
+    def bad_block(self) -> int:
+        return int(self._lib.kpp_factors_bad_block(self.handle))
+
+    def block(self, j: int):
+        """FP64 lower Cholesky factor of block j as a numpy array."""
+        import numpy as np
+        ln = min(self.P.s, self.P.rows - j * self.P.s)
+        out = np.zeros((ln, ln))
+        _check(self._lib.kpp_factors_get_block(self.handle, j, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self._lib.kpp_factors_destroy(self.handle)
+            self.handle = None
+
+
+def _report_or_raise(rc: int, rep: Report, allow_no_conv: bool) -> Report:
+    allow = (ERR_NO_CONVERGENCE,) if allow_no_conv else ()
+    _check(rc, allow=allow)
+    return rep
+
+
+def kpp_solve(A, b, x, P: Partition, F: Factors, prm: Params, stream=None, allow_no_conv: bool = False) -> Report:
+    """Kaczmarz++ on device tensors; x (float64, cols) holds x0 and receives the result."""
+    rep = Report()
+    m = matrix(A)
+    rc = load().kpp_solve(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), P.handle,
+                          F.handle, ctypes.byref(prm), ctypes.byref(rep), _stream_ptr(stream))
+    return _report_or_raise(rc, rep, allow_no_conv)
+
+
+def cdpp_solve(A, b, x, P: Partition, F: Factors, prm: Params, stream=None, allow_no_conv: bool = False) -> Report:
+    """CD++ on device tensors (A symmetric n x n); x holds x0 and receives the result."""
+    rep = Report()
+    m = matrix(A)
+    rc = load().cdpp_solve(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), P.handle,
+                           F.handle, ctypes.byref(prm), ctypes.byref(rep), _stream_ptr(stream))
+    return _report_or_raise(rc, rep, allow_no_conv)
+
+
+def kpp_solve_batched(As: list, Bs: list, Xs: list, P: Partition, Fs: list, prm: Params, stream=None,
+                      allow_no_conv: bool = False) -> list:
+    """Batched K++: systems i with A_i (rows x cols), B_i (rows x k) and X_i (cols x k), FP64 panels."""
+    n = len(As)
+    k = Bs[0].shape[1] if Bs[0].dim() == 2 else 1
+    mats = (Matrix * n)(*[matrix(a) for a in As])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in Bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Xs])
+    fp = (ctypes.c_void_p * n)(*[f.handle.value for f in Fs])
+    reps = (Report * (n * k))()
+    rc = load().kpp_solve_batched(n, mats, bp, xp, k, P.handle, fp, ctypes.byref(prm), reps, _stream_ptr(stream))
+    _check(rc, allow=(ERR_NO_CONVERGENCE,) if allow_no_conv else ())
+    return list(reps)
+
+
+def solve_host(A_np, b_np, x_np, s: int, mode: int, prm: Params, stream=None) -> Report:
+    """End-to-end call on host (numpy) buffers: copies in, factors, solves, copies x back."""
+    import numpy as np
+    m = host_matrix(A_np)
+    assert b_np.dtype == np.float64 and x_np.dtype == np.float64 and x_np.flags.c_contiguous
+    rep = Report()
+    rc = load().kpp_solve_host(ctypes.byref(m), ctypes.c_void_p(b_np.ctypes.data), ctypes.c_void_p(x_np.ctypes.data),
+                               int(s), int(mode), ctypes.byref(prm), ctypes.byref(rep), _stream_ptr(stream))
+    _check(rc, allow=(ERR_NO_CONVERGENCE,))
+    return rep
+
+
+def rel_residual(A, b, x, stream=None) -> float:
+    """|A x - b| / |b| with FP64 accumulation, on the device."""
+    out = ctypes.c_double()
+    m = matrix(A)
+    _check(load().kpp_rel_residual(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                   ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
+
+
+def sample_blocks(seed: int, sys_id: int, t0: int, count: int, nb: int, stream=None):
+    """Device-drawn block indices for steps t0..t0+count-1 (int32 CUDA tensor)."""
+    import torch
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    _check(load().kpp_sample_blocks(seed, sys_id, t0, count, nb, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def build_info() -> str:
+    return load().kpp_build_info().decode()

@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (FP64 path): relative iterate error <= 1e-10 at equal iteration counts, identical block
+sequences (bitwise), identical stop iterations; final |Ax-b|/|b| <= 1e-8.  The FP32/BF16 forms are
+compared on what is unique: the converged solution, within the bound |x - x_o| <= kappa * (res + res_o)
+|x_o| implied by both residuals.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_11673_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_2501_11673_gb300 import build as kbuild
+    from paper_2501_11673_gb300 import kpp
+    kbuild.build()
+    kpp.load()
+    return kpp
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_device_block_draws_match_oracle(K):
+    for nb, sys_id, seed in [(100, 0, 0), (64, 3, 123456789), (7, 11, 2**63 + 5), (1, 0, 1)]:
+        d = K.sample_blocks(seed, sys_id, 0, 4096, nb).cpu().numpy()
+        o = np.array([oracle.sample_block(seed, t, sys_id, nb) for t in range(4096)])
+        np.testing.assert_array_equal(d, o)
+    d = K.sample_blocks(9, 2, (1 << 33) + 17, 64, 13).cpu().numpy()
+    o = np.array([oracle.sample_block(9, (1 << 33) + 17 + t, 2, 13) for t in range(64)])
+    np.testing.assert_array_equal(d, o)
+
+
+@pytest.mark.parametrize("m,n,s", [(103, 37, 10), (64, 64, 64), (50, 200, 7)])
+def test_kpp_factors_match_oracle(K, m, n, s):
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    lam = 0.05
+    P = K.Partition(m, s)
+    F = K.Factors(dev(A), P, lam, 0)
+    L = oracle.kpp_factor(A, s, lam)
+    for j in range(P.nb):
+        Lo = oracle.factor_block(L, j, m, s)
+        np.testing.assert_allclose(F.block(j), Lo, rtol=1e-11, atol=1e-11 * np.abs(Lo).max())
+
+
+def test_cdpp_factors_and_not_spd(K):
+    A, b, _ = W.spd(96, 4, 10.0, 100.0, 1.0, 2.0, seed_A=5, seed_b=6)
+    P = K.Partition(96, 20)
+    F = K.Factors(dev(A), P, 1e-4, 1)
+    L = oracle.cdpp_factor(A, 20, 1e-4)
+    for j in range(P.nb):
+        Lo = oracle.factor_block(L, j, 96, 20)
+        np.testing.assert_allclose(F.block(j), Lo, rtol=1e-11, atol=1e-12 * np.abs(Lo).max())
+    # a block with two equal rows and lambda = 0 is singular: the factor reports it
+    Bm = np.random.default_rng(1).standard_normal((40, 30))
+    Bm[25] = Bm[21]
+    Fb = K.Factors(dev(Bm), K.Partition(40, 10), 0.0, 0, allow_not_spd=True)
+    assert Fb.status == K.ERR_NOT_SPD and Fb.bad_block == 2
+
+
+def _kpp_pair(K, A, b, s, lam, T=None, tol=0.0, seed=3, grid=0, adaptive=True, x0=None, eta=None, cd=False,
+              dtype=torch.float64):
+    m, n = A.shape
+    P = K.Partition(m, s)
+    Ad = dev(A, dtype)
+    F = K.Factors(Ad, P, lam, 1 if cd else 0)
+    x = dev(np.zeros(n) if x0 is None else x0)
+    prm = K.params(lam=lam, tol=tol, max_iters=T if T is not None else 10**6, seed=seed, grid=grid,
+                   adaptive_rho=int(adaptive), eta=eta)
+    solve = K.cdpp_solve if cd else K.kpp_solve
+    rep = solve(Ad, dev(b), x, P, F, prm, allow_no_conv=True)
+    Lo = oracle.cdpp_factor(A, s, lam) if cd else oracle.kpp_factor(A, s, lam)
+    res = oracle.run(A, b, Lo, s, cd=cd, lam=lam, tol=tol, max_iters=T if T is not None else 10**6, seed=seed,
+                     adaptive=adaptive, eta=eta, x0=x0)
+    return x.cpu().numpy(), rep, res
+
+
+@pytest.mark.parametrize("grid", [1, 3, 8, 40])
+def test_kpp_fp64_lockstep_ragged(K, grid):
+    rng = np.random.default_rng(7)
+    m, n, s = 103, 37, 10  # 11 blocks, the last of 3 rows
+    A = rng.standard_normal((m, n)) @ np.diag(np.geomspace(1, 30, n))
+    b = A @ rng.standard_normal(n)
+    for T in (1, 5, 2 * 11 * 3, 2 * 11 * 7 + 4):
+        x, rep, res = _kpp_pair(K, A, b, s, 1e-2, T=T, grid=grid)
+        assert rep.iters == T == res.iters
+        assert rel(x, res.x) <= 1e-10, (T, rel(x, res.x))
+
+
+def test_kpp_fp64_lockstep_fixed_rho_and_no_momentum(K):
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((90, 60))
+    b = rng.standard_normal(90)
+    x, rep, res = _kpp_pair(K, A, b, 9, 0.3, T=150, adaptive=False, eta=0.0)
+    assert rel(x, res.x) <= 1e-10
+    x, rep, res = _kpp_pair(K, A, b, 9, 0.3, T=150, adaptive=False, eta=0.05)
+    assert rel(x, res.x) <= 1e-10
+
+
+def test_kpp_fp64_single_row_blocks_and_single_block(K):
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((30, 20))
+    b = A @ rng.standard_normal(20)
+    x, rep, res = _kpp_pair(K, A, b, 1, 0.0, T=200, eta=0.0, adaptive=False)
+    assert rel(x, res.x) <= 1e-10
+    A2 = rng.standard_normal((12, 40))
+    b2 = rng.standard_normal(12)
+    x, rep, res = _kpp_pair(K, A2, b2, 12, 0.0, T=1, eta=0.0, adaptive=False)
+    np.testing.assert_allclose(x, np.linalg.pinv(A2) @ b2, rtol=1e-9, atol=1e-11)
+
+
+def test_kpp_fp64_2000x200_to_tolerance(K):
+    sy = W.kpp_fp64_2000x200()
+    x, rep, res = _kpp_pair(K, sy.A, sy.b, sy.s, sy.lam, tol=sy.tol, seed=0)
+    assert rep.status == K.OK and res.status == oracle.OK
+    assert rep.iters == res.iters
+    assert rep.rel_res_true <= 1e-8
+    assert rel(x, res.x) <= 1e-10
+
+
+@pytest.mark.parametrize("grid", [1, 5, 16])
+def test_cdpp_fp64_lockstep_ragged(K, grid):
+    A, b, _ = W.spd(200, 6, 1e2, 1e3, 1.0, 5.0, seed_A=10, seed_b=11)
+    for T in (1, 7, 2 * 13 * 4, 2 * 13 * 9 + 5):
+        x, rep, res = _kpp_pair(K, A, b, 16, 1e-4, T=T, grid=grid, cd=True)
+        assert rep.iters == T == res.iters
+        assert rel(x, res.x) <= 1e-10, (T, rel(x, res.x))
+
+
+def test_cdpp_fp64_nonzero_start(K):
+    A, b, _ = W.spd(130, 3, 1e2, 1e3, 1.0, 5.0, seed_A=12, seed_b=13)
+    x0 = np.random.default_rng(3).standard_normal(130)
+    x, rep, res = _kpp_pair(K, A, b, 13, 1e-4, T=300, cd=True, x0=x0)
+    assert rel(x, res.x) <= 1e-10
+
+
+@pytest.mark.slow
+def test_cdpp_fp64_spd4096_to_tolerance(K):
+    sy = W.cdpp_fp64_spd()
+    x, rep, res = _kpp_pair(K, sy.A, sy.b, sy.s, sy.lam, tol=sy.tol, seed=1, cd=True)
+    assert rep.status == K.OK and res.status == oracle.OK
+    assert rep.iters == res.iters
+    assert rep.rel_res_true <= 1e-8
+    assert rel(x, res.x) <= 1e-10
+
+
+def test_status_no_convergence_keeps_last_iterate(K):
+    sy = W.kpp_fp64_2000x200()
+    x, rep, res = _kpp_pair(K, sy.A, sy.b, sy.s, sy.lam, T=300, tol=1e-14, seed=0)
+    assert rep.status == K.ERR_NO_CONVERGENCE and res.status == oracle.NO_CONVERGENCE
+    assert rel(x, res.x) <= 1e-10
+
+
+def test_argument_errors(K):
+    A = dev(np.eye(8))
+    P = K.Partition(8, 4)
+    F = K.Factors(A, P, 0.1, 0)
+    x = dev(np.zeros(8))
+    with pytest.raises(K.KppError) as e:
+        K.kpp_solve(A, dev(np.ones(8)), x, P, F, K.params(lam=0.2))  # lambda differs from the factors'
+    assert e.value.status == K.ERR_ARG
+    with pytest.raises(K.KppError):
+        K.cdpp_solve(A, dev(np.ones(8)), x, P, F, K.params(lam=0.1))  # K++ factors used for CD++
+    with pytest.raises(K.KppError):
+        K.Factors(dev(np.ones((8, 5))), P, 0.1, 1)  # CD++ needs a square matrix
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_mixed_precision_refinement_reaches_1e8(K, dtype):
+    sy = W.kpp_mixed_lowrank(m=16384, n=512, s=128, n_out=16)
+    A = W.round_to_storage(sy.A, dtype)
+    b = A @ sy.x_star
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    m, n = A.shape
+    P = K.Partition(m, sy.s)
+    Ad = dev(A, tdt)
+    assert np.array_equal(Ad.double().cpu().numpy(), A)
+    F = K.Factors(Ad, P, sy.lam, 0)
+    x = dev(np.zeros(n))
+    rep = K.kpp_solve(Ad, dev(b), x, P, F, K.params(lam=sy.lam, tol=1e-8, refine=1, inner_tol=1e-3, seed=0))
+    assert rep.status == K.OK and rep.rel_res_true <= 1e-8 and rep.outer >= 1
+    xo = np.linalg.lstsq(A, b, rcond=None)[0]
+    kappa = sy.spectrum.max() / sy.spectrum.min() * 2.0
+    assert rel(x.cpu().numpy(), xo) <= kappa * 2e-8
+
+
+def test_mixed_cdpp_refinement(K):
+    A, b, _ = W.spd(512, 8, 1e2, 1e3, 1.0, 10.0, seed_A=20, seed_b=21)
+    A32 = W.round_to_storage(A, "f32")
+    P = K.Partition(512, 64)
+    Ad = dev(A32, torch.float32)
+    F = K.Factors(Ad, P, 1e-4, 1)
+    x = dev(np.zeros(512))
+    rep = K.cdpp_solve(Ad, dev(b), x, P, F, K.params(lam=1e-4, tol=1e-8, refine=1, inner_tol=1e-3, seed=2))
+    assert rep.status == K.OK and rep.rel_res_true <= 1e-8
+    xo = np.linalg.solve(A32, b)
+    assert rel(x.cpu().numpy(), xo) <= 1e3 * 2e-8
+
+
+def test_batched_multi_rhs_matches_single_rhs_oracle(K):
+    nsys, k, m, n, s, lam = 3, 3, 60, 25, 7, 0.05
+    As, Bs = [], []
+    for i in range(nsys):
+        rng = np.random.default_rng(100 + i)
+        As.append(rng.standard_normal((m, n)))
+        Bs.append(rng.standard_normal((m, k)))
+    P = K.Partition(m, s)
+    Ad = [dev(a) for a in As]
+    Fs = [K.Factors(a, P, lam, 0) for a in Ad]
+    Xd = [dev(np.zeros((n, k))) for _ in range(nsys)]
+    T = 2 * 9 * 5 + 3
+    reps = K.kpp_solve_batched(Ad, [dev(bb) for bb in Bs], Xd, P, Fs,
+                               K.params(lam=lam, tol=0.0, max_iters=T, seed=4, sys_id=10), allow_no_conv=True)
+    assert len(reps) == nsys * k
+    for i in range(nsys):
+        L = oracle.kpp_factor(As[i], s, lam)
+        for c in range(k):
+            res = oracle.run(As[i], Bs[i][:, c], L, s, lam=lam, tol=0.0, max_iters=T, seed=4, sys=10 + i)
+            assert rel(Xd[i][:, c].cpu().numpy(), res.x) <= 1e-10
+
+
+def test_host_entry_point_matches_device_path(K):
+    sy = W.kpp_fp64_2000x200()
+    x_host = np.zeros(sy.A.shape[1])
+    rep = K.solve_host(np.ascontiguousarray(sy.A), sy.b.copy(), x_host, sy.s, 0,
+                       K.params(lam=sy.lam, tol=sy.tol, seed=0))
+    assert rep.status == K.OK and rep.rel_res_true <= 1e-8
+    x, rep2, res = _kpp_pair(K, sy.A, sy.b, sy.s, sy.lam, tol=sy.tol, seed=0)
+    np.testing.assert_array_equal(x_host, x)
