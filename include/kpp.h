@@ -188,6 +188,25 @@ kpp_status kpp_solve_batched(int32_t nsys, const kpp_matrix *A, const double *co
 kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t count, int32_t nb, int32_t *out,
                              void *stream);
 
+/* CD++ FP64 solve that allocates no device memory.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc, such as a process whose GPU memory is owned by
+ * another allocator (a serving runtime or framework pool that reserved the device) or a request
+ * path that must not block on the allocator or fail half way with an out-of-memory error.
+ * It runs the same kernel as cdpp_solve, with the same arguments and results.  The scratch
+ * (momentum, maintained residuals, projection buffer, scalars, barrier words, partial sums) lives
+ * in one fixed device array of about 400 KiB inside the library.  Every GPU that loads the library
+ * holds that array until the process exits.
+ * Limits: A FP64, n <= 16384, s <= 256, one right-hand side.  Larger sizes return KPP_ERR_ARG with
+ * a message; nothing is allocated.  The caller passes A, b, x and factors made by
+ * kpp_factor_blocks(mode 1).  No timing is taken (report.device_ms is NaN).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls share the one array
+ * and it keeps the last call's contents (each call clears what must start at zero), so calls whose
+ * work overlaps on the GPU -- on different streams, or from different threads -- race and must not
+ * be issued.  Synchronises `stream`. */
+kpp_status cdpp_solve_noalloc(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
+                              const kpp_params *p, kpp_report *rep, void *stream);
+
 /* Library build information: "sm_103a; <compiler>; <date>". */
 const char *kpp_build_info(void);
 

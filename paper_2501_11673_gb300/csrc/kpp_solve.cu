@@ -566,6 +566,22 @@ cudaError_t launch_residual(const kpp_matrix &A, int k, const double *b, const d
     return cudaGetLastError();
 }
 
+cudaError_t launch_residual_grid(const kpp_matrix &A, int k, const double *b, const double *x, float *r32,
+                                 double *part, int grid, cudaStream_t st) {
+    switch (A.dtype) {
+        case KPP_F64:
+            residual_kernel<double><<<grid, 256, 0, st>>>((const double *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part);
+            break;
+        case KPP_F32:
+            residual_kernel<float><<<grid, 256, 0, st>>>((const float *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part);
+            break;
+        default:
+            residual_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)A.data, A.ld, A.rows, A.cols,
+                                                                 k, b, x, r32, part);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_axpy(int64_t n, const float *d, double *x, cudaStream_t st) {
     axpy_f32_to_f64_kernel<<<2 * sm_count(), 256, 0, st>>>(n, d, x);
     return cudaGetLastError();

@@ -61,6 +61,8 @@ cudaError_t launch_sample_blocks(uint64_t seed, uint32_t sys, int64_t t0, int64_
                                  cudaStream_t st);
 cudaError_t launch_residual(const kpp_matrix &A, int k, const double *b, const double *x, float *r32, double *part,
                             cudaStream_t st);
+cudaError_t launch_residual_grid(const kpp_matrix &A, int k, const double *b, const double *x, float *r32,
+                                 double *part, int grid, cudaStream_t st);
 cudaError_t launch_axpy(int64_t n, const float *d, double *x, cudaStream_t st);
 cudaError_t launch_f64_to_f32(int64_t n, const double *a, float *o, cudaStream_t st);
 cudaError_t launch_negate_copy(size_t n, const void *src, void *dst, bool f64, cudaStream_t st);

@@ -31,7 +31,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NUMERIC, ERR_NO_CONVERGENCE, ER
 EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_partition", "kpp_partition_destroy",
            "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block",
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
-           "kpp_solve_batched", "kpp_sample_blocks", "kpp_build_info"]
+           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_build_info"]
 
 
 class KppError(RuntimeError):
@@ -91,7 +91,7 @@ def load(path: str | None = None):
         lib.kpp_factors_bad_block.argtypes = [vp]
         lib.kpp_factors_bad_block.restype = i64
         lib.kpp_factors_get_block.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
-        for name in ("kpp_solve", "cdpp_solve"):
+        for name in ("kpp_solve", "cdpp_solve", "cdpp_solve_noalloc"):
             f = getattr(lib, name)
             f.argtypes = [ctypes.POINTER(Matrix), vp, vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
         lib.kpp_solve_host.argtypes = [ctypes.POINTER(Matrix), vp, vp, i32, i32, ctypes.POINTER(Params),
@@ -100,7 +100,7 @@ def load(path: str | None = None):
         lib.kpp_solve_batched.argtypes = [i32, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
                                           vp, ctypes.POINTER(vp), ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
         lib.kpp_sample_blocks.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i64, i64, i32, vp, vp]
-        for name in ("kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
+        for name in ("cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
                      "kpp_solve_host", "kpp_rel_residual", "kpp_solve_batched"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -244,6 +244,18 @@ def cdpp_solve(A, b, x, P: Partition, F: Factors, prm: Params, stream=None, allo
     m = matrix(A)
     rc = load().cdpp_solve(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), P.handle,
                            F.handle, ctypes.byref(prm), ctypes.byref(rep), _stream_ptr(stream))
+    return _report_or_raise(rc, rep, allow_no_conv)
+
+
+def cdpp_solve_noalloc(A, b, x, P: Partition, F: Factors, prm: Params, stream=None,
+                       allow_no_conv: bool = False) -> Report:
+    """CD++ FP64 through the entry point that allocates no device memory (fixed internal scratch;
+    n <= 16384, s <= 256).  For callers that cannot allocate device memory; same results as
+    cdpp_solve.  Calls must not overlap on the GPU."""
+    rep = Report()
+    m = matrix(A)
+    rc = load().cdpp_solve_noalloc(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                   P.handle, F.handle, ctypes.byref(prm), ctypes.byref(rep), _stream_ptr(stream))
     return _report_or_raise(rc, rep, allow_no_conv)
 
 
