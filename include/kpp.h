@@ -207,6 +207,13 @@ kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t
 kpp_status cdpp_solve_noalloc(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
                               const kpp_params *p, kpp_report *rep, void *stream);
 
+/* Select the solve kernel for later calls in this process: 2 (default) uses the small-block kernel
+ * (one barrier per step, TMA-prefetched A tiles and memoised inverses) wherever the shape allows it
+ * (s even and <= 256, row stride a multiple of 16 bytes, per-CTA chunk <= 256 columns); 1 always
+ * uses the general kernel.  Both compute the same iteration.  Not thread-safe with concurrent solves.
+ * Errors: KPP_ERR_ARG for another value. */
+kpp_status kpp_set_kernel_variant(int32_t variant);
+
 /* Library build information: "sm_103a; <compiler>; <date>". */
 const char *kpp_build_info(void);
 

@@ -138,20 +138,26 @@ static int auto_grid(int64_t cols, int nsys) {
 }
 
 // Run the persistent kernel over nsys systems that share shape, dtype, s and k.
+static bool g_use_v2 = true;
+
 static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd, int k, int s, double eta,
                                  double tol, int adaptive, int confirm, int64_t max_iters, uint64_t seed, int grid,
                                  bool init_residual, int64_t t0, cudaStream_t st, float *ms_out, int *err_out) {
+    const bool use_v2 = g_use_v2;
     kpp_status rc = KPP_OK;
     const int nsys = (int)sys.size();
     const kpp_matrix &A0 = *sys[0].A;
     const bool f64 = dtype == KPP_F64;
     const size_t tcs = f64 ? 8 : 4;
     const int KP = pick_kp(k);
-    const int G = grid > 0 ? grid : auto_grid(A0.cols, nsys);
+    int G = grid > 0 ? grid : auto_grid(A0.cols, nsys);
     const int64_t sector = 32 / (int64_t)dtype_size(dtype);
     int64_t CW = (A0.cols + G - 1) / G;
     CW = (CW + sector - 1) / sector * sector;
+    G = (int)((A0.cols + CW - 1) / CW);  // no CTA without columns
     const int nb = (int)((A0.rows + s - 1) / s);
+    bool v2 = use_v2;
+    for (int i = 0; v2 && i < nsys; ++i) v2 = solve2_eligible(*sys[i].A, s, CW, KP, f64);
     Common cm{};
     cm.rows = A0.rows;
     cm.cols = A0.cols;
@@ -171,13 +177,15 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     cm.timeout_ns = 2000000000ull;
 
     const size_t smem = solve_smem_bytes(s, KP, CW, tcs);
-    if (smem > 220 * 1024) {
+    if (!v2 && smem > 220 * 1024) {
         set_error("shared memory %zu B exceeds the per-CTA limit (s=%d, k=%d, chunk=%lld)", smem, s, k, (long long)CW);
         return KPP_ERR_UNSUPPORTED;
     }
     Scratch scr(st);
     std::vector<SysArgs> args(nsys);
     SysArgs *d_args = nullptr;
+    void *d_sys2 = nullptr;
+    std::vector<unsigned char> h2;
     unsigned *bars = nullptr;
     int *errs = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -197,16 +205,18 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
         CUDA_OR(scr.alloc(&a.m, vec_n * tcs), KPP_ERR_CUDA);
         CUDA_OR(cudaMemsetAsync(a.m, 0, vec_n * tcs, st), KPP_ERR_CUDA);
         if (cd) {
-            CUDA_OR(scr.alloc(&a.Rx, vec_r * tcs), KPP_ERR_CUDA);
+            // v2 keeps two published copies of R_x (steps of even / odd index)
+            CUDA_OR(scr.alloc(&a.Rx, (v2 ? 2 : 1) * vec_r * tcs), KPP_ERR_CUDA);
             CUDA_OR(scr.alloc(&a.Rm, vec_r * tcs), KPP_ERR_CUDA);
             CUDA_OR(cudaMemsetAsync(a.Rm, 0, vec_r * tcs, st), KPP_ERR_CUDA);
             if (!init_residual) {  // x0 = 0: R_x = -b
-                CUDA_OR(launch_negate_copy(vec_r, a.b, a.Rx, f64, st), KPP_ERR_CUDA);
+                void *dst = (v2 && (t0 & 1)) ? (void *)((char *)a.Rx + vec_r * tcs) : a.Rx;
+                CUDA_OR(launch_negate_copy(vec_r, a.b, dst, f64, st), KPP_ERR_CUDA);
             }
         } else {
             a.Rx = a.Rm = nullptr;
         }
-        CUDA_OR(scr.alloc(&a.part, (size_t)G * s * KP * tcs), KPP_ERR_CUDA);
+        CUDA_OR(scr.alloc(&a.part, (v2 ? 2 : 1) * (size_t)G * s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc(&a.rbuf, (size_t)s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc(&a.ybuf, (size_t)s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc((void **)&a.rpart, (size_t)G * KP * sizeof(double)), KPP_ERR_CUDA);
@@ -218,13 +228,33 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
         a.sys_id = sys[i].sys_id;
         a.t0 = t0;
     }
-    CUDA_OR(scr.alloc((void **)&d_args, nsys * sizeof(SysArgs)), KPP_ERR_CUDA);
-    CUDA_OR(cudaMemcpyAsync(d_args, args.data(), nsys * sizeof(SysArgs), cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
+    if (v2) {
+        const size_t sb = sys2_bytes();
+        h2.assign(sb * nsys, 0);
+        for (int i = 0; i < nsys; ++i) {
+            alignas(128) unsigned char tm[128];
+            if (!make_tmap_2d(tm, sys[i].A->data, dtype, sys[i].A->cols, sys[i].A->rows, sys[i].A->ld, (uint32_t)CW,
+                              (uint32_t)s)) {
+                set_error("cuTensorMapEncodeTiled failed for system %d", i);
+                rc = KPP_ERR_CUDA;
+                goto cleanup;
+            }
+            sys2_fill(h2.data() + sb * i, args[i], tm);
+        }
+        CUDA_OR(scr.alloc(&d_sys2, sb * nsys), KPP_ERR_CUDA);
+        CUDA_OR(cudaMemcpyAsync(d_sys2, h2.data(), sb * nsys, cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
+        CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);  // h2 is pageable and local
+    } else {
+        CUDA_OR(scr.alloc((void **)&d_args, nsys * sizeof(SysArgs)), KPP_ERR_CUDA);
+        CUDA_OR(cudaMemcpyAsync(d_args, args.data(), nsys * sizeof(SysArgs), cudaMemcpyHostToDevice, st),
+                KPP_ERR_CUDA);
+    }
     CUDA_OR(cudaEventCreate(&e0), KPP_ERR_CUDA);
     CUDA_OR(cudaEventCreate(&e1), KPP_ERR_CUDA);
     CUDA_OR(cudaEventRecord(e0, st), KPP_ERR_CUDA);
     {
-        cudaError_t le = launch_solve(dtype, f64, cd, d_args, nsys, cm, KP, st);
+        cudaError_t le = v2 ? launch_solve2(dtype, cd, d_sys2, nsys, cm, KP, st)
+                            : launch_solve(dtype, f64, cd, d_args, nsys, cm, KP, st);
         if (le == cudaErrorCooperativeLaunchTooLarge) {
             set_error("%d systems x %d CTAs do not fit co-resident on this GPU", nsys, G);
             rc = KPP_ERR_UNSUPPORTED;
@@ -589,6 +619,16 @@ kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t
         set_error("sample kernel: %s", cudaGetErrorString(e));
         return KPP_ERR_CUDA;
     }
+    return KPP_OK;
+}
+
+kpp_status kpp_set_kernel_variant(int32_t variant) {
+    clear_error();
+    if (variant != 1 && variant != 2) {
+        set_error("kpp_set_kernel_variant: variant must be 1 or 2");
+        return KPP_ERR_ARG;
+    }
+    g_use_v2 = variant == 2;
     return KPP_OK;
 }
 

@@ -31,7 +31,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NUMERIC, ERR_NO_CONVERGENCE, ER
 EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_partition", "kpp_partition_destroy",
            "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block",
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
-           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_build_info"]
+           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_build_info"]
 
 
 class KppError(RuntimeError):
@@ -100,7 +100,8 @@ def load(path: str | None = None):
         lib.kpp_solve_batched.argtypes = [i32, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
                                           vp, ctypes.POINTER(vp), ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
         lib.kpp_sample_blocks.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i64, i64, i32, vp, vp]
-        for name in ("cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
+        lib.kpp_set_kernel_variant.argtypes = [i32]
+        for name in ("kpp_set_kernel_variant", "cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
                      "kpp_solve_host", "kpp_rel_residual", "kpp_solve_batched"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -301,6 +302,11 @@ def sample_blocks(seed: int, sys_id: int, t0: int, count: int, nb: int, stream=N
     out = torch.empty(count, dtype=torch.int32, device="cuda")
     _check(load().kpp_sample_blocks(seed, sys_id, t0, count, nb, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def set_kernel_variant(v: int) -> None:
+    """1: general kernel everywhere; 2 (default): small-block kernel where the shape allows it."""
+    _check(load().kpp_set_kernel_variant(int(v)))
 
 
 def build_info() -> str:

@@ -90,10 +90,18 @@ def _kpp_pair(K, A, b, s, lam, T=None, tol=0.0, seed=3, grid=0, adaptive=True, x
     return x.cpu().numpy(), rep, res
 
 
+@pytest.fixture(params=[1, 2], ids=["general", "smallblock"])
+def variant(request, K):
+    K.set_kernel_variant(request.param)
+    yield request.param
+    K.set_kernel_variant(2)
+
+
 @pytest.mark.parametrize("grid", [1, 3, 8, 40])
-def test_kpp_fp64_lockstep_ragged(K, grid):
+@pytest.mark.parametrize("shape", [(103, 37, 10), (104, 40, 10)])
+def test_kpp_fp64_lockstep_ragged(K, variant, grid, shape):
     rng = np.random.default_rng(7)
-    m, n, s = 103, 37, 10  # 11 blocks, the last of 3 rows
+    m, n, s = shape  # 11 blocks, the last of 3 (or 4) rows; 40 columns qualify for the small-block kernel
     A = rng.standard_normal((m, n)) @ np.diag(np.geomspace(1, 30, n))
     b = A @ rng.standard_normal(n)
     for T in (1, 5, 2 * 11 * 3, 2 * 11 * 7 + 4):
@@ -124,7 +132,7 @@ def test_kpp_fp64_single_row_blocks_and_single_block(K):
     np.testing.assert_allclose(x, np.linalg.pinv(A2) @ b2, rtol=1e-9, atol=1e-11)
 
 
-def test_kpp_fp64_2000x200_to_tolerance(K):
+def test_kpp_fp64_2000x200_to_tolerance(K, variant):
     sy = W.kpp_fp64_2000x200()
     x, rep, res = _kpp_pair(K, sy.A, sy.b, sy.s, sy.lam, tol=sy.tol, seed=0)
     assert rep.status == K.OK and res.status == oracle.OK
@@ -134,7 +142,7 @@ def test_kpp_fp64_2000x200_to_tolerance(K):
 
 
 @pytest.mark.parametrize("grid", [1, 5, 16])
-def test_cdpp_fp64_lockstep_ragged(K, grid):
+def test_cdpp_fp64_lockstep_ragged(K, variant, grid):
     A, b, _ = W.spd(200, 6, 1e2, 1e3, 1.0, 5.0, seed_A=10, seed_b=11)
     for T in (1, 7, 2 * 13 * 4, 2 * 13 * 9 + 5):
         x, rep, res = _kpp_pair(K, A, b, 16, 1e-4, T=T, grid=grid, cd=True)
@@ -150,7 +158,7 @@ def test_cdpp_fp64_nonzero_start(K):
 
 
 @pytest.mark.slow
-def test_cdpp_fp64_spd4096_to_tolerance(K):
+def test_cdpp_fp64_spd4096_to_tolerance(K, variant):
     sy = W.cdpp_fp64_spd()
     x, rep, res = _kpp_pair(K, sy.A, sy.b, sy.s, sy.lam, tol=sy.tol, seed=1, cd=True)
     assert rep.status == K.OK and res.status == oracle.OK
@@ -181,7 +189,7 @@ def test_argument_errors(K):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_mixed_precision_refinement_reaches_1e8(K, dtype):
+def test_mixed_precision_refinement_reaches_1e8(K, variant, dtype):
     sy = W.kpp_mixed_lowrank(m=16384, n=512, s=128, n_out=16)
     A = W.round_to_storage(sy.A, dtype)
     b = A @ sy.x_star
@@ -199,7 +207,7 @@ def test_mixed_precision_refinement_reaches_1e8(K, dtype):
     assert rel(x.cpu().numpy(), xo) <= kappa * 2e-8
 
 
-def test_mixed_cdpp_refinement(K):
+def test_mixed_cdpp_refinement(K, variant):
     A, b, _ = W.spd(512, 8, 1e2, 1e3, 1.0, 10.0, seed_A=20, seed_b=21)
     A32 = W.round_to_storage(A, "f32")
     P = K.Partition(512, 64)
@@ -212,8 +220,10 @@ def test_mixed_cdpp_refinement(K):
     assert rel(x.cpu().numpy(), xo) <= 1e3 * 2e-8
 
 
-def test_batched_multi_rhs_matches_single_rhs_oracle(K):
-    nsys, k, m, n, s, lam = 3, 3, 60, 25, 7, 0.05
+@pytest.mark.parametrize("shape", [(60, 25, 7), (60, 24, 6)])
+def test_batched_multi_rhs_matches_single_rhs_oracle(K, variant, shape):
+    nsys, k, lam = 3, 3, 0.05
+    m, n, s = shape
     As, Bs = [], []
     for i in range(nsys):
         rng = np.random.default_rng(100 + i)
