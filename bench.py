@@ -265,7 +265,7 @@ def main():
     ach_flops = mean_iters * flops / (kms / 1e3) / 1e9
     ach_bytes = mean_iters * byts / (kms / 1e3) / 1e9
     hbm = peaks.get("hbm_gbs", 6800.0)
-    roof = {"kernel": "solve_kernel", "bound": "alu", "achieved": ach_flops, "peak": fp64_peak, "unit": "GFLOP/s",
+    roof = {"kernel": "cd3_kernel" if cd else "solve2_kernel", "bound": "alu", "achieved": ach_flops, "peak": fp64_peak, "unit": "GFLOP/s",
             "frac": ach_flops / fp64_peak, "traffic": None,
             "per_iter": {"flops": flops, "bytes": byts},
             "hbm_view": {"achieved": ach_bytes, "peak": hbm, "unit": "GB/s", "frac": ach_bytes / hbm,

@@ -207,11 +207,15 @@ kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t
 kpp_status cdpp_solve_noalloc(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
                               const kpp_params *p, kpp_report *rep, void *stream);
 
-/* Select the solve kernel for later calls in this process: 2 (default) uses the small-block kernel
- * (one barrier per step, TMA-prefetched A tiles and memoised inverses) wherever the shape allows it
- * (s even and <= 256, row stride a multiple of 16 bytes, per-CTA chunk <= 256 columns); 1 always
- * uses the general kernel.  Both compute the same iteration.  Not thread-safe with concurrent solves.
- * Errors: KPP_ERR_ARG for another value. */
+/* Select the solve kernel for later calls in this process.  All variants compute the same iteration.
+ *   3 (default): CD++ uses the dataflow kernel (no per-step barrier: the owners of the next block
+ *     hand r over through a tagged mailbox; FP64 streams the memoised W_j = G_j^{-1} A_{S_j}); K++ uses
+ *     the small-block kernel; each only where the shape allows it, else as below;
+ *   2: the small-block kernel (one barrier per step, TMA-prefetched tiles and memoised inverses) where
+ *     the shape allows it (s even and <= 256, row stride a multiple of 16 bytes, per-CTA chunk <= 256
+ *     columns, shared memory fits), else the general kernel;
+ *   1: the general kernel always.
+ * Not thread-safe with concurrent solves.  Errors: KPP_ERR_ARG for another value. */
 kpp_status kpp_set_kernel_variant(int32_t variant);
 
 /* Library build information: "sm_103a; <compiler>; <date>". */

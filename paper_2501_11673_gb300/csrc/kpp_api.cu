@@ -56,6 +56,8 @@ void FactorSet::release() {
     if (L) cudaFree(L);
     if (Ginv) cudaFree(Ginv);
     if (Ginv32) cudaFree(Ginv32);
+    if (W) cudaFree(W);
+    W = nullptr;
     L = nullptr;
     Ginv = nullptr;
     Ginv32 = nullptr;
@@ -138,12 +140,12 @@ static int auto_grid(int64_t cols, int nsys) {
 }
 
 // Run the persistent kernel over nsys systems that share shape, dtype, s and k.
-static bool g_use_v2 = true;
+static int g_variant = 3;
 
 static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd, int k, int s, double eta,
                                  double tol, int adaptive, int confirm, int64_t max_iters, uint64_t seed, int grid,
                                  bool init_residual, int64_t t0, cudaStream_t st, float *ms_out, int *err_out) {
-    const bool use_v2 = g_use_v2;
+    const bool use_v2 = g_variant >= 2;
     kpp_status rc = KPP_OK;
     const int nsys = (int)sys.size();
     const kpp_matrix &A0 = *sys[0].A;
@@ -158,6 +160,14 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     const int nb = (int)((A0.rows + s - 1) / s);
     bool v2 = use_v2;
     for (int i = 0; v2 && i < nsys; ++i) v2 = solve2_eligible(*sys[i].A, s, CW, KP, f64);
+    // CD++ dataflow kernel: same eligibility as v2, plus the memoised W for FP64
+    bool v3 = cd && v2 && g_variant >= 3;
+    for (int i = 0; v3 && i < nsys; ++i) {
+        if (f64 && !sys[i].F->W) v3 = false;
+        const size_t tas = f64 ? 8 : dtype_size(dtype);
+        if (cd3_smem_bytes(s, CW, KP, (int)tas, (int)tcs, f64) > 200 * 1024) v3 = false;
+    }
+    if (v3) v2 = false;
     Common cm{};
     cm.rows = A0.rows;
     cm.cols = A0.cols;
@@ -205,7 +215,7 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
         CUDA_OR(scr.alloc(&a.m, vec_n * tcs), KPP_ERR_CUDA);
         CUDA_OR(cudaMemsetAsync(a.m, 0, vec_n * tcs, st), KPP_ERR_CUDA);
         if (cd) {
-            // v2 keeps two published copies of R_x (steps of even / odd index)
+            // v2 keeps two published copies of R_x (steps of even / odd index); v1 and v3 one
             CUDA_OR(scr.alloc(&a.Rx, (v2 ? 2 : 1) * vec_r * tcs), KPP_ERR_CUDA);
             CUDA_OR(scr.alloc(&a.Rm, vec_r * tcs), KPP_ERR_CUDA);
             CUDA_OR(cudaMemsetAsync(a.Rm, 0, vec_r * tcs, st), KPP_ERR_CUDA);
@@ -228,7 +238,33 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
         a.sys_id = sys[i].sys_id;
         a.t0 = t0;
     }
-    if (v2) {
+    if (v3) {
+        const size_t sb = sys3_bytes();
+        const size_t mb = cd3_mail_bytes(s, KP, f64);
+        h2.assign(sb * nsys, 0);
+        for (int i = 0; i < nsys; ++i) {
+            alignas(128) unsigned char tm[128];
+            const void *src = f64 ? (const void *)sys[i].F->W : sys[i].A->data;
+            const int64_t ld = f64 ? sys[i].A->cols : sys[i].A->ld;
+            void *mail = nullptr;
+            CUDA_OR(scr.alloc(&mail, mb), KPP_ERR_CUDA);
+            CUDA_OR(cudaMemsetAsync(mail, 0, mb, st), KPP_ERR_CUDA);
+            if (!make_tmap_2d(tm, src, dtype, sys[i].A->cols, sys[i].A->rows, ld, (uint32_t)CW, (uint32_t)s)) {
+                set_error("cuTensorMapEncodeTiled failed for system %d", i);
+                rc = KPP_ERR_CUDA;
+                goto cleanup;
+            }
+            sys3_fill(h2.data() + sb * i, args[i], tm, mail);
+        }
+        CUDA_OR(scr.alloc(&d_sys2, sb * nsys), KPP_ERR_CUDA);
+        if ((uintptr_t)d_sys2 & 127) {
+            set_error("descriptor buffer not 128-byte aligned");
+            rc = KPP_ERR_CUDA;
+            goto cleanup;
+        }
+        CUDA_OR(cudaMemcpyAsync(d_sys2, h2.data(), sb * nsys, cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
+        CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
+    } else if (v2) {
         const size_t sb = sys2_bytes();
         h2.assign(sb * nsys, 0);
         for (int i = 0; i < nsys; ++i) {
@@ -242,6 +278,11 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
             sys2_fill(h2.data() + sb * i, args[i], tm);
         }
         CUDA_OR(scr.alloc(&d_sys2, sb * nsys), KPP_ERR_CUDA);
+        if ((uintptr_t)d_sys2 & 127) {  // tensor maps must be 64-byte aligned in memory
+            set_error("descriptor buffer not 128-byte aligned");
+            rc = KPP_ERR_CUDA;
+            goto cleanup;
+        }
         CUDA_OR(cudaMemcpyAsync(d_sys2, h2.data(), sb * nsys, cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
         CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);  // h2 is pageable and local
     } else {
@@ -253,8 +294,9 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     CUDA_OR(cudaEventCreate(&e1), KPP_ERR_CUDA);
     CUDA_OR(cudaEventRecord(e0, st), KPP_ERR_CUDA);
     {
-        cudaError_t le = v2 ? launch_solve2(dtype, cd, d_sys2, nsys, cm, KP, st)
-                            : launch_solve(dtype, f64, cd, d_args, nsys, cm, KP, st);
+        cudaError_t le = v3   ? launch_cd3(dtype, d_sys2, nsys, cm, KP, st)
+                         : v2 ? launch_solve2(dtype, cd, d_sys2, nsys, cm, KP, st)
+                              : launch_solve(dtype, f64, cd, d_args, nsys, cm, KP, st);
         if (le == cudaErrorCooperativeLaunchTooLarge) {
             set_error("%d systems x %d CTAs do not fit co-resident on this GPU", nsys, G);
             rc = KPP_ERR_UNSUPPORTED;
@@ -624,11 +666,11 @@ kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t
 
 kpp_status kpp_set_kernel_variant(int32_t variant) {
     clear_error();
-    if (variant != 1 && variant != 2) {
-        set_error("kpp_set_kernel_variant: variant must be 1 or 2");
+    if (variant < 1 || variant > 3) {
+        set_error("kpp_set_kernel_variant: variant must be 1, 2 or 3");
         return KPP_ERR_ARG;
     }
-    g_use_v2 = variant == 2;
+    g_variant = variant;
     return KPP_OK;
 }
 

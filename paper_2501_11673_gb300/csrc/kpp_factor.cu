@@ -171,6 +171,55 @@ __global__ void __launch_bounds__(512) cholesky_inverse_kernel(int64_t rows, int
 }
 
 // ---------------------------------------------------------------------------------------------
+// CD++ FP64: W_j = G_j^{-1} A_{S_j} for every block (rows j s .. j s + len of W).  With A symmetric,
+// u = A_{:,S} y = A_S^T G^{-1} r = W_S^T r, so the solve applies the memoised inverse and the block
+// rows in one pass.  Grid (nb, ceil(cols / 64)); each CTA computes a len x 64 tile, FP64.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) cd_w_kernel(const double *__restrict__ A, int64_t lda, int64_t n, int s,
+                                                   const double *__restrict__ Ginv, double *__restrict__ W) {
+    const int j = blockIdx.x;
+    const int64_t r0 = (int64_t)j * s;
+    const int len = (int)min64(s, n - r0);
+    const int64_t col0 = (int64_t)blockIdx.y * 64;
+    __shared__ double sg[64][65];
+    __shared__ double sa[64][65];
+    const double *Gj = Ginv + (size_t)j * s * s;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+    for (int a0 = 0; a0 < len; a0 += 64) {
+        double acc[4][4] = {};
+        for (int d0 = 0; d0 < len; d0 += 64) {
+            for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+                const int rr = e >> 6, cc = e & 63;
+                sg[rr][cc] = (a0 + rr < len && d0 + cc < len) ? Gj[(size_t)(a0 + rr) * len + d0 + cc] : 0.0;
+                sa[rr][cc] = (d0 + rr < len && col0 + cc < n) ? A[(r0 + d0 + rr) * lda + col0 + cc] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int d = 0; d < 64; ++d) {
+                double gv[4], av[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) gv[u] = sg[ty * 4 + u][d];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) av[v] = sa[d][tx * 4 + v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(gv[u], av[v], acc[u][v]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int a = a0 + ty * 4 + u;
+                const int64_t c = col0 + tx * 4 + v;
+                if (a < len && c < n) W[(r0 + a) * n + c] = acc[u][v];
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------------------------
 template <typename TA>
@@ -245,6 +294,12 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
             rc = KPP_ERR_NOT_SPD;
             set_error("block %d: Cholesky pivot not positive", hb);
         }
+    }
+    if (rc == KPP_OK && mode == 1 && A.dtype == KPP_F64) {
+        KPP_TRY(cudaMalloc(&F.W, (size_t)rows * rows * sizeof(double)));
+        dim3 grid((unsigned)nb, (unsigned)((rows + 63) / 64));
+        cd_w_kernel<<<grid, 256, 0, st>>>((const double *)A.data, A.ld, rows, s, F.Ginv, F.W);
+        KPP_TRY(cudaGetLastError());
     }
 done:
 #undef KPP_TRY

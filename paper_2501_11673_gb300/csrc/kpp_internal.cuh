@@ -108,7 +108,8 @@ __device__ __forceinline__ bool group_barrier(GroupSync &gs) {
     gs.target += 1u;
     if (threadIdx.x == 0) {
         unsigned want = gs.target * gs.G;
-        __threadfence();
+        // release: the CTA's writes (ordered before this thread by __syncthreads) become visible
+        // to any CTA whose acquire load sees this arrival
         red_release_add_u32(gs.ctr, 1u);
         unsigned v = ld_acquire_u32(gs.ctr);
         uint64_t t0 = 0;
@@ -123,7 +124,6 @@ __device__ __forceinline__ bool group_barrier(GroupSync &gs) {
             }
             v = ld_acquire_u32(gs.ctr);
         }
-        __threadfence();
         s_ok = ((int)(v - want) < (int)(ERR_BIAS / 2u)) ? 1 : 0;
     }
     __syncthreads();

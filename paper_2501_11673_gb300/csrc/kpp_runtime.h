@@ -23,6 +23,7 @@ struct FactorSet {
     double *L = nullptr;      // nb x s x s, FP64 lower Cholesky factors (block j: len x len, ld len)
     double *Ginv = nullptr;   // nb x s x s, FP64 (G_j)^{-1}
     float *Ginv32 = nullptr;  // nb x s x s, FP32 copy (FP32/BF16 storage only)
+    double *W = nullptr;      // CD++ FP64 only: rows x cols, block j rows = G_j^{-1} A_{S_j} (row-major, ld cols)
     void release();
 };
 

@@ -75,4 +75,11 @@ size_t sys2_bytes();
 void sys2_fill(void *dst_host, const SysArgs &a, const void *tmap);
 cudaError_t launch_solve2(int dtype, bool cd, const void *d_sys, int nsys, const Common &cm, int KP, cudaStream_t st);
 
+// Dataflow CD++ kernel (kpp_cd3.cu).
+size_t cd3_smem_bytes(int s, int64_t CW, int KP, int ta_size, int tc_size, bool use_w);
+size_t cd3_mail_bytes(int s, int KP, bool f64);
+size_t sys3_bytes();
+void sys3_fill(void *dst_host, const SysArgs &a, const void *tmap, void *mail);
+cudaError_t launch_cd3(int dtype, const void *d_sys, int nsys, const Common &cm, int KP, cudaStream_t st);
+
 }  // namespace kpp

@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
     __shared__ double s_rn2[KP];
     __shared__ int s_stop, s_need, s_fail;
     __shared__ int s_pending[2];
+    __shared__ TC s_beta[KP], s_keep[KP];
     __shared__ unsigned s_phase[2];
 
     GroupSync gs{sa.bar, sa.err, 0u, (unsigned)cm.G, cm.timeout_ns};
@@ -208,6 +209,11 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             }
         };
 
+        if (threadIdx.x < KP) {
+            const double rho = st[threadIdx.x].rho;
+            s_beta[threadIdx.x] = (TC)((1.0 - rho) / (1.0 + rho));
+            s_keep[threadIdx.x] = (TC)((threadIdx.x < k && st[threadIdx.x].active) ? 1 : 0);
+        }
         __syncthreads();
         if (threadIdx.x == 0 && t < cm.max_iters) {
             issue(t, (int)(t & 1));
@@ -290,9 +296,8 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
                 TC beta[KP], keep[KP];
 #pragma unroll
                 for (int c = 0; c < KP; ++c) {
-                    const double rho = st[c].rho;
-                    beta[c] = (TC)((1.0 - rho) / (1.0 + rho));
-                    keep[c] = (TC)((c < k && st[c].active) ? 1 : 0);
+                    beta[c] = s_beta[c];
+                    keep[c] = s_keep[c];
                 }
                 const TC eta = (TC)cm.eta;
                 const TA *tl = tile[bf];
@@ -396,6 +401,11 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
                     }
                 }
                 if (threadIdx.x < k && st[threadIdx.x].active) checkpoint_column(st[threadIdx.x], cm, zeta);
+                if (threadIdx.x < KP) {
+                    const double rho = st[threadIdx.x].rho;
+                    s_beta[threadIdx.x] = (TC)((1.0 - rho) / (1.0 + rho));
+                    s_keep[threadIdx.x] = (TC)((threadIdx.x < k && st[threadIdx.x].active) ? 1 : 0);
+                }
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     int any = 0;

@@ -305,7 +305,8 @@ def sample_blocks(seed: int, sys_id: int, t0: int, count: int, nb: int, stream=N
 
 
 def set_kernel_variant(v: int) -> None:
-    """1: general kernel everywhere; 2 (default): small-block kernel where the shape allows it."""
+    """1: general kernel everywhere; 2: small-block kernel where the shape allows it; 3 (default): as 2,
+    and the dataflow kernel for CD++ where the shape allows it."""
     _check(load().kpp_set_kernel_variant(int(v)))
 
 

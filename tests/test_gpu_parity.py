@@ -90,11 +90,11 @@ def _kpp_pair(K, A, b, s, lam, T=None, tol=0.0, seed=3, grid=0, adaptive=True, x
     return x.cpu().numpy(), rep, res
 
 
-@pytest.fixture(params=[1, 2], ids=["general", "smallblock"])
+@pytest.fixture(params=[1, 2, 3], ids=["general", "smallblock", "dataflow"])
 def variant(request, K):
     K.set_kernel_variant(request.param)
     yield request.param
-    K.set_kernel_variant(2)
+    K.set_kernel_variant(3)
 
 
 @pytest.mark.parametrize("grid", [1, 3, 8, 40])
