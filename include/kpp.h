@@ -207,6 +207,19 @@ kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t
 kpp_status cdpp_solve_noalloc(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
                               const kpp_params *p, kpp_report *rep, void *stream);
 
+/* The block Grams of the K++ factor phase (Sec. 4; Eq. 1.3): G_j = A_{S_j} A_{S_j}^T + lambda I for
+ * every block of the contiguous partition into blocks of s rows.  A: device matrix (any dtype).
+ * G_out: device FP64 buffer of nb * s * s doubles; block j is written at G_out + j*s*s as a len x len
+ * row-major matrix (leading dimension len, len = rows of block j).  Only its lower triangle (with the
+ * diagonal) is written; the caller owns G_out.
+ * engine: 0 automatic (tensor cores for BF16 storage, CUDA cores otherwise), 1 CUDA cores with FP64
+ * accumulation, 2 tcgen05 tensor cores with FP32 accumulation (kind::f16 for BF16; kind::tf32 for
+ * FP32, i.e. TF32 products).  *engine_used (may be NULL) receives 1 or 2.
+ * Errors: KPP_ERR_ARG; KPP_ERR_UNSUPPORTED when engine 2 cannot take the matrix (FP64 storage, rows
+ * not 16-byte aligned); KPP_ERR_CUDA.  Synchronises `stream`. */
+kpp_status kpp_block_gram(const kpp_matrix *A, int32_t s, double lambda, int32_t engine, double *G_out,
+                          int32_t *engine_used, void *stream);
+
 /* Select the solve kernel for later calls in this process.  All variants compute the same iteration.
  *   3 (default): CD++ uses the dataflow kernel (no per-step barrier: the owners of the next block
  *     hand r over through a tagged mailbox; FP64 streams the memoised W_j = G_j^{-1} A_{S_j}); K++ uses

@@ -674,6 +674,32 @@ kpp_status kpp_set_kernel_variant(int32_t variant) {
     return KPP_OK;
 }
 
+kpp_status kpp_block_gram(const kpp_matrix *A, int32_t s, double lambda, int32_t engine, double *G_out,
+                          int32_t *engine_used, void *stream) {
+    clear_error();
+    if (!matrix_ok(A) || s < 1 || s > 1024 || !G_out || engine < 0 || engine > 2) {
+        set_error("kpp_block_gram: invalid argument");
+        return KPP_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int used = block_gram(*A, s, lambda, G_out, engine, st);
+    if (engine_used) *engine_used = used;
+    if (used < 0) {
+        if (engine == 2) {
+            set_error("kpp_block_gram: the tensor-core Gram does not support this matrix (dtype, alignment)");
+            return KPP_ERR_UNSUPPORTED;
+        }
+        set_error("kpp_block_gram: launch failed");
+        return KPP_ERR_CUDA;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_error("kpp_block_gram: %s", cudaGetErrorString(e));
+        return KPP_ERR_CUDA;
+    }
+    return KPP_OK;
+}
+
 kpp_status kpp_rel_residual(const kpp_matrix *A, const double *b, const double *x, double *out_host, void *stream) {
     clear_error();
     if (!matrix_ok(A) || !b || !x || !out_host) {

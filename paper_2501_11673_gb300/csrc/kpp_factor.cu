@@ -237,6 +237,15 @@ static void launch_principal(const void *A, int64_t lda, int64_t n, int s, doubl
     principal_block_kernel<TA><<<(unsigned)nb, 256, 0, st>>>((const TA *)A, lda, n, s, lam, G);
 }
 
+int block_gram(const kpp_matrix &A, int s, double lam, double *G, int engine, cudaStream_t st) {
+    if (engine != 1 && A.dtype != KPP_F64 && gram_tc(A, s, lam, G, st, engine == 2)) return 2;
+    if (engine == 2) return -1;
+    if (A.dtype == KPP_F64) launch_gram<double>(A.data, A.ld, A.rows, A.cols, s, lam, G, st);
+    else if (A.dtype == KPP_F32) launch_gram<float>(A.data, A.ld, A.rows, A.cols, s, lam, G, st);
+    else launch_gram<__nv_bfloat16>(A.data, A.ld, A.rows, A.cols, s, lam, G, st);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
 kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, FactorSet &F, cudaStream_t st) {
     const int64_t rows = A.rows;
     const int64_t nb = (rows + s - 1) / s;
@@ -271,11 +280,10 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
         KPP_TRY(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, st));
     }
     if (mode == 0) {
-        if (A.dtype == KPP_F64) {
-            launch_gram<double>(A.data, A.ld, rows, A.cols, s, lam, G, st);
-        } else if (!gram_tc(A, s, lam, G, st)) {
-            if (A.dtype == KPP_F32) launch_gram<float>(A.data, A.ld, rows, A.cols, s, lam, G, st);
-            else launch_gram<__nv_bfloat16>(A.data, A.ld, rows, A.cols, s, lam, G, st);
+        if (block_gram(A, s, lam, G, 0, st) < 0) {
+            rc = KPP_ERR_CUDA;
+            set_error("block Gram launch failed");
+            goto done;
         }
     } else {
         if (A.dtype == KPP_F64) launch_principal<double>(A.data, A.ld, rows, s, lam, G, st);

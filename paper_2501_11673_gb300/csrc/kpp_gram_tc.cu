@@ -1,12 +1,287 @@
-// kpp_gram_tc.cu -- block Gram A_S A_S^T on the tcgen05 tensor cores (FP32/BF16 storage).
+// kpp_gram_tc.cu -- block Gram G_j = A_{S_j} A_{S_j}^T + lam I on the tcgen05 tensor cores (Sec. 4:
+// the memoised factor of K++ is chol(A_S A_S^T + lam I); Alg. 1 line 7).
+//
+// FP32 / BF16 storage only (kind::tf32 / kind::f16, FP32 accumulation in tensor memory); the result is
+// widened to FP64 for the FP64 Cholesky.  One CTA computes one 128 x 256 tile of one block's Gram:
+//   * warp 0, one thread: TMA producer -- K-major tiles of the block rows (128-byte swizzle) into a
+//     4-stage shared-memory ring, one mbarrier per stage for "full" and one for "empty";
+//   * warp 1, one thread: MMA issuer -- tcgen05.mma (M=128, N=256, K=16 bf16 / K=8 tf32) into 256 TMEM
+//     columns; tcgen05.commit frees a stage when its MMAs are done, and signals the epilogue at the end;
+//   * warps 0-3: epilogue -- tcgen05.ld of their 32 TMEM lanes, + lam on the diagonal, FP64 stores of
+//     the lower triangle (all the Cholesky reads).
+// Only tiles that touch the lower triangle of G are launched.  No cluster, no multicast: each CTA loads
+// its own tiles.  Every wait is bounded; a wait that runs out sets the error word and the CTA winds
+// down (it still waits, bounded, for its MMAs before releasing tensor memory).
+#include <cuda.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
 #include "kpp_internal.cuh"
 #include "kpp_runtime.h"
+#include "kpp_solve.h"
 
 namespace kpp {
 
-bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st) {
-    (void)A; (void)s; (void)lam; (void)G; (void)st;
-    return false;
+constexpr int TC_M = 128, TC_N = 256, TC_STAGES = 4;
+constexpr int TC_ROWB = 128;                               // bytes of K per tile row (one swizzle atom row)
+constexpr int TC_ABYTES = TC_M * TC_ROWB;                  // 16 KiB
+constexpr int TC_BBYTES = TC_N * TC_ROWB;                  // 32 KiB
+constexpr int TC_STAGE_BYTES = TC_ABYTES + TC_BBYTES;      // 48 KiB
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024; // + alignment slack
+constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
+
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);       // start address
+    d |= (uint64_t)1u << 16;                        // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;              // stride byte offset: next 8-row atom
+    d |= (uint64_t)1u << 46;                        // fixed 0b001
+    d |= (uint64_t)2u << 61;                        // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A and B of one type (1 = bf16 for kind::f16, 2 = tf32),
+// both K-major, N = 256, M = 128.
+__host__ __device__ constexpr uint32_t umma_idesc(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <bool BF16>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+    if (BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct GramTile {
+    int j, ta, tc;
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t rows,
+                                                         int64_t cols, int s, double lam, const GramTile *tiles,
+                                                         double *__restrict__ G, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_err;
+
+    const GramTile tile = tiles[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)tile.j * s;
+    const int len = (int)min64(s, rows - r0);
+    const int BK = TC_ROWB / (BF16 ? 2 : 4);                 // K elements per stage
+    const int KSTEP = BF16 ? 16 : 8;                         // K of one MMA
+    const int nk = (int)((cols + BK - 1) / BK);
+    constexpr uint32_t idesc = umma_idesc(BF16 ? 1u : 2u);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(&full_bar[i], 1);
+            mbar_init(&empty_bar[i], 1);
+        }
+        mbar_init(&done_bar, 1);
+        fence_mbar_init();
+        s_err = 0;
+    }
+    if (warp == 0) {  // whole warp: allocate 256 TMEM columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        int stage = 0;
+        unsigned phase = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            if (kt >= TC_STAGES) {
+                if (!mbar_wait_bounded(&empty_bar[stage], phase ^ 1u, TC_TIMEOUT_NS)) {
+                    s_err = 1;
+                    break;
+                }
+            }
+            unsigned char *a_s = sm + stage * TC_STAGE_BYTES;
+            unsigned char *b_s = a_s + TC_ABYTES;
+            mbar_arrive_expect_tx(&full_bar[stage], TC_STAGE_BYTES);
+            const int kx = kt * BK;
+            tma_load_2d(a_s, &tmap, kx, (int)(r0 + tile.ta * TC_M), &full_bar[stage]);
+            tma_load_2d(b_s, &tmap, kx, (int)(r0 + tile.tc * TC_N), &full_bar[stage]);
+            tma_load_2d(b_s + TC_ABYTES, &tmap, kx, (int)(r0 + tile.tc * TC_N + TC_M), &full_bar[stage]);
+            if (++stage == TC_STAGES) {
+                stage = 0;
+                phase ^= 1u;
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        int stage = 0;
+        unsigned phase = 0;
+        int issued = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            if (!mbar_wait_bounded(&full_bar[stage], phase, TC_TIMEOUT_NS)) {
+                s_err = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(sm + stage * TC_STAGE_BYTES);
+            const uint32_t b_addr = a_addr + TC_ABYTES;
+            for (int kk = 0; kk < BK / KSTEP; ++kk) {
+                const uint32_t koff = (uint32_t)(kk * KSTEP * (BF16 ? 2 : 4));  // bytes along the 128-byte row
+                umma<BF16>(tmem, umma_desc_sw128(a_addr + koff), umma_desc_sw128(b_addr + koff), idesc,
+                           (kt > 0 || kk > 0) ? 1u : 0u);
+                ++issued;
+            }
+            umma_commit(&empty_bar[stage]);  // stage reusable once these MMAs have read it
+            if (++stage == TC_STAGES) {
+                stage = 0;
+                phase ^= 1u;
+            }
+        }
+        umma_commit(&done_bar);  // all issued MMAs complete (also on the error path)
+        (void)issued;
+    }
+    __syncwarp();
+    // epilogue: every thread owns TMEM lane (32 * warp + lane) = tile row
+    bool ok = true;
+    if (lane == 0) ok = mbar_wait_bounded(&done_bar, 0, TC_TIMEOUT_NS);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    tc_fence_after();
+    if (ok && !s_err) {
+        const int a = tile.ta * TC_M + warp * 32 + lane;  // row of G within the block
+        double *Gj = G + (size_t)tile.j * s * s;
+        for (int c0 = 0; c0 < TC_N; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            const int cb = tile.tc * TC_N + c0;
+            if (a < len) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int c = cb + q;
+                    if (c <= a && c < len) Gj[(size_t)a * len + c] = (double)__uint_as_float(v[q]) + (c == a ? lam : 0.0);
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn2)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static bool gram_tc_disabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("KPP_GRAM_TC");
+        v = (e && e[0] == '0') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st, bool allow_tf32) {
+    if (gram_tc_disabled()) return false;
+    if (A.dtype != KPP_BF16 && !(A.dtype == KPP_F32 && allow_tf32)) return false;
+    const size_t es = A.dtype == KPP_F32 ? 4 : 2;
+    if (((uintptr_t)A.data & 15) || ((A.ld * es) & 15) || A.rows > 0x7fffffffLL || A.cols > 0x7fffffffLL) return false;
+    void *fnp = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fnp, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return false;
+    EncodeTiledFn2 enc = (EncodeTiledFn2)fnp;
+    CUtensorMap tm;
+    cuuint64_t dims[2] = {(cuuint64_t)A.cols, (cuuint64_t)A.rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(A.ld * es)};
+    cuuint32_t box[2] = {(cuuint32_t)(TC_ROWB / es), (cuuint32_t)TC_M};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&tm, A.dtype == KPP_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void *>(A.data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    // tiles of the lower triangle: row tile ta (128 rows), column tile tc (256 columns), 256 tc <= 128 ta + 127
+    const int64_t nb = (A.rows + s - 1) / s;
+    const int mt = (s + TC_M - 1) / TC_M, ntl = (s + TC_N - 1) / TC_N;
+    std::vector<GramTile> tl;
+    for (int64_t j = 0; j < nb; ++j)
+        for (int ta = 0; ta < mt; ++ta)
+            for (int tc = 0; tc < ntl; ++tc)
+                if (tc * TC_N <= ta * TC_M + TC_M - 1) tl.push_back(GramTile{(int)j, ta, tc});
+    GramTile *d_tiles = nullptr;
+    int *d_err = nullptr;
+    int herr = 0;
+    bool ok = cudaMallocAsync((void **)&d_tiles, tl.size() * sizeof(GramTile), st) == cudaSuccess;
+    ok = ok && cudaMallocAsync((void **)&d_err, sizeof(int), st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(d_err, 0, sizeof(int), st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(d_tiles, tl.data(), tl.size() * sizeof(GramTile), cudaMemcpyHostToDevice, st) ==
+                   cudaSuccess;
+    if (ok) {
+        auto kern = A.dtype == KPP_BF16 ? gram_tc_kernel<true> : gram_tc_kernel<false>;
+        ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) == cudaSuccess;
+        if (ok) {
+            kern<<<(unsigned)tl.size(), 128, TC_SMEM, st>>>(tm, A.rows, A.cols, s, lam, d_tiles, G, d_err);
+            ok = cudaGetLastError() == cudaSuccess;
+        }
+        ok = ok && cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    if (d_tiles) cudaFreeAsync(d_tiles, st);
+    if (d_err) cudaFreeAsync(d_err, st);
+    if (!ok || herr) {
+        set_error("tensor-core Gram failed (%s); using the CUDA-core Gram", herr ? "device wait expired" : "launch");
+        return false;
+    }
+    return true;
 }
 
 }  // namespace kpp

@@ -32,7 +32,13 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
 // Tensor-core block Gram for FP32/BF16 storage (kpp_gram_tc.cu).  Writes G (nb x s x s, FP64,
 // block j packed with leading dimension len) and returns true, or returns false when the shape is
 // not supported by the tensor-core kernel (the caller then uses the CUDA-core kernel).
-bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st);
+// FP32 storage goes through the tensor cores only when allow_tf32 is set (plain TF32 products).
+bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st, bool allow_tf32 = false);
+
+// Block Grams only (lower triangles, FP64, packed per block with leading dimension len):
+// engine 0 = automatic, 1 = CUDA cores with FP64 accumulation, 2 = tensor cores (BF16, or TF32 for
+// FP32 storage).  Returns the engine used, or -1.
+int block_gram(const kpp_matrix &A, int s, double lam, double *G, int engine, cudaStream_t st);
 
 // Number of SMs of the current device (cached).
 int sm_count();

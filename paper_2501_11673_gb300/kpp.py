@@ -31,7 +31,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NUMERIC, ERR_NO_CONVERGENCE, ER
 EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_partition", "kpp_partition_destroy",
            "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block",
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
-           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_build_info"]
+           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_block_gram", "kpp_build_info"]
 
 
 class KppError(RuntimeError):
@@ -101,6 +101,8 @@ def load(path: str | None = None):
                                           vp, ctypes.POINTER(vp), ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
         lib.kpp_sample_blocks.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i64, i64, i32, vp, vp]
         lib.kpp_set_kernel_variant.argtypes = [i32]
+        lib.kpp_block_gram.argtypes = [ctypes.POINTER(Matrix), i32, dbl, i32, vp, ctypes.POINTER(i32), vp]
+        lib.kpp_block_gram.restype = ctypes.c_int
         for name in ("kpp_set_kernel_variant", "cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
                      "kpp_solve_host", "kpp_rel_residual", "kpp_solve_batched"):
             getattr(lib, name).restype = ctypes.c_int
@@ -302,6 +304,19 @@ def sample_blocks(seed: int, sys_id: int, t0: int, count: int, nb: int, stream=N
     out = torch.empty(count, dtype=torch.int32, device="cuda")
     _check(load().kpp_sample_blocks(seed, sys_id, t0, count, nb, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def block_gram(A, s: int, lam: float, engine: int = 0, stream=None):
+    """Lower triangles of the block Grams A_S A_S^T + lam I (FP64, (nb, s, s) packed per block) and the
+    engine used (1 CUDA cores FP64-accumulate, 2 tensor cores FP32-accumulate)."""
+    import torch
+    nb = -(-A.shape[0] // s)
+    G = torch.zeros(nb * s * s, dtype=torch.float64, device=A.device)
+    used = ctypes.c_int32(-1)
+    m = matrix(A)
+    _check(load().kpp_block_gram(ctypes.byref(m), int(s), float(lam), int(engine), ctypes.c_void_p(G.data_ptr()),
+                                 ctypes.byref(used), _stream_ptr(stream)))
+    return G, used.value
 
 
 def set_kernel_variant(v: int) -> None:

@@ -252,3 +252,48 @@ def test_host_entry_point_matches_device_path(K):
     assert rep.status == K.OK and rep.rel_res_true <= 1e-8
     x, rep2, res = _kpp_pair(K, sy.A, sy.b, sy.s, sy.lam, tol=sy.tol, seed=0)
     np.testing.assert_array_equal(x_host, x)
+
+
+def _unpack_lower(G, j, rows, s):
+    ln = min(s, rows - j * s)
+    blk = G[j * s * s: j * s * s + ln * ln].reshape(ln, ln)
+    return np.tril(blk)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+@pytest.mark.parametrize("m,n,s", [(300, 1000, 128), (520, 200, 256), (1100, 776, 512), (64, 104, 64),
+                                   (256, 4096, 256)])
+def test_tensor_core_gram_matches_fp64_gram(K, dtype, m, n, s):
+    """tcgen05 Gram (FP32 accumulation; TF32 products for FP32 storage) against the FP64 CUDA-core Gram
+    and the oracle's definition, on the rounded storage values."""
+    rng = np.random.default_rng(m + n + s)
+    A = W.round_to_storage(rng.standard_normal((m, n)), dtype)
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    Ad = dev(A, tdt)
+    lam = 0.25
+    Gt, used = K.block_gram(Ad, s, lam, engine=2)
+    assert used == 2
+    G64, used64 = K.block_gram(Ad, s, lam, engine=1)
+    assert used64 == 1
+    Gt, G64 = Gt.cpu().numpy(), G64.cpu().numpy()
+    nb = -(-m // s)
+    # bf16 products are exact, so only FP32 accumulation errs: the tensor core sums K-slices of 16 exactly
+    # enough and rounds once per slice, about (n / 16) * 2^-23 relative on a diagonal entry.  TF32
+    # truncates each product to 11 bits (2^-10 relative) on top of that.
+    tol = max(1e-6, (n / 16) * 2.0 ** -23) + (0.0 if dtype == "bf16" else 2.0 ** -9)
+    for j in range(nb):
+        ref = np.tril(A[j * s:(j + 1) * s] @ A[j * s:(j + 1) * s].T) + lam * np.eye(min(s, m - j * s))
+        scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+        np.testing.assert_allclose(_unpack_lower(G64, j, m, s), ref, rtol=1e-12, atol=1e-12 * scale.max())
+        err = np.abs(_unpack_lower(Gt, j, m, s) - ref) / np.tril(scale)
+        assert np.nanmax(err) <= tol, (j, float(np.nanmax(err)))
+
+
+def test_tensor_core_gram_refuses_unaligned_rows_and_auto_falls_back(K):
+    A = dev(np.ones((64, 777)), torch.bfloat16)  # 1554-byte rows: not a TMA stride
+    with pytest.raises(K.KppError) as e:
+        K.block_gram(A, 64, 0.0, engine=2)
+    assert e.value.status == K.ERR_UNSUPPORTED
+    G, used = K.block_gram(A, 64, 0.0, engine=0)
+    assert used == 1
+    np.testing.assert_allclose(G.cpu().numpy()[:64 * 64].reshape(64, 64)[5, 3], 777.0)
