@@ -159,7 +159,7 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     G = (int)((A0.cols + CW - 1) / CW);  // no CTA without columns
     const int nb = (int)((A0.rows + s - 1) / s);
     bool v2 = use_v2;
-    for (int i = 0; v2 && i < nsys; ++i) v2 = solve2_eligible(*sys[i].A, s, CW, KP, f64);
+    for (int i = 0; v2 && i < nsys; ++i) v2 = solve2_eligible(*sys[i].A, s, CW, KP, f64, cd, G);
     // CD++ dataflow kernel: same eligibility as v2, plus the memoised W for FP64
     bool v3 = cd && v2 && g_variant >= 3;
     for (int i = 0; v3 && i < nsys; ++i) {
@@ -270,7 +270,7 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
         for (int i = 0; i < nsys; ++i) {
             alignas(128) unsigned char tm[128];
             if (!make_tmap_2d(tm, sys[i].A->data, dtype, sys[i].A->cols, sys[i].A->rows, sys[i].A->ld, (uint32_t)CW,
-                              (uint32_t)s)) {
+                              (uint32_t)std::min(s, 256))) {
                 set_error("cuTensorMapEncodeTiled failed for system %d", i);
                 rc = KPP_ERR_CUDA;
                 goto cleanup;
@@ -383,6 +383,9 @@ static kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *con
     std::vector<int64_t> iters(nsys, 0), outer(nsys, 0);
     for (int i = 0; i < nsys; ++i) init_scalars(sc[i], k, p.rho0);
     float ms = 0.f;
+    // refinement: the last outer check already holds |r|^2 and |b|^2 of the returned x
+    std::vector<std::vector<double>> bn2(nsys), res2(nsys);
+    bool have_final = false;
 
     if (dtype == KPP_F64) {
         // plain FP64 path: the kernel iterates directly on the caller's b and x
@@ -397,7 +400,6 @@ static kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *con
         // FP32 / BF16 storage: FP32 iterations, FP64 outer refinement (or a single FP32 solve)
         Scratch scr(st);
         std::vector<float *> b32(nsys), d32(nsys);
-        std::vector<std::vector<double>> bn2(nsys), res2(nsys);
         std::vector<int> done(nsys, 0);
         const size_t nr = (size_t)rows * k, nc = (size_t)cols * k;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -446,7 +448,10 @@ static kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *con
                     if (!active) done[i] = 1;
                     else any = true;
                 }
-                if (!any || outer_it == p.max_outer) break;
+                if (!any || outer_it == p.max_outer) {
+                    have_final = true;
+                    break;
+                }
                 // inner FP32 solve of A d = r from d = 0 (momentum restarts, rho carries over)
                 std::vector<SysInput> act;
                 std::vector<int> idx;
@@ -492,8 +497,13 @@ static kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *con
     kpp_status worst = rc;
     for (int i = 0; i < nsys; ++i) {
         std::vector<double> r2, b2;
-        kpp_status r3 = residual_norms(A[i], k, B[i], X[i], nullptr, r2, &b2, st);
-        if (r3 != KPP_OK) return r3;
+        if (have_final) {
+            r2 = res2[i];
+            b2 = bn2[i];
+        } else {
+            kpp_status r3 = residual_norms(A[i], k, B[i], X[i], nullptr, r2, &b2, st);
+            if (r3 != KPP_OK) return r3;
+        }
         for (int c = 0; c < k; ++c) {
             const double rel = b2[c] > 0 ? std::sqrt(r2[c] / b2[c]) : std::sqrt(r2[c]);
             kpp_status cs = (kpp_status)sc[i][c].status;

@@ -86,86 +86,226 @@ __global__ void principal_block_kernel(const TA *__restrict__ A, int64_t lda, in
 }
 
 // ---------------------------------------------------------------------------------------------
-// In-place lower Cholesky of each block's G (len x len, row-major, leading dimension len), then
-// Linv = L^{-1} and Ginv = Linv^T Linv.  One CTA per block.  Works in global memory (the block sits
-// in L2); right-looking, one column per step.  A non-positive or non-finite pivot records the block
-// in *bad (atomicMin) and leaves that block's outputs as NaN.
+// In-place lower Cholesky of each block's G (len x len, row-major, leading dimension len), FP64.
+// One CTA per block, working in global memory (the block sits in L2).  Right-looking, blocked by
+// panels of PB columns: the panel is factored column by column, copied (transposed) to shared
+// memory, and the trailing lower triangle takes one rank-PB update per panel, so every load of
+// G[i][k] carries PB FMAs.  A non-positive or non-finite pivot records the block in *bad
+// (atomicMin) and leaves its outputs NaN.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) cholesky_inverse_kernel(int64_t rows, int s, double *__restrict__ G,
-                                                               double *__restrict__ L, double *__restrict__ Linv,
-                                                               double *__restrict__ Ginv, float *__restrict__ Ginv32,
-                                                               int *__restrict__ bad) {
+constexpr int CHOL_PB = 8;
+constexpr int CHOL_NT = 512;
+
+__global__ void __launch_bounds__(CHOL_NT) cholesky_kernel(int64_t rows, int s, double *__restrict__ G,
+                                                          double *__restrict__ L, int *__restrict__ bad) {
     const int j = blockIdx.x;
     const int len = (int)min64(s, rows - (int64_t)j * s);
     double *Gj = G + (size_t)j * s * s;
     double *Lj = L + (size_t)j * s * s;
-    double *Ij = Linv + (size_t)j * s * s;
-    double *Vj = Ginv + (size_t)j * s * s;
+    extern __shared__ double panelT[];  // CHOL_PB x s: panelT[c][i - jb]
     __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = CHOL_NT / 32;
     if (threadIdx.x == 0) s_fail = 0;
     __syncthreads();
-    for (int c = 0; c < len; ++c) {
-        if (threadIdx.x == 0) {
-            double d = Gj[(size_t)c * len + c];
-            if (!(d > 0.0) || !isfinite(d)) {
-                s_fail = 1;
-            } else {
-                Gj[(size_t)c * len + c] = sqrt(d);
+    for (int jb = 0; jb < len && !s_fail; jb += CHOL_PB) {
+        const int pw = min(CHOL_PB, len - jb);
+        // (a) factor the panel columns
+        for (int c = jb; c < jb + pw; ++c) {
+            if (threadIdx.x == 0) {
+                const double d = Gj[(size_t)c * len + c];
+                if (!(d > 0.0) || !isfinite(d)) s_fail = 1;
+                else Gj[(size_t)c * len + c] = sqrt(d);
             }
+            __syncthreads();
+            if (s_fail) break;
+            const double ljj = Gj[(size_t)c * len + c];
+            for (int i = c + 1 + threadIdx.x; i < len; i += CHOL_NT) Gj[(size_t)i * len + c] /= ljj;
+            __syncthreads();
+            // update the rest of the panel: G[i][c2] -= L[i][c] L[c2][c], c < c2 < jb + pw, i >= c2
+            for (int c2 = c + 1; c2 < jb + pw; ++c2) {
+                const double l2 = Gj[(size_t)c2 * len + c];
+                for (int i = c2 + threadIdx.x; i < len; i += CHOL_NT) Gj[(size_t)i * len + c2] -= Gj[(size_t)i * len + c] * l2;
+            }
+            __syncthreads();
+        }
+        if (s_fail) break;
+        const int t0 = jb + pw;  // first trailing row/column
+        if (t0 >= len) break;
+        // (b) panel rows below it, transposed into shared memory
+        for (int e = threadIdx.x; e < pw * (len - jb); e += CHOL_NT) {
+            const int c = e / (len - jb), i = e % (len - jb);
+            panelT[c * s + i] = Gj[(size_t)(jb + i) * len + jb + c];
         }
         __syncthreads();
-        if (s_fail) break;
-        const double ljj = Gj[(size_t)c * len + c];
-        for (int i = c + 1 + threadIdx.x; i < len; i += blockDim.x) Gj[(size_t)i * len + c] /= ljj;
-        __syncthreads();
-        // trailing update of the lower triangle: G[i][k] -= L[i][c] L[k][c], c < k <= i
-        // (one warp per row i, lanes along k)
-        {
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-            for (int i = c + 1 + warp; i < len; i += nw) {
-                const double lic = Gj[(size_t)i * len + c];
-                for (int k = c + 1 + lane; k <= i; k += 32) Gj[(size_t)i * len + k] -= lic * Gj[(size_t)k * len + c];
+        // (c) trailing update of the lower triangle: warp per row i, lanes along k
+        for (int i = t0 + warp; i < len; i += nw) {
+            double li[CHOL_PB];
+#pragma unroll
+            for (int c = 0; c < CHOL_PB; ++c) li[c] = c < pw ? panelT[c * s + (i - jb)] : 0.0;
+            double *row = Gj + (size_t)i * len;
+            for (int k = t0 + lane; k <= i; k += 32) {
+                double v = row[k];
+#pragma unroll
+                for (int c = 0; c < CHOL_PB; ++c) v = fma(-li[c], panelT[c * s + (k - jb)], v);
+                row[k] = v;
             }
         }
         __syncthreads();
     }
     if (s_fail) {
         if (threadIdx.x == 0) atomicMin(bad, j);
-        for (int e = threadIdx.x; e < len * len; e += blockDim.x) {
-            Lj[e] = NAN;
-            Vj[e] = NAN;
-            if (Ginv32) Ginv32[(size_t)j * s * s + e] = NAN;
-        }
+        for (int e = threadIdx.x; e < len * len; e += CHOL_NT) Lj[e] = NAN;
         return;
     }
-    // L with a zero upper triangle
-    for (int e = threadIdx.x; e < len * len; e += blockDim.x) {
-        int a = e / len, c = e % len;
+    for (int e = threadIdx.x; e < len * len; e += CHOL_NT) {
+        const int a = e / len, c = e % len;
         Lj[e] = (c <= a) ? Gj[e] : 0.0;
     }
-    __syncthreads();
-    // Linv column by column (one thread per column): forward substitution L X = I
-    for (int c = threadIdx.x; c < len; c += blockDim.x) {
-        for (int i = 0; i < c; ++i) Ij[(size_t)i * len + c] = 0.0;
-        Ij[(size_t)c * len + c] = 1.0 / Lj[(size_t)c * len + c];
-        for (int i = c + 1; i < len; ++i) {
-            double v = 0.0;
-            for (int k = c; k < i; ++k) v += Lj[(size_t)i * len + k] * Ij[(size_t)k * len + c];
-            Ij[(size_t)i * len + c] = -v / Lj[(size_t)i * len + i];
-        }
+}
+
+// G^{-1} = L^{-T} L^{-1} from the FP64 factor, in the arithmetic TI: FP64 for FP64 storage; FP32 for the
+// FP32 inner solves of the mixed-precision form, where only the FP32 inverse is used.  (An approximate
+// inverse changes the rate of the iteration, not its fixed point: the update vanishes exactly when the
+// block residual does.)  One CTA per block, 64 x 64 tiles in shared memory:
+//   1. Linv block row by block row: D = (L_II)^{-1} by substitution in shared memory, then
+//      Linv_IJ = -D (sum_{K=J}^{I-1} L_IK Linv_KJ) for J < I (tile products);
+//   2. Ginv_AB = sum_{C >= max(A,B)} Linv_CA^T Linv_CB for A <= B, mirrored.
+// Blocks whose factor failed (NaN) give NaN.
+constexpr int IT = 64;          // tile
+constexpr int ITP = IT + 1;     // padded leading dimension in shared memory
+constexpr int INV_NT = 256;
+
+template <typename TI>
+__device__ __forceinline__ void tile_load_f64(TI *dst, const double *src, int ld, int r0, int c0, int len) {
+    for (int e = threadIdx.x; e < IT * IT; e += INV_NT) {
+        const int r = e / IT, c = e % IT;
+        const int gr = r0 + r, gc = c0 + c;
+        dst[r * ITP + c] = (gr < len && gc < len) ? (TI)src[(size_t)gr * ld + gc] : (TI)0;
     }
+}
+template <typename TI>
+__device__ __forceinline__ void tile_load(TI *dst, const TI *src, int ld, int r0, int c0, int len) {
+    for (int e = threadIdx.x; e < IT * IT; e += INV_NT) {
+        const int r = e / IT, c = e % IT;
+        const int gr = r0 + r, gc = c0 + c;
+        dst[r * ITP + c] = (gr < len && gc < len) ? src[(size_t)gr * ld + gc] : (TI)0;
+    }
+}
+// acc += op(A) B with op(A) = A or A^T; thread (ty, tx) owns rows ty*4.., columns tx*4..
+template <typename TI, bool TRANS_A>
+__device__ __forceinline__ void tile_mma(TI (&acc)[4][4], const TI *A, const TI *B) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 4
+    for (int k = 0; k < IT; ++k) {
+        TI a[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = TRANS_A ? A[k * ITP + ty * 4 + u] : A[(ty * 4 + u) * ITP + k];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) bv[v] = B[k * ITP + tx * 4 + v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * bv[v];
+    }
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(INV_NT) inverse_kernel(int64_t rows, int s, const double *__restrict__ L,
+                                                         TI *__restrict__ Linv, TI *__restrict__ Ginv) {
+    const int j = blockIdx.x;
+    const int len = (int)min64(s, rows - (int64_t)j * s);
+    const double *Lj = L + (size_t)j * s * s;
+    TI *Xj = Linv + (size_t)j * s * s;
+    TI *Vj = Ginv + (size_t)j * s * s;
+    extern __shared__ __align__(16) unsigned char inv_smem[];
+    TI *sA = (TI *)inv_smem;       // IT x ITP each
+    TI *sB = sA + IT * ITP;
+    TI *sD = sB + IT * ITP;
+    TI *sT = sD + IT * ITP;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (isnan(Lj[0])) {
+        for (int e = threadIdx.x; e < len * len; e += INV_NT) Vj[e] = (TI)NAN;
+        return;
+    }
+    const int nt = (len + IT - 1) / IT;
+    for (int I = 0; I < nt; ++I) {
+        // D = inverse of the diagonal tile (lower triangular), by columns in shared memory
+        tile_load_f64<TI>(sA, Lj, len, I * IT, I * IT, len);
+        __syncthreads();
+        const int tl = min(IT, len - I * IT);
+        for (int e = threadIdx.x; e < IT * IT; e += INV_NT) sD[(e / IT) * ITP + e % IT] = (TI)0;
+        __syncthreads();
+        if (threadIdx.x < tl) {
+            const int c = threadIdx.x;
+            sD[c * ITP + c] = (TI)1 / sA[c * ITP + c];
+            for (int i = c + 1; i < tl; ++i) {
+                TI v = (TI)0;
+                for (int k = c; k < i; ++k) v += sA[i * ITP + k] * sD[k * ITP + c];
+                sD[i * ITP + c] = -v / sA[i * ITP + i];
+            }
+        }
+        __syncthreads();
+        // Linv_II = D
+        for (int e = threadIdx.x; e < IT * IT; e += INV_NT) {
+            const int r = e / IT, c = e % IT;
+            if (r < tl && c < tl) Xj[(size_t)(I * IT + r) * len + I * IT + c] = sD[r * ITP + c];
+        }
+        // Linv_IJ = -D sum_K L_IK Linv_KJ
+        for (int J = 0; J < I; ++J) {
+            TI acc[4][4] = {};
+            for (int Kt = J; Kt < I; ++Kt) {
+                __syncthreads();
+                tile_load_f64<TI>(sA, Lj, len, I * IT, Kt * IT, len);
+                tile_load<TI>(sB, Xj, len, Kt * IT, J * IT, len);
+                __syncthreads();
+                tile_mma<TI, false>(acc, sA, sB);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) sT[(ty * 4 + u) * ITP + tx * 4 + v] = acc[u][v];
+            __syncthreads();
+            TI out[4][4] = {};
+            tile_mma<TI, false>(out, sD, sT);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = I * IT + ty * 4 + u, c = J * IT + tx * 4 + v;
+                    if (r < len && c < len) Xj[(size_t)r * len + c] = -out[u][v];
+                }
+        }
+        // upper part of block row I is zero
+        for (int e = threadIdx.x; e < tl * len; e += INV_NT) {
+            const int r = I * IT + e / len, c = e % len;
+            if (c >= (I + 1) * IT) Xj[(size_t)r * len + c] = (TI)0;
+        }
+        __syncthreads();
+    }
+    __threadfence_block();
     __syncthreads();
-    // Ginv[a][b] = sum_{c >= max(a,b)} Linv[c][a] Linv[c][b]
-    for (int e = threadIdx.x; e < len * len; e += blockDim.x) {
-        int a = e / len, b = e % len;
-        if (b < a) continue;
-        double v = 0.0;
-        for (int c = b; c < len; ++c) v += Ij[(size_t)c * len + a] * Ij[(size_t)c * len + b];
-        Vj[(size_t)a * len + b] = v;
-        Vj[(size_t)b * len + a] = v;
-        if (Ginv32) {
-            Ginv32[(size_t)j * s * s + (size_t)a * len + b] = (float)v;
-            Ginv32[(size_t)j * s * s + (size_t)b * len + a] = (float)v;
+    // Ginv_AB = sum_{C >= B} Linv_CA^T Linv_CB  (A <= B), mirrored
+    for (int A = 0; A < nt; ++A) {
+        for (int B = A; B < nt; ++B) {
+            TI acc[4][4] = {};
+            for (int C = B; C < nt; ++C) {
+                __syncthreads();
+                tile_load<TI>(sA, Xj, len, C * IT, A * IT, len);
+                tile_load<TI>(sB, Xj, len, C * IT, B * IT, len);
+                __syncthreads();
+                tile_mma<TI, true>(acc, sA, sB);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = A * IT + ty * 4 + u, c = B * IT + tx * 4 + v;
+                    if (r < len && c < len) {
+                        Vj[(size_t)r * len + c] = acc[u][v];
+                        Vj[(size_t)c * len + r] = acc[u][v];
+                    }
+                }
         }
     }
 }
@@ -270,8 +410,8 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
         }                                                                    \
     } while (0)
     KPP_TRY(cudaMalloc(&F.L, nb * blk * sizeof(double)));
-    KPP_TRY(cudaMalloc(&F.Ginv, nb * blk * sizeof(double)));
-    if (A.dtype != KPP_F64) KPP_TRY(cudaMalloc(&F.Ginv32, nb * blk * sizeof(float)));
+    if (A.dtype == KPP_F64) KPP_TRY(cudaMalloc(&F.Ginv, nb * blk * sizeof(double)));
+    else KPP_TRY(cudaMalloc(&F.Ginv32, nb * blk * sizeof(float)));
     KPP_TRY(cudaMalloc(&G, nb * blk * sizeof(double)));
     KPP_TRY(cudaMalloc(&Linv, nb * blk * sizeof(double)));
     KPP_TRY(cudaMalloc(&bad, sizeof(int)));
@@ -291,7 +431,19 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
         else launch_principal<__nv_bfloat16>(A.data, A.ld, rows, s, lam, G, st);
     }
     KPP_TRY(cudaGetLastError());
-    cholesky_inverse_kernel<<<(unsigned)nb, 512, 0, st>>>(rows, s, G, F.L, Linv, F.Ginv, F.Ginv32, bad);
+    KPP_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(CHOL_PB * s * sizeof(double))));
+    cholesky_kernel<<<(unsigned)nb, CHOL_NT, CHOL_PB * s * sizeof(double), st>>>(rows, s, G, F.L, bad);
+    KPP_TRY(cudaGetLastError());
+    if (A.dtype == KPP_F64) {
+        const int sm64 = 4 * IT * ITP * (int)sizeof(double);
+        KPP_TRY(cudaFuncSetAttribute(inverse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
+        inverse_kernel<double><<<(unsigned)nb, INV_NT, sm64, st>>>(rows, s, F.L, Linv, F.Ginv);
+    } else {
+        const int sm32 = 4 * IT * ITP * (int)sizeof(float);
+        KPP_TRY(cudaFuncSetAttribute(inverse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32));
+        inverse_kernel<float><<<(unsigned)nb, INV_NT, sm32, st>>>(rows, s, F.L, (float *)Linv, F.Ginv32);
+    }
     KPP_TRY(cudaGetLastError());
     {
         int hb = 0;

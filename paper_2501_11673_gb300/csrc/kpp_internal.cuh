@@ -55,6 +55,21 @@ __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ double widen(float v) { return (double)v; }
 __device__ __forceinline__ double widen(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
+// Exact FP32 -> FP64 widening with integer operations (rebias the exponent, shift the mantissa), so
+// that an FP64-bound loop spends its FP64 pipe on FMAs only.  Zero and subnormal inputs (exponent 0)
+// take the conversion instruction; inf / NaN do not occur in a valid matrix.
+__device__ __forceinline__ double widen_int(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u) return (double)f;
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    const uint32_t lo = (u & 7u) << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen_fast(double v) { return v; }
+__device__ __forceinline__ double widen_fast(float v) { return widen_int(v); }
+__device__ __forceinline__ double widen_fast(__nv_bfloat16 v) { return widen_int(__bfloat162float(v)); }
+
 template <typename T> __device__ __forceinline__ T load_as(const double v);
 template <> __device__ __forceinline__ double load_as<double>(const double v) { return v; }
 template <> __device__ __forceinline__ float load_as<float>(const double v) { return (float)v; }

@@ -149,15 +149,16 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SysArgs *__restrict_
                         s_r[e] = v;
                     }
                 } else {
+                    // one warp per entry: lanes sum strided partials, then a fixed shuffle tree
                     TC *rbuf = (TC *)sa.rbuf;
-                    for (int e = g * NT + threadIdx.x; e < len * KP; e += cm.G * NT) {
+                    for (int e = g * NW + warp; e < len * KP; e += cm.G * NW) {
                         const int a = e / KP, c = e % KP;
                         TC v = (TC)0;
-                        if (c < k) {
-                            for (int h = 0; h < cm.G; ++h) v += __ldcg(part + ((size_t)h * s + a) * KP + c);
-                            v -= b[(S0 + a) * k + c];
-                        }
-                        rbuf[e] = v;
+                        if (c < k)
+                            for (int h = lane; h < cm.G; h += 32) v += __ldcg(part + ((size_t)h * s + a) * KP + c);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0) rbuf[e] = (c < k) ? v - b[(S0 + a) * k + c] : (TC)0;
                     }
                     if (!group_barrier(gs)) break;
                     for (int e = threadIdx.x; e < len * KP; e += NT) s_r[e] = __ldcg(rbuf + e);
@@ -343,20 +344,75 @@ finish:
 // ---------------------------------------------------------------------------------------------
 // Standalone FP64 residual r = b - A x (rows x k) with per-CTA partial sums of |r|^2 (fixed grid and
 // fixed order: deterministic).  Optionally stores r rounded to FP32 (the inner right-hand side of a
-// refinement step).  Warp per row, lanes over columns.
+// refinement step).  Warp per row; each lane reads 16-byte vectors of the row (8 bf16 / 4 fp32 /
+// 2 fp64 entries), several in flight; x comes from shared memory when it fits (k = 1, cols <= 24576).
+// Stored entries are widened exactly and every product and sum is FP64.
 // ---------------------------------------------------------------------------------------------
+template <typename TA> struct Vec16;
+template <> struct Vec16<double> { static constexpr int n = 2; };
+template <> struct Vec16<float> { static constexpr int n = 4; };
+template <> struct Vec16<__nv_bfloat16> { static constexpr int n = 8; };
+
+constexpr int RES_SMEM_COLS = 24576;
+
 template <typename TA>
 __global__ void __launch_bounds__(256) residual_kernel(const TA *__restrict__ A, int64_t lda, int64_t rows,
                                                        int64_t cols, int k, const double *__restrict__ b,
                                                        const double *__restrict__ x, float *__restrict__ r32,
                                                        double *__restrict__ part /* gridDim.x x k */) {
+    constexpr int V = Vec16<TA>::n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    extern __shared__ double xs[];
     __shared__ double s_acc[8][32];
+    const bool vec_ok = ((lda * (int64_t)sizeof(TA)) % 16 == 0) && (((uintptr_t)A & 15) == 0);
+    const bool x_in_smem = (k == 1) && x && cols <= RES_SMEM_COLS;
+    if (x_in_smem) {
+        for (int64_t i = threadIdx.x; i < cols; i += blockDim.x) xs[i] = x[i];
+        __syncthreads();
+    }
     double acc2[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) acc2[c] = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < rows; i += (int64_t)gridDim.x * 8) {
         const TA *row = A + i * lda;
+        if (k == 1) {
+            double v = 0.0;
+            if (x) {
+                if (vec_ok) {
+                    const int64_t nvec = cols / V;
+                    const uint4 *rv = (const uint4 *)row;
+                    int64_t q = lane;
+#pragma unroll 1
+                    for (; q + 96 < nvec; q += 128) {
+                        uint4 w[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) w[u] = __ldg(rv + q + 32 * u);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const TA *e = (const TA *)&w[u];
+                            const int64_t c0 = (q + 32 * u) * V;
+#pragma unroll
+                            for (int z = 0; z < V; ++z) v = fma(widen_fast(e[z]), x_in_smem ? xs[c0 + z] : x[c0 + z], v);
+                        }
+                    }
+                    for (; q < nvec; q += 32) {
+                        const uint4 w = __ldg(rv + q);
+                        const TA *e = (const TA *)&w;
+#pragma unroll
+                        for (int z = 0; z < V; ++z) v = fma(widen_fast(e[z]), x_in_smem ? xs[q * V + z] : x[q * V + z], v);
+                    }
+                    for (int64_t col = nvec * V + lane; col < cols; col += 32) v = fma(widen(row[col]), x[col], v);
+                } else {
+                    for (int64_t col = lane; col < cols; col += 32) v = fma(widen(row[col]), x[col], v);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            const double r = b[i] - v;
+            if (lane == 0 && r32) r32[i] = (float)r;
+            acc2[0] += r * r;
+            continue;
+        }
         for (int c0 = 0; c0 < k; c0 += 8) {
             double v[8];
 #pragma unroll
@@ -392,6 +448,16 @@ __global__ void __launch_bounds__(256) residual_kernel(const TA *__restrict__ A,
         for (int w = 0; w < 8; ++w) t += s_acc[w][threadIdx.x];
         part[(size_t)blockIdx.x * k + threadIdx.x] = t;
     }
+}
+
+template <typename TA>
+static void launch_res_t(const kpp_matrix &A, int k, const double *b, const double *x, float *r32, double *part,
+                         int grid, cudaStream_t st) {
+    const bool sm = (k == 1) && x && A.cols <= RES_SMEM_COLS;
+    const size_t smem = sm ? (size_t)A.cols * sizeof(double) : 0;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(residual_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    residual_kernel<TA><<<grid, 256, smem, st>>>((const TA *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part);
 }
 
 __global__ void axpy_f32_to_f64_kernel(int64_t n, const float *__restrict__ d, double *__restrict__ x) {
@@ -469,33 +535,15 @@ int residual_grid() { return 4 * sm_count(); }
 
 cudaError_t launch_residual(const kpp_matrix &A, int k, const double *b, const double *x, float *r32, double *part,
                             cudaStream_t st) {
-    const int grid = residual_grid();
-    switch (A.dtype) {
-        case KPP_F64:
-            residual_kernel<double><<<grid, 256, 0, st>>>((const double *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part);
-            break;
-        case KPP_F32:
-            residual_kernel<float><<<grid, 256, 0, st>>>((const float *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part);
-            break;
-        default:
-            residual_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)A.data, A.ld, A.rows, A.cols,
-                                                                 k, b, x, r32, part);
-    }
-    return cudaGetLastError();
+    return launch_residual_grid(A, k, b, x, r32, part, residual_grid(), st);
 }
 
 cudaError_t launch_residual_grid(const kpp_matrix &A, int k, const double *b, const double *x, float *r32,
                                  double *part, int grid, cudaStream_t st) {
     switch (A.dtype) {
-        case KPP_F64:
-            residual_kernel<double><<<grid, 256, 0, st>>>((const double *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part);
-            break;
-        case KPP_F32:
-            residual_kernel<float><<<grid, 256, 0, st>>>((const float *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part);
-            break;
-        default:
-            residual_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)A.data, A.ld, A.rows, A.cols,
-                                                                 k, b, x, r32, part);
+        case KPP_F64: launch_res_t<double>(A, k, b, x, r32, part, grid, st); break;
+        case KPP_F32: launch_res_t<float>(A, k, b, x, r32, part, grid, st); break;
+        default: launch_res_t<__nv_bfloat16>(A, k, b, x, r32, part, grid, st);
     }
     return cudaGetLastError();
 }

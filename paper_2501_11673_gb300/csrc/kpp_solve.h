@@ -68,7 +68,7 @@ cudaError_t launch_f64_to_f32(int64_t n, const double *a, float *o, cudaStream_t
 cudaError_t launch_negate_copy(size_t n, const void *src, void *dst, bool f64, cudaStream_t st);
 
 // Small-block kernel (kpp_solve2.cu).
-bool solve2_eligible(const kpp_matrix &A, int s, int64_t CW, int KP, bool f64);
+bool solve2_eligible(const kpp_matrix &A, int s, int64_t CW, int KP, bool f64, bool cd, int G);
 bool make_tmap_2d(void *out, const void *base, int dtype, uint64_t cols, uint64_t rows, uint64_t ld_elems,
                   uint32_t box_cols, uint32_t box_rows);
 size_t sys2_bytes();

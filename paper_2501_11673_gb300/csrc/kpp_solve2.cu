@@ -30,16 +30,19 @@ struct alignas(128) Sys2 {
 };
 
 struct Smem2 {           // byte offsets into dynamic shared memory
-    int tile[2], ginv[2], xc, mc, rxc, rmc, r, y, yp, red, total;
+    int tile[2], ginv[2], xc, mc, rxc, rmc, r, y, yp, red, grows, total;
 };
+
+// rows of G^{-1} one CTA applies in distributed-y mode: a = g + G * w, w = 0 .. dy_rows-1
+__host__ __device__ inline int dy_rows(int s, int G) { return (s + G - 1) / G; }
 
 __host__ __device__ inline int align128(int v) { return (v + 127) / 128 * 128; }
 
-__host__ __device__ inline Smem2 smem2_layout(int s, int64_t CW, int KP, int ta_size, int tc_size) {
+__host__ __device__ inline Smem2 smem2_layout(int s, int64_t CW, int KP, int ta_size, int tc_size, bool dist_y) {
     Smem2 L;
     int o = 0;
     const int tile = align128((int)(s * CW * ta_size));
-    const int ginv = align128(s * s * tc_size);
+    const int ginv = dist_y ? 0 : align128(s * s * tc_size);
     const int vec = align128((int)(CW * KP * tc_size));
     L.tile[0] = o; o += tile;
     L.tile[1] = o; o += tile;
@@ -53,11 +56,17 @@ __host__ __device__ inline Smem2 smem2_layout(int s, int64_t CW, int KP, int ta_
     L.y = o; o += align128(s * KP * tc_size);
     L.yp = o; o += align128(NT * KP * tc_size);
     L.red = o; o += align128(NW * 32 * KP * tc_size);
+    L.grows = o;
     L.total = o;
     return L;
 }
 
-template <typename TA, typename TC, int KP, bool CD>
+__host__ __device__ inline int smem2_total(int s, int64_t CW, int KP, int ta_size, int tc_size, bool dist_y, int G) {
+    const Smem2 L = smem2_layout(s, CW, KP, ta_size, tc_size, dist_y);
+    return L.total + (dist_y ? align128(dy_rows(s, G) * s * tc_size) : 0);
+}
+
+template <typename TA, typename TC, int KP, bool CD, bool DY>
 __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ systems, Common cm) {
     const Sys2 &sys = systems[blockIdx.x / cm.G];
     const SysArgs sa = sys.a;
@@ -71,7 +80,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
     const TC *__restrict__ Ginv = (const TC *)sa.Ginv;
 
     extern __shared__ __align__(128) unsigned char sm[];
-    const Smem2 L = smem2_layout(s, cm.CW, KP, (int)sizeof(TA), (int)sizeof(TC));
+    const Smem2 L = smem2_layout(s, cm.CW, KP, (int)sizeof(TA), (int)sizeof(TC), DY);
     TA *tile[2] = {(TA *)(sm + L.tile[0]), (TA *)(sm + L.tile[1])};
     TC *ginv[2] = {(TC *)(sm + L.ginv[0]), (TC *)(sm + L.ginv[1])};
     TC *xc = (TC *)(sm + L.xc);
@@ -82,7 +91,11 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
     TC *s_y = (TC *)(sm + L.y);
     TC *s_yp = (TC *)(sm + L.yp);
     TC *s_red = (TC *)(sm + L.red);
+    TC *s_grows = (TC *)(sm + L.grows);  // distributed y: my rows of G^{-1} for the current step
     __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar_g;
+    __shared__ int s_gpending;
+    __shared__ unsigned s_gphase;
     __shared__ ColState st[KP];
     __shared__ double s_part[NW * KP];
     __shared__ double s_rn2[KP];
@@ -116,10 +129,13 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
     if (threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
+        mbar_init(&mbar_g, 1);
         fence_mbar_init();
         tensormap_acquire(tmap);
         s_pending[0] = s_pending[1] = 0;
         s_phase[0] = s_phase[1] = 0;
+        s_gpending = 0;
+        s_gphase = 0;
         s_fail = 0;
     }
     {
@@ -165,12 +181,30 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
         auto issue = [&](int64_t tt, int bf) {
             const int j = draw_block(cm.seed, tt, sa.sys_id, nb);
             const int len = (int)min64(s, rows - (int64_t)j * s);
-            const unsigned gbytes = (unsigned)((len * len * (int)sizeof(TC) + 15) / 16 * 16);
-            const unsigned abytes = (unsigned)(s * CWs * (int)sizeof(TA));
+            const unsigned gbytes = DY ? 0u : (unsigned)((len * len * (int)sizeof(TC) + 15) / 16 * 16);
+            const int box = s < 256 ? s : 256;
+            const int nbox = (s + box - 1) / box;
+            const unsigned abytes = (unsigned)(nbox * box * CWs * (int)sizeof(TA));
             mbar_arrive_expect_tx(&mbar[bf], abytes + gbytes);
-            tma_load_2d(tile[bf], tmap, (int)c0, j * s, &mbar[bf]);
-            bulk_load(ginv[bf], Ginv + (size_t)j * s * s, gbytes, &mbar[bf]);
+            for (int q = 0; q < nbox; ++q)
+                tma_load_2d(tile[bf] + (size_t)q * box * CWs, tmap, (int)c0, j * s + q * box, &mbar[bf]);
+            if (gbytes) bulk_load(ginv[bf], Ginv + (size_t)j * s * s, gbytes, &mbar[bf]);
             s_pending[bf] = 1;
+        };
+        // distributed y: bulk-copy my rows a = g + G w of G^{-1}_{j(tt)} (each row len values, padded to 16 B)
+        auto issue_rows = [&](int64_t tt) {
+            const int j = draw_block(cm.seed, tt, sa.sys_id, nb);
+            const int len = (int)min64(s, rows - (int64_t)j * s);
+            const unsigned rb = (unsigned)((len * (int)sizeof(TC) + 15) / 16 * 16);
+            const unsigned rbs = (unsigned)(s * sizeof(TC));  // row stride in the shared buffer
+            int nr = 0;
+            for (int a = g; a < len; a += cm.G) ++nr;
+            mbar_arrive_expect_tx(&mbar_g, rb * (unsigned)nr);
+            int w = 0;
+            for (int a = g; a < len; a += cm.G, ++w)
+                bulk_load((unsigned char *)s_grows + (size_t)w * rbs, Ginv + (size_t)j * s * s + (size_t)a * len, rb,
+                          &mbar_g);
+            s_gpending = 1;
         };
         // wait for buffer bf (all threads); false on timeout
         auto wait_buf = [&](int bf) -> bool {
@@ -218,6 +252,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
         if (threadIdx.x == 0 && t < cm.max_iters) {
             issue(t, (int)(t & 1));
             if (t + 1 < cm.max_iters) issue(t + 1, (int)((t + 1) & 1));
+            if (DY) issue_rows(t);
         }
         if (!CD && t < cm.max_iters) {
             if (!wait_buf((int)(t & 1))) goto drain;
@@ -234,14 +269,32 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             // ---- block residual r ----
             if (!CD) {
                 const TC *part = (const TC *)sa.part + (size_t)bf * cm.G * s * KP;
-                for (int e = threadIdx.x; e < len * KP; e += NT) {
-                    const int a = e / KP, c = e % KP;
-                    TC v = (TC)0;
-                    if (c < k) {
-                        for (int h = 0; h < cm.G; ++h) v += __ldcg(part + ((size_t)h * s + a) * KP + c);
-                        v -= b[(S0 + a) * k + c];
+                if (cm.reduce_redundant) {
+                    for (int e = threadIdx.x; e < len * KP; e += NT) {
+                        const int a = e / KP, c = e % KP;
+                        TC v = (TC)0;
+                        if (c < k) {
+                            for (int h = 0; h < cm.G; ++h) v += __ldcg(part + ((size_t)h * s + a) * KP + c);
+                            v -= b[(S0 + a) * k + c];
+                        }
+                        s_r[e] = v;
                     }
-                    s_r[e] = v;
+                } else {
+                    // warp per entry across the group (lanes over partials, fixed tree), then exchange
+                    TC *rbuf = (TC *)sa.rbuf;
+                    for (int e = g * NW + warp; e < len * KP; e += cm.G * NW) {
+                        const int a = e / KP, c = e % KP;
+                        TC v = (TC)0;
+                        if (c < k) {
+#pragma unroll 8
+                            for (int h = lane; h < cm.G; h += 32) v += __ldcg(part + ((size_t)h * s + a) * KP + c);
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0) rbuf[e] = (c < k) ? v - b[(S0 + a) * k + c] : (TC)0;
+                    }
+                    if (!group_barrier(gs)) break;
+                    for (int e = threadIdx.x; e < len * KP; e += NT) s_r[e] = __ldcg(rbuf + e);
                 }
             } else {
                 for (int e = threadIdx.x; e < len * KP; e += NT) {
@@ -262,8 +315,44 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
                 if (lane == 0) s_rn2[c] = v;
             }
 
-            // ---- y = G^{-1} r, every CTA (G^{-1} symmetric: read by columns) ----
-            {
+            // ---- y = G^{-1} r ----
+            if (DY) {
+                // rows of G^{-1} spread over the group (warp per row), then exchange
+                __syncthreads();
+                TC *ybuf = (TC *)sa.ybuf;
+                if (threadIdx.x == 0) {
+                    if (!mbar_wait_bounded(&mbar_g, s_gphase, cm.timeout_ns)) {
+                        s_fail = 1;
+                        group_fail(gs, KPP_ERR_TIMEOUT);
+                    } else {
+                        s_gphase ^= 1u;
+                        s_gpending = 0;
+                    }
+                }
+                __syncthreads();
+                if (s_fail) break;
+                int w = warp;
+                for (int a = g + cm.G * warp; a < len; a += cm.G * NW, w += NW) {
+                    TC acc[KP];
+#pragma unroll
+                    for (int c = 0; c < KP; ++c) acc[c] = (TC)0;
+                    const TC *grow = s_grows + (size_t)w * s;
+                    for (int d = lane; d < len; d += 32) {
+                        const TC gval = grow[d];
+#pragma unroll
+                        for (int c = 0; c < KP; ++c) acc[c] = tfma<TC>(gval, s_r[d * KP + c], acc[c]);
+                    }
+                    warp_reduce<TC, KP>(acc);
+                    if (lane == 0)
+#pragma unroll
+                        for (int c = 0; c < KP; ++c) ybuf[(size_t)a * KP + c] = acc[c];
+                }
+                __syncthreads();
+                if (threadIdx.x == 0 && t + 1 < cm.max_iters) issue_rows(t + 1);
+                if (!group_barrier(gs)) break;
+                for (int e = threadIdx.x; e < len * KP; e += NT) s_y[e] = __ldcg(ybuf + e);
+                __syncthreads();
+            } else {
                 const TC *gv = ginv[bf];
                 const int RG = min(NT, (len + 31) / 32 * 32);
                 const int Q = NT / RG;
@@ -431,6 +520,11 @@ drain:
                 else group_fail(gs, KPP_ERR_TIMEOUT);
                 s_pending[bf] = 0;
             }
+        if (DY && s_gpending) {
+            if (mbar_wait_bounded(&mbar_g, s_gphase, cm.timeout_ns)) s_gphase ^= 1u;
+            else group_fail(gs, KPP_ERR_TIMEOUT);
+            s_gpending = 0;
+        }
     }
     __syncthreads();
     if (g == 0 && threadIdx.x < k) {
@@ -482,23 +576,34 @@ bool make_tmap_2d(void *out, const void *base, int dtype, uint64_t cols, uint64_
     return r == CUDA_SUCCESS;
 }
 
-size_t solve2_smem_bytes(int s, int64_t CW, int KP, int ta_size, int tc_size) {
-    return (size_t)smem2_layout(s, CW, KP, ta_size, tc_size).total;
+size_t solve2_smem_bytes(int s, int64_t CW, int KP, int ta_size, int tc_size, bool dist_y, int G) {
+    return (size_t)smem2_total(s, CW, KP, ta_size, tc_size, dist_y, G);
 }
 
-bool solve2_eligible(const kpp_matrix &A, int s, int64_t CW, int KP, bool f64) {
+// G^{-1} double-buffered in shared memory when it fits; otherwise its rows are applied across the group.
+static bool solve2_dist_y(int s, int64_t CW, int KP, int es, int tcs) {
+    return solve2_smem_bytes(s, CW, KP, es, tcs, false, 1) > 200 * 1024;
+}
+
+bool solve2_eligible(const kpp_matrix &A, int s, int64_t CW, int KP, bool f64, bool cd, int G) {
     const int es = A.dtype == KPP_F64 ? 8 : (A.dtype == KPP_F32 ? 4 : 2);
     const int tcs = f64 ? 8 : 4;
-    if (s < 2 || s > 256 || (s & 1) || CW > 256 || CW < 1) return false;
+    if (s < 2 || s > 1024 || (s & 1) || CW > 256 || CW < 1) return false;
+    if (s > 256 && (s % 256)) return false;  // whole 256-row boxes
     if (((uintptr_t)A.data & 15) || ((A.ld * es) & 15) || ((CW * es) & 15)) return false;
-    if (solve2_smem_bytes(s, CW, KP, es, tcs) > 200 * 1024) return false;
+    const bool dy = solve2_dist_y(s, CW, KP, es, tcs);
+    if (dy && cd) return false;  // CD++ with large blocks stays on the general kernel
+    if (solve2_smem_bytes(s, CW, KP, es, tcs, dy, G) > 200 * 1024) return false;
+    // rows of G^{-1} are bulk-copied: every row offset must stay 16-byte aligned, so no ragged block
+    if (dy && ((s * tcs) % 16 || A.rows % s)) return false;
     return encode_fn() != nullptr;
 }
 
 template <typename TA, typename TC, int KP, bool CD>
 static cudaError_t launch2_t(const void *d_sys, int nsys, const Common &cm, cudaStream_t st) {
-    auto kern = solve2_kernel<TA, TC, KP, CD>;
-    const size_t smem = solve2_smem_bytes(cm.s, cm.CW, KP, sizeof(TA), sizeof(TC));
+    const bool dy = solve2_dist_y(cm.s, cm.CW, KP, sizeof(TA), sizeof(TC));
+    auto kern = dy ? solve2_kernel<TA, TC, KP, CD, true> : solve2_kernel<TA, TC, KP, CD, false>;
+    const size_t smem = solve2_smem_bytes(cm.s, cm.CW, KP, sizeof(TA), sizeof(TC), dy, cm.G);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

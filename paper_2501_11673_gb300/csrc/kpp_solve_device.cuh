@@ -49,7 +49,7 @@ __device__ bool true_residual_phase(const SysArgs &sa, const Common &cm, int g, 
         for (int c = 0; c < KP; ++c) v[c] = 0.0;
         const TA *row = A + i * sa.lda;
         for (int64_t col = lane; col < cm.cols; col += 32) {
-            double a = widen(row[col]);
+            double a = widen_fast(row[col]);
 #pragma unroll
             for (int c = 0; c < KP; ++c)
                 if (c < k) v[c] = fma(a, (double)__ldcg(x + col * k + c), v[c]);

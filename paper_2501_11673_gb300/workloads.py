@@ -170,3 +170,78 @@ def serving_requests(n_req: int = 1024, n_mats: int = 32, mean_gap_ms: float = 2
     mats = rng.integers(0, n_mats, n_req)
     ks = rng.integers(k_lo, k_hi + 1, n_req)
     return [(float(t[i]), int(mats[i]), int(ks[i]), 1000 + i) for i in range(n_req)]
+
+
+# ---------------------------------------------------------------------------------------------
+# Device-side generators (torch, seeded) for the workloads too large to build on the host.
+# Same recipes as above; the stored (rounded) matrix is the system and b is formed in FP64 from it.
+# ---------------------------------------------------------------------------------------------
+
+def torch_haar(n: int, gen, device: str = "cuda"):
+    import torch
+    g = torch.randn(n, n, generator=gen, device=device, dtype=torch.float64)
+    q, r = torch.linalg.qr(g)
+    return q * torch.sign(torch.diagonal(r))[None, :]
+
+
+def torch_lowrank_ls(m: int, n: int, n_out: int, out_lo: float, out_hi: float, bulk_lo: float, bulk_hi: float,
+                     seed: int, dtype: str = "bf16", noise: float = 0.0, device: str = "cuda"):
+    """A = Z diag(d) V^T stored in `dtype` (Z_ij ~ N(0, 1/m), V Haar), x* ~ N(0, I), b = A_stored x* (FP64)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    v = torch_haar(n, gen, device)
+    out = torch.logspace(math.log10(out_hi), math.log10(out_lo), n_out, dtype=torch.float64, device=device)
+    bulk = torch.rand(n - n_out, generator=gen, device=device, dtype=torch.float64) * (bulk_hi - bulk_lo) + bulk_lo
+    d = torch.cat([out, torch.sort(bulk, descending=True).values])
+    dvt = (d[:, None] * v.T).to(torch.float32)
+    tdt = {"bf16": torch.bfloat16, "f32": torch.float32}[dtype]
+    A = torch.empty(m, n, dtype=tdt, device=device)
+    chunk = 16384
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for r0 in range(0, m, chunk):
+            z = torch.randn(min(chunk, m - r0), n, generator=gen, device=device, dtype=torch.float32)
+            A[r0:r0 + z.shape[0]] = (z @ dvt * (1.0 / math.sqrt(m))).to(tdt)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    x_star = torch.randn(n, generator=gen, device=device, dtype=torch.float64)
+    b = torch.empty(m, dtype=torch.float64, device=device)
+    for r0 in range(0, m, chunk):
+        b[r0:r0 + chunk] = A[r0:r0 + chunk].double() @ x_star
+    if noise:
+        b += noise * torch.randn(m, generator=gen, device=device, dtype=torch.float64)
+    return A, b, x_star, d
+
+
+def torch_gaussian_rows(m: int, n: int, n_big: int, scale: float, seed: int, k_rhs: int, dtype: str = "f32",
+                        device: str = "cuda"):
+    """Under-determined A (m x n, i.i.d. N(0,1), n_big seeded rows scaled), B ~ N(0, I) (m x k_rhs, FP64)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    tdt = {"bf16": torch.bfloat16, "f32": torch.float32}[dtype]
+    A = torch.randn(m, n, generator=gen, device=device, dtype=torch.float32)
+    rows = torch.randperm(m, generator=gen, device=device)[:n_big]
+    A[rows] *= scale
+    B = torch.randn(m, k_rhs, generator=gen, device=device, dtype=torch.float64)
+    return A.to(tdt), B, torch.sort(rows).values
+
+
+def torch_spd(n: int, n_out: int, out_lo: float, out_hi: float, bulk_lo: float, bulk_hi: float, seed: int,
+              dtype: str = "f64", device: str = "cuda"):
+    """Exactly symmetric A = U diag(sigma) U^T (U Haar) in `dtype`, built in FP64 on the device."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    u = torch_haar(n, gen, device)
+    out = torch.logspace(math.log10(out_hi), math.log10(out_lo), n_out, dtype=torch.float64, device=device)
+    bulk = torch.rand(n - n_out, generator=gen, device=device, dtype=torch.float64) * (bulk_hi - bulk_lo) + bulk_lo
+    sig = torch.cat([out, torch.sort(bulk, descending=True).values])
+    A = (u * sig[None, :]) @ u.T
+    A = 0.5 * (A + A.T)
+    tdt = {"bf16": torch.bfloat16, "f32": torch.float32, "f64": torch.float64}[dtype]
+    A = A.to(tdt)
+    A = 0.5 * (A + A.T)  # symmetric again after rounding (exact: a + a = 2a, halving is exact)
+    return A.contiguous(), sig

@@ -297,3 +297,35 @@ def test_tensor_core_gram_refuses_unaligned_rows_and_auto_falls_back(K):
     G, used = K.block_gram(A, 64, 0.0, engine=0)
     assert used == 1
     np.testing.assert_allclose(G.cpu().numpy()[:64 * 64].reshape(64, 64)[5, 3], 777.0)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_mixed_storage_factors_match_oracle(K, dtype):
+    """FP64 Cholesky of the tensor-core / CUDA-core Gram of the stored matrix, against the oracle's factor
+    of the same (widened) matrix; tolerance from the FP32 accumulation of the Gram."""
+    rng = np.random.default_rng(12)
+    m, n, s = 600, 1024, 128
+    A = W.round_to_storage(rng.standard_normal((m, n)), dtype)
+    P = K.Partition(m, s)
+    F = K.Factors(dev(A, torch.bfloat16 if dtype == "bf16" else torch.float32), P, 0.5, 0)
+    L = oracle.kpp_factor(A, s, 0.5)
+    for j in range(P.nb):
+        Lo = oracle.factor_block(L, j, m, s)
+        np.testing.assert_allclose(F.block(j), Lo, rtol=1e-4, atol=1e-4 * np.abs(Lo).max())
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_true_residual_is_exact_fp64_of_stored_entries(K, dtype):
+    """kpp_rel_residual widens stored entries exactly (integer rebias) and sums in FP64: compare with
+    numpy FP64 on the widened matrix, including zeros and subnormal-range bf16 entries."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((300, 520))
+    A[0, :10] = 0.0
+    A[1, :10] = 1e-39  # subnormal in fp32 / bf16
+    A[2, :10] = -3e-42
+    Ar = W.round_to_storage(A, dtype) if dtype == "bf16" else A.astype(np.float32).astype(np.float64)
+    x = rng.standard_normal(520)
+    b = Ar @ x + 1e-3 * rng.standard_normal(300)
+    got = K.rel_residual(dev(Ar, torch.bfloat16 if dtype == "bf16" else torch.float32), dev(b), dev(x))
+    want = np.linalg.norm(b - Ar @ x) / np.linalg.norm(b)
+    assert abs(got - want) <= 1e-12 * want
