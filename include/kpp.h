@@ -212,9 +212,12 @@ kpp_status cdpp_solve_noalloc(const kpp_matrix *A, const double *b, double *x, k
  * G_out: device FP64 buffer of nb * s * s doubles; block j is written at G_out + j*s*s as a len x len
  * row-major matrix (leading dimension len, len = rows of block j).  Only its lower triangle (with the
  * diagonal) is written; the caller owns G_out.
- * engine: 0 automatic (tensor cores for BF16 storage, CUDA cores otherwise), 1 CUDA cores with FP64
- * accumulation, 2 tcgen05 tensor cores with FP32 accumulation (kind::f16 for BF16; kind::tf32 for
- * FP32, i.e. TF32 products).  *engine_used (may be NULL) receives 1 or 2.
+ * engine: 0 automatic (tensor cores for BF16 and FP32 storage -- FP32 as engine 3 -- CUDA cores for
+ * FP64), 1 CUDA cores with FP64 accumulation, 2 tcgen05 tensor cores with FP32 accumulation and one
+ * product per element pair (kind::f16 for BF16, exact products; kind::tf32 for FP32, i.e. products of
+ * 11-bit mantissas), 3 FP32 storage only: each value split as hi + lo with hi its TF32 rounding, and
+ * hi*hi + hi*lo + lo*hi on kind::tf32 (products good to about 2^-22).  *engine_used (may be NULL)
+ * receives 1, 2 or 3.
  * Errors: KPP_ERR_ARG; KPP_ERR_UNSUPPORTED when engine 2 cannot take the matrix (FP64 storage, rows
  * not 16-byte aligned); KPP_ERR_CUDA.  Synchronises `stream`. */
 kpp_status kpp_block_gram(const kpp_matrix *A, int32_t s, double lambda, int32_t engine, double *G_out,

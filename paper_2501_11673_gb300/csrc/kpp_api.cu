@@ -168,8 +168,33 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
         if (cd3_smem_bytes(s, CW, KP, (int)tas, (int)tcs, f64) > 200 * 1024) v3 = false;
     }
     if (v3) v2 = false;
+    // wide FP32 / BF16 K++ systems: the streaming kernel (column chunks too wide for the small-block one)
+    bool v4 = !f64 && !cd && g_variant >= 2 && !v2 && KP <= 8 && s >= 2 && s <= 256;
+    if (v4) {
+        const int64_t TK = stream_tk(dtype);
+        for (int i = 0; v4 && i < nsys; ++i) {
+            const kpp_matrix &Ai = *sys[i].A;
+            if (((uintptr_t)Ai.data & 15) || ((Ai.ld * (int64_t)dtype_size(dtype)) & 15)) v4 = false;
+        }
+        if (A0.cols % TK) v4 = false;
+        const int per_sm = v4 ? stream_per_sm(dtype, s, KP) : 0;
+        int G4 = per_sm > 0 ? std::max(1, per_sm * sm_count() / nsys) : 0;
+        if (grid > 0) G4 = grid;
+        if (G4 < 1) v4 = false;
+        if (v4) {
+            int64_t CW4 = (A0.cols + G4 - 1) / G4;
+            CW4 = (CW4 + TK - 1) / TK * TK;
+            const int G4b = (int)((A0.cols + CW4 - 1) / CW4);
+            if (CW4 / TK < 6 || (int64_t)G4b * nsys > (int64_t)per_sm * sm_count()) {
+                v4 = false;
+            } else {
+                G = G4b;
+                CW = CW4;
+            }
+        }
+    }
     Common cm{};
-    cm.rows = A0.rows;
+    cm.rows = A0.rows;  // (filled after the kernel choice below)
     cm.cols = A0.cols;
     cm.s = s;
     cm.nb = nb;
@@ -187,7 +212,7 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     cm.timeout_ns = 2000000000ull;
 
     const size_t smem = solve_smem_bytes(s, KP, CW, tcs);
-    if (!v2 && smem > 220 * 1024) {
+    if (!v2 && !v3 && !v4 && smem > 220 * 1024) {
         set_error("shared memory %zu B exceeds the per-CTA limit (s=%d, k=%d, chunk=%lld)", smem, s, k, (long long)CW);
         return KPP_ERR_UNSUPPORTED;
     }
@@ -226,7 +251,7 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
         } else {
             a.Rx = a.Rm = nullptr;
         }
-        CUDA_OR(scr.alloc(&a.part, (v2 ? 2 : 1) * (size_t)G * s * KP * tcs), KPP_ERR_CUDA);
+        CUDA_OR(scr.alloc(&a.part, (v2 || v4 ? 2 : 1) * (size_t)G * s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc(&a.rbuf, (size_t)s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc(&a.ybuf, (size_t)s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc((void **)&a.rpart, (size_t)G * KP * sizeof(double)), KPP_ERR_CUDA);
@@ -238,7 +263,30 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
         a.sys_id = sys[i].sys_id;
         a.t0 = t0;
     }
-    if (v3) {
+    if (v4) {
+        const size_t sb = sys4_bytes();
+        h2.assign(sb * nsys, 0);
+        for (int i = 0; i < nsys; ++i) {
+            alignas(128) unsigned char tm[128];
+            const kpp_matrix &Ai = *sys[i].A;
+            if (!make_tmap_2d(tm, Ai.data, dtype, Ai.cols, Ai.rows, Ai.ld, (uint32_t)stream_tk(dtype), (uint32_t)s, true)) {
+                set_error("cuTensorMapEncodeTiled failed for system %d", i);
+                rc = KPP_ERR_CUDA;
+                goto cleanup;
+            }
+            const SysArgs &a = args[i];
+            sys4_fill(h2.data() + sb * i, tm, (const float *)a.b, (float *)a.x, (float *)a.m, (const float *)a.Ginv,
+                      (float *)a.part, a.rpart, a.sc, a.bar, a.err, a.sys_id, a.t0);
+        }
+        CUDA_OR(scr.alloc(&d_sys2, sb * nsys), KPP_ERR_CUDA);
+        if ((uintptr_t)d_sys2 & 127) {
+            set_error("descriptor buffer not 128-byte aligned");
+            rc = KPP_ERR_CUDA;
+            goto cleanup;
+        }
+        CUDA_OR(cudaMemcpyAsync(d_sys2, h2.data(), sb * nsys, cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
+        CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
+    } else if (v3) {
         const size_t sb = sys3_bytes();
         const size_t mb = cd3_mail_bytes(s, KP, f64);
         h2.assign(sb * nsys, 0);
@@ -294,7 +342,8 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     CUDA_OR(cudaEventCreate(&e1), KPP_ERR_CUDA);
     CUDA_OR(cudaEventRecord(e0, st), KPP_ERR_CUDA);
     {
-        cudaError_t le = v3   ? launch_cd3(dtype, d_sys2, nsys, cm, KP, st)
+        cudaError_t le = v4   ? launch_stream(dtype, d_sys2, nsys, cm, KP, st)
+                         : v3 ? launch_cd3(dtype, d_sys2, nsys, cm, KP, st)
                          : v2 ? launch_solve2(dtype, cd, d_sys2, nsys, cm, KP, st)
                               : launch_solve(dtype, f64, cd, d_args, nsys, cm, KP, st);
         if (le == cudaErrorCooperativeLaunchTooLarge) {
@@ -687,7 +736,7 @@ kpp_status kpp_set_kernel_variant(int32_t variant) {
 kpp_status kpp_block_gram(const kpp_matrix *A, int32_t s, double lambda, int32_t engine, double *G_out,
                           int32_t *engine_used, void *stream) {
     clear_error();
-    if (!matrix_ok(A) || s < 1 || s > 1024 || !G_out || engine < 0 || engine > 2) {
+    if (!matrix_ok(A) || s < 1 || s > 1024 || !G_out || engine < 0 || engine > 3) {
         set_error("kpp_block_gram: invalid argument");
         return KPP_ERR_ARG;
     }
@@ -695,7 +744,7 @@ kpp_status kpp_block_gram(const kpp_matrix *A, int32_t s, double lambda, int32_t
     const int used = block_gram(*A, s, lambda, G_out, engine, st);
     if (engine_used) *engine_used = used;
     if (used < 0) {
-        if (engine == 2) {
+        if (engine == 2 || engine == 3) {
             set_error("kpp_block_gram: the tensor-core Gram does not support this matrix (dtype, alignment)");
             return KPP_ERR_UNSUPPORTED;
         }

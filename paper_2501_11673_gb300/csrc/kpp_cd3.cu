@@ -116,8 +116,12 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
 
     extern __shared__ __align__(128) unsigned char sm[];
     const Smem3 L = smem3_layout(s, cm.CW, KP, (int)sizeof(TA), (int)sizeof(TC), USE_W);
-    TA *tile[2] = {(TA *)(sm + L.tile[0]), (TA *)(sm + L.tile[1])};
-    TC *ginv[2] = {(TC *)(sm + L.ginv[0]), (TC *)(sm + L.ginv[1])};
+    unsigned char *const tile0 = sm + L.tile[0];
+    const int tile_stride = L.tile[1] - L.tile[0];
+    unsigned char *const ginv0 = sm + L.ginv[0];
+    const int ginv_stride = L.ginv[1] - L.ginv[0];
+#define TILE(bf) ((TA *)(tile0 + (bf) * tile_stride))
+#define GINV(bf) ((TC *)(ginv0 + (bf) * ginv_stride))
     TC *xc = (TC *)(sm + L.xc);
     TC *mc = (TC *)(sm + L.mc);
     TC *rxc = (TC *)(sm + L.rxc);
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
     __shared__ double s_part[NW * KP];
     __shared__ double s_rn2[KP];
     __shared__ int s_stop, s_need, s_fail;
-    __shared__ int s_pending[2], s_glo[2];
+    __shared__ int s_pending[2], s_glo[2];  // (shared: indexed by the runtime buffer number)
     __shared__ unsigned s_phase[2];
     __shared__ TC s_beta[KP], s_keep[KP];
 
@@ -222,8 +226,8 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
             }
             const unsigned gbytes = (unsigned)(((ghi - glo) * len * (int)sizeof(TC) + 15) / 16 * 16);
             mbar_arrive_expect_tx(&mbar[bf], abytes + gbytes);
-            tma_load_2d(tile[bf], tmap, (int)c0, (int)S0, &mbar[bf]);
-            if (gbytes) bulk_load(ginv[bf], Ginv + (size_t)j * s * s + (size_t)glo * len, gbytes, &mbar[bf]);
+            tma_load_2d(TILE(bf), tmap, (int)c0, (int)S0, &mbar[bf]);
+            if (gbytes) bulk_load(GINV(bf), Ginv + (size_t)j * s * s + (size_t)glo * len, gbytes, &mbar[bf]);
             s_glo[bf] = glo;
             s_pending[bf] = 1;
         };
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
             // ---- y = G^{-1} r: all of it (FP32 path), or only my chunk's rows of the block (W path) ----
             const int64_t olo = max64(c0, S0), ohi = min64(c1, S0 + len);  // my columns inside S
             {
-                const TC *gv = ginv[bf];
+                const TC *gv = GINV(bf);
                 if (!USE_W) {
                     const int RG = min(NT, (len + 31) / 32 * 32);
                     const int Q = NT / RG;
@@ -361,14 +365,8 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
 
             // ---- u on my chunk: W tile^T r (W path) or A tile^T y; update the chunk state ----
             {
-                TC beta[KP], keep[KP];
-#pragma unroll
-                for (int c = 0; c < KP; ++c) {
-                    beta[c] = s_beta[c];
-                    keep[c] = s_keep[c];
-                }
                 const TC eta = (TC)cm.eta;
-                const TA *tl = tile[bf];
+                const TA *tl = TILE(bf);
                 const TC *vin = USE_W ? s_r : s_y;
                 for (int cg = 0; cg < cw; cg += 32) {
                     const int cc = cg + lane;
@@ -388,17 +386,17 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
                     for (int e = threadIdx.x; e < 32 * KP; e += NT) {
                         const int ln = e / KP, c = e % KP;
                         const int ccc = cg + ln;
-                        if (ccc < cw && c < k && keep[c] != (TC)0) {
+                        if (ccc < cw && c < k && s_keep[c] != (TC)0) {
                             TC u = (TC)0;
 #pragma unroll
                             for (int w = 0; w < NW; ++w) u += s_red[(w * 32 + ln) * KP + c];
                             const int li = ccc * KP + c;
                             const int64_t col = c0 + ccc;
-                            const TC rm = beta[c] * (rmc[li] - u);
+                            const TC rm = s_beta[c] * (rmc[li] - u);
                             rmc[li] = rm;
                             rxc[li] = rxc[li] - u + eta * rm;
                             const TC wv = (col >= S0 && col < S0 + len) ? s_y[(col - S0) * KP + c] : (TC)0;
-                            const TC mm = beta[c] * (mc[li] - wv);
+                            const TC mm = s_beta[c] * (mc[li] - wv);
                             mc[li] = mm;
                             xc[li] = xc[li] - wv + eta * mm;
                         }
@@ -493,6 +491,8 @@ drain:
         out.active = cs.active; out.status = cs.status; out.res_est = cs.res_est; out.bn2 = cs.bn2;
         out.t = t;
     }
+#undef TILE
+#undef GINV
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -378,8 +378,10 @@ static void launch_principal(const void *A, int64_t lda, int64_t n, int s, doubl
 }
 
 int block_gram(const kpp_matrix &A, int s, double lam, double *G, int engine, cudaStream_t st) {
-    if (engine != 1 && A.dtype != KPP_F64 && gram_tc(A, s, lam, G, st, engine == 2)) return 2;
-    if (engine == 2) return -1;
+    // engine 2: one tensor-core product per tile (bf16, or plain tf32 for FP32 storage);
+    // engine 3 / automatic for FP32: FP32 split into two tf32 halves, three products
+    if (engine != 1 && A.dtype != KPP_F64 && gram_tc(A, s, lam, G, st, engine == 2)) return engine == 2 ? 2 : (A.dtype == KPP_F32 ? 3 : 2);
+    if (engine == 2 || engine == 3) return -1;
     if (A.dtype == KPP_F64) launch_gram<double>(A.data, A.ld, A.rows, A.cols, s, lam, G, st);
     else if (A.dtype == KPP_F32) launch_gram<float>(A.data, A.ld, A.rows, A.cols, s, lam, G, st);
     else launch_gram<__nv_bfloat16>(A.data, A.ld, A.rows, A.cols, s, lam, G, st);

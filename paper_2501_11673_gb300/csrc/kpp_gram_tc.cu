@@ -91,13 +91,24 @@ struct GramTile {
     int j, ta, tc;
 };
 
-template <bool BF16>
+// round an FP32 value to the nearest TF32 (10 explicit mantissa bits), ties to even
+__device__ __forceinline__ float tf32_round(float v) {
+    uint32_t u = __float_as_uint(v);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return __uint_as_float(u & 0xFFFFE000u);
+}
+
+template <int MODE>  // 0: bf16 (kind::f16); 1: tf32; 2: FP32 split as hi + lo TF32 (3 products)
 __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t rows,
                                                          int64_t cols, int s, double lam, const GramTile *tiles,
                                                          double *__restrict__ G, int *err) {
+    constexpr bool BF16 = MODE == 0;
+    constexpr bool SPLIT = MODE == 2;
+    constexpr int STAGES = SPLIT ? 2 : TC_STAGES;
+    constexpr int SBYTES = SPLIT ? 2 * TC_STAGE_BYTES : TC_STAGE_BYTES;  // split: hi tiles, then lo tiles
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], split_bar[TC_STAGES], done_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_err;
 
@@ -111,9 +122,10 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
     constexpr uint32_t idesc = umma_idesc(BF16 ? 1u : 2u);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) {
+        for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full_bar[i], 1);
             mbar_init(&empty_bar[i], 1);
+            mbar_init(&split_bar[i], 1);
         }
         mbar_init(&done_bar, 1);
         fence_mbar_init();
@@ -135,20 +147,20 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
         int stage = 0;
         unsigned phase = 0;
         for (int kt = 0; kt < nk; ++kt) {
-            if (kt >= TC_STAGES) {
+            if (kt >= STAGES) {
                 if (!mbar_wait_bounded(&empty_bar[stage], phase ^ 1u, TC_TIMEOUT_NS)) {
                     s_err = 1;
                     break;
                 }
             }
-            unsigned char *a_s = sm + stage * TC_STAGE_BYTES;
+            unsigned char *a_s = sm + stage * SBYTES;
             unsigned char *b_s = a_s + TC_ABYTES;
             mbar_arrive_expect_tx(&full_bar[stage], TC_STAGE_BYTES);
             const int kx = kt * BK;
             tma_load_2d(a_s, &tmap, kx, (int)(r0 + tile.ta * TC_M), &full_bar[stage]);
             tma_load_2d(b_s, &tmap, kx, (int)(r0 + tile.tc * TC_N), &full_bar[stage]);
             tma_load_2d(b_s + TC_ABYTES, &tmap, kx, (int)(r0 + tile.tc * TC_N + TC_M), &full_bar[stage]);
-            if (++stage == TC_STAGES) {
+            if (++stage == STAGES) {
                 stage = 0;
                 phase ^= 1u;
             }
@@ -157,29 +169,63 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
         // MMA issuer
         int stage = 0;
         unsigned phase = 0;
-        int issued = 0;
         for (int kt = 0; kt < nk; ++kt) {
-            if (!mbar_wait_bounded(&full_bar[stage], phase, TC_TIMEOUT_NS)) {
+            if (!mbar_wait_bounded(SPLIT ? &split_bar[stage] : &full_bar[stage], phase, TC_TIMEOUT_NS)) {
                 s_err = 1;
                 break;
             }
             tc_fence_after();
-            const uint32_t a_addr = smem_u32(sm + stage * TC_STAGE_BYTES);
+            const uint32_t a_addr = smem_u32(sm + stage * SBYTES);
             const uint32_t b_addr = a_addr + TC_ABYTES;
             for (int kk = 0; kk < BK / KSTEP; ++kk) {
                 const uint32_t koff = (uint32_t)(kk * KSTEP * (BF16 ? 2 : 4));  // bytes along the 128-byte row
-                umma<BF16>(tmem, umma_desc_sw128(a_addr + koff), umma_desc_sw128(b_addr + koff), idesc,
-                           (kt > 0 || kk > 0) ? 1u : 0u);
-                ++issued;
+                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                umma<BF16>(tmem, umma_desc_sw128(a_addr + koff), umma_desc_sw128(b_addr + koff), idesc, acc);
+                if (SPLIT) {
+                    const uint32_t lo = TC_STAGE_BYTES;  // lo tiles follow the hi tiles
+                    umma<false>(tmem, umma_desc_sw128(a_addr + koff), umma_desc_sw128(b_addr + lo + koff), idesc, 1u);
+                    umma<false>(tmem, umma_desc_sw128(a_addr + lo + koff), umma_desc_sw128(b_addr + koff), idesc, 1u);
+                }
             }
             umma_commit(&empty_bar[stage]);  // stage reusable once these MMAs have read it
-            if (++stage == TC_STAGES) {
+            if (++stage == STAGES) {
                 stage = 0;
                 phase ^= 1u;
             }
         }
         umma_commit(&done_bar);  // all issued MMAs complete (also on the error path)
-        (void)issued;
+    } else if (SPLIT && warp >= 2) {
+        // splitters (64 threads): x -> hi = tf32(x) in place, lo = x - hi at the same offset of the lo tiles
+        int stage = 0;
+        unsigned phase = 0;
+        const int t64 = threadIdx.x - 64;
+        for (int kt = 0; kt < nk; ++kt) {
+            bool ok = true;
+            if (t64 == 0) ok = mbar_wait_bounded(&full_bar[stage], phase, TC_TIMEOUT_NS);
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            if (t64 == 0 && !ok) s_err = 1;
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            if (s_err) break;
+            float4 *hi = (float4 *)(sm + stage * SBYTES);
+            float4 *lo = (float4 *)(sm + stage * SBYTES + TC_STAGE_BYTES);
+            for (int e = t64; e < TC_STAGE_BYTES / 16; e += 64) {
+                const float4 v = hi[e];
+                float4 h, l;
+                h.x = tf32_round(v.x); l.x = v.x - h.x;
+                h.y = tf32_round(v.y); l.y = v.y - h.y;
+                h.z = tf32_round(v.z); l.z = v.z - h.z;
+                h.w = tf32_round(v.w); l.w = v.w - h.w;
+                hi[e] = h;
+                lo[e] = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            if (t64 == 0) mbar_arrive_expect_tx(&split_bar[stage], 0);
+            if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1u;
+            }
+        }
     }
     __syncwarp();
     // epilogue: every thread owns TMEM lane (32 * warp + lane) = tile row
@@ -231,7 +277,8 @@ static bool gram_tc_disabled() {
 
 bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st, bool allow_tf32) {
     if (gram_tc_disabled()) return false;
-    if (A.dtype != KPP_BF16 && !(A.dtype == KPP_F32 && allow_tf32)) return false;
+    if (A.dtype != KPP_BF16 && A.dtype != KPP_F32) return false;
+    const int mode = A.dtype == KPP_BF16 ? 0 : (allow_tf32 ? 1 : 2);
     const size_t es = A.dtype == KPP_F32 ? 4 : 2;
     if (((uintptr_t)A.data & 15) || ((A.ld * es) & 15) || A.rows > 0x7fffffffLL || A.cols > 0x7fffffffLL) return false;
     void *fnp = nullptr;
@@ -266,10 +313,11 @@ bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st,
     ok = ok && cudaMemcpyAsync(d_tiles, tl.data(), tl.size() * sizeof(GramTile), cudaMemcpyHostToDevice, st) ==
                    cudaSuccess;
     if (ok) {
-        auto kern = A.dtype == KPP_BF16 ? gram_tc_kernel<true> : gram_tc_kernel<false>;
-        ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) == cudaSuccess;
+        auto kern = mode == 0 ? gram_tc_kernel<0> : (mode == 1 ? gram_tc_kernel<1> : gram_tc_kernel<2>);
+        const int smem = mode == 2 ? 2 * 2 * TC_STAGE_BYTES + 1024 : TC_SMEM;
+        ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
         if (ok) {
-            kern<<<(unsigned)tl.size(), 128, TC_SMEM, st>>>(tm, A.rows, A.cols, s, lam, d_tiles, G, d_err);
+            kern<<<(unsigned)tl.size(), 128, smem, st>>>(tm, A.rows, A.cols, s, lam, d_tiles, G, d_err);
             ok = cudaGetLastError() == cudaSuccess;
         }
         ok = ok && cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;

@@ -205,13 +205,13 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SysArgs *__restrict_
             __syncthreads();
 
             // ---- back-projection and update on my column chunk ----
-            TC beta[KP], keep[KP];
-#pragma unroll
-            for (int c = 0; c < KP; ++c) {
-                const double rho = st[c].rho;
-                beta[c] = (TC)((1.0 - rho) / (1.0 + rho));
-                keep[c] = (TC)((c < k && st[c].active) ? 1 : 0);
+            __shared__ TC s_beta[KP], s_keep[KP];  // read with a runtime rhs index below
+            if (threadIdx.x < KP) {
+                const double rho = st[threadIdx.x].rho;
+                s_beta[threadIdx.x] = (TC)((1.0 - rho) / (1.0 + rho));
+                s_keep[threadIdx.x] = (TC)((threadIdx.x < k && st[threadIdx.x].active) ? 1 : 0);
             }
+            __syncthreads();
             const TC eta = (TC)cm.eta;
             for (int64_t cb = c0; cb < c1; cb += 32) {
                 const int64_t col = cb + lane;
@@ -234,21 +234,21 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SysArgs *__restrict_
                 for (int e = threadIdx.x; e < 32 * KP; e += NT) {
                     const int ln = e / KP, c = e % KP;
                     const int64_t cl = cb + ln;
-                    if (cl < c1 && c < k && keep[c] != (TC)0) {
+                    if (cl < c1 && c < k && s_keep[c] != (TC)0) {
                         TC u = (TC)0;
 #pragma unroll
                         for (int w = 0; w < NW; ++w) u += s_red[(w * 32 + ln) * KP + c];
                         const size_t idx = (size_t)cl * k + c;
                         if (!CD) {
-                            const TC mm = beta[c] * (__ldcg(mv + idx) - u);
+                            const TC mm = s_beta[c] * (__ldcg(mv + idx) - u);
                             mv[idx] = mm;
                             x[idx] = __ldcg(x + idx) - u + eta * mm;
                         } else {
-                            const TC rm = beta[c] * (__ldcg(Rm + idx) - u);
+                            const TC rm = s_beta[c] * (__ldcg(Rm + idx) - u);
                             Rm[idx] = rm;
                             Rx[idx] = __ldcg(Rx + idx) - u + eta * rm;
                             const TC wv = (cl >= S0 && cl < S0 + len) ? s_y[(cl - S0) * KP + c] : (TC)0;
-                            const TC mm = beta[c] * (__ldcg(mv + idx) - wv);
+                            const TC mm = s_beta[c] * (__ldcg(mv + idx) - wv);
                             mv[idx] = mm;
                             x[idx] = __ldcg(x + idx) - wv + eta * mm;
                         }
@@ -439,9 +439,9 @@ __global__ void __launch_bounds__(256) residual_kernel(const TA *__restrict__ A,
             }
         }
     }
-    for (int c = 0; c < k; ++c) {
-        if (lane == 0) s_acc[warp][c] = acc2[c];
-    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+        if (c < k && lane == 0) s_acc[warp][c] = acc2[c];
     __syncthreads();
     if (threadIdx.x < k) {
         double t = 0.0;

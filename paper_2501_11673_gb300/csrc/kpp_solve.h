@@ -70,7 +70,7 @@ cudaError_t launch_negate_copy(size_t n, const void *src, void *dst, bool f64, c
 // Small-block kernel (kpp_solve2.cu).
 bool solve2_eligible(const kpp_matrix &A, int s, int64_t CW, int KP, bool f64, bool cd, int G);
 bool make_tmap_2d(void *out, const void *base, int dtype, uint64_t cols, uint64_t rows, uint64_t ld_elems,
-                  uint32_t box_cols, uint32_t box_rows);
+                  uint32_t box_cols, uint32_t box_rows, bool swizzle128 = false);
 size_t sys2_bytes();
 void sys2_fill(void *dst_host, const SysArgs &a, const void *tmap);
 cudaError_t launch_solve2(int dtype, bool cd, const void *d_sys, int nsys, const Common &cm, int KP, cudaStream_t st);
@@ -81,5 +81,14 @@ size_t cd3_mail_bytes(int s, int KP, bool f64);
 size_t sys3_bytes();
 void sys3_fill(void *dst_host, const SysArgs &a, const void *tmap, void *mail);
 cudaError_t launch_cd3(int dtype, const void *d_sys, int nsys, const Common &cm, int KP, cudaStream_t st);
+
+// Streaming batched K++ kernel for wide FP32 / BF16 systems (kpp_stream.cu).
+size_t sys4_bytes();
+void sys4_fill(void *dst, const void *tmap, const float *b, float *X, float *M, const float *Ginv, float *part,
+               double *rpart, SolveScalars *sc, unsigned *bar, int *err, uint32_t sys_id, int64_t t0);
+int stream_tk(int dtype);
+size_t stream_smem_bytes(int s, int KP);
+int stream_per_sm(int dtype, int s, int KP);
+cudaError_t launch_stream(int dtype, const void *d_sys, int nsys, const Common &cm, int KP, cudaStream_t st);
 
 }  // namespace kpp

@@ -81,8 +81,13 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
 
     extern __shared__ __align__(128) unsigned char sm[];
     const Smem2 L = smem2_layout(s, cm.CW, KP, (int)sizeof(TA), (int)sizeof(TC), DY);
-    TA *tile[2] = {(TA *)(sm + L.tile[0]), (TA *)(sm + L.tile[1])};
-    TC *ginv[2] = {(TC *)(sm + L.ginv[0]), (TC *)(sm + L.ginv[1])};
+    // double buffers addressed by arithmetic (a runtime-indexed pointer array would live in local memory)
+    unsigned char *const tile0 = sm + L.tile[0];
+    const int tile_stride = L.tile[1] - L.tile[0];
+    unsigned char *const ginv0 = sm + L.ginv[0];
+    const int ginv_stride = L.ginv[1] - L.ginv[0];
+#define TILE(bf) ((TA *)(tile0 + (bf) * tile_stride))
+#define GINV(bf) ((TC *)(ginv0 + (bf) * ginv_stride))
     TC *xc = (TC *)(sm + L.xc);
     TC *mc = (TC *)(sm + L.mc);
     TC *rxc = (TC *)(sm + L.rxc);
@@ -111,7 +116,8 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
     const int CWs = (int)cm.CW;  // leading dimension of the shared tile
     const int zeta = nb;
     int64_t t = sa.t0;
-    TC *Rxp[2] = {(TC *)sa.Rx, (TC *)sa.Rx + (size_t)rows * k};
+    TC *const Rx0 = (TC *)sa.Rx;  // two published copies of R_x: Rx0 + parity * rows * k
+#define RXP(par) (Rx0 + (size_t)(par) * rows * k)
 
     // ---- set-up ----
     if (threadIdx.x < KP) {
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
         if (!group_barrier(gs)) goto drain;
     }
     if (CD && cm.init_residual) {
-        if (!true_residual_phase<TA, TC, KP>(sa, cm, g, gs, st, s_part, Rxp[t & 1])) goto drain;
+        if (!true_residual_phase<TA, TC, KP>(sa, cm, g, gs, st, s_part, RXP(t & 1))) goto drain;
     }
     // chunk state into shared memory
     for (int e = threadIdx.x; e < cw * KP; e += NT) {
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
         xc[e] = (c < k) ? __ldcg(x + gi) : (TC)0;
         mc[e] = (TC)0;
         if (CD) {
-            rxc[e] = (c < k) ? __ldcg(Rxp[t & 1] + gi) : (TC)0;
+            rxc[e] = (c < k) ? __ldcg(RXP(t & 1) + gi) : (TC)0;
             rmc[e] = (TC)0;
         }
     }
@@ -187,8 +193,8 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             const unsigned abytes = (unsigned)(nbox * box * CWs * (int)sizeof(TA));
             mbar_arrive_expect_tx(&mbar[bf], abytes + gbytes);
             for (int q = 0; q < nbox; ++q)
-                tma_load_2d(tile[bf] + (size_t)q * box * CWs, tmap, (int)c0, j * s + q * box, &mbar[bf]);
-            if (gbytes) bulk_load(ginv[bf], Ginv + (size_t)j * s * s, gbytes, &mbar[bf]);
+                tma_load_2d(TILE(bf) + (size_t)q * box * CWs, tmap, (int)c0, j * s + q * box, &mbar[bf]);
+            if (gbytes) bulk_load(GINV(bf), Ginv + (size_t)j * s * s, gbytes, &mbar[bf]);
             s_pending[bf] = 1;
         };
         // distributed y: bulk-copy my rows a = g + G w of G^{-1}_{j(tt)} (each row len values, padded to 16 B)
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
         auto partial = [&](int64_t tt) {
             const int j = draw_block(cm.seed, tt, sa.sys_id, nb);
             const int len = (int)min64(s, rows - (int64_t)j * s);
-            const TA *tl = tile[tt & 1];
+            const TA *tl = TILE(tt & 1);
             TC *part = (TC *)sa.part + ((size_t)(tt & 1) * cm.G + g) * s * KP;
             for (int a = warp; a < len; a += NW) {
                 TC acc[KP];
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             } else {
                 for (int e = threadIdx.x; e < len * KP; e += NT) {
                     const int a = e / KP, c = e % KP;
-                    s_r[e] = (c < k) ? __ldcg(Rxp[bf] + (S0 + a) * k + c) : (TC)0;
+                    s_r[e] = (c < k) ? __ldcg(RXP(bf) + (S0 + a) * k + c) : (TC)0;
                 }
                 if (!wait_buf(bf)) break;
             }
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
                 for (int e = threadIdx.x; e < len * KP; e += NT) s_y[e] = __ldcg(ybuf + e);
                 __syncthreads();
             } else {
-                const TC *gv = ginv[bf];
+                const TC *gv = GINV(bf);
                 const int RG = min(NT, (len + 31) / 32 * 32);
                 const int Q = NT / RG;
                 const int a = threadIdx.x % RG, q = threadIdx.x / RG;
@@ -382,14 +388,8 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
 
             // ---- back-projection and update of my chunk (shared memory) ----
             {
-                TC beta[KP], keep[KP];
-#pragma unroll
-                for (int c = 0; c < KP; ++c) {
-                    beta[c] = s_beta[c];
-                    keep[c] = s_keep[c];
-                }
                 const TC eta = (TC)cm.eta;
-                const TA *tl = tile[bf];
+                const TA *tl = TILE(bf);
                 for (int cg = 0; cg < cw; cg += 32) {
                     const int cc = cg + lane;
                     TC acc[KP];
@@ -408,22 +408,22 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
                     for (int e = threadIdx.x; e < 32 * KP; e += NT) {
                         const int ln = e / KP, c = e % KP;
                         const int ccc = cg + ln;
-                        if (ccc < cw && c < k && keep[c] != (TC)0) {
+                        if (ccc < cw && c < k && s_keep[c] != (TC)0) {
                             TC u = (TC)0;
 #pragma unroll
                             for (int w = 0; w < NW; ++w) u += s_red[(w * 32 + ln) * KP + c];
                             const int li = ccc * KP + c;
                             if (!CD) {
-                                const TC mm = beta[c] * (mc[li] - u);
+                                const TC mm = s_beta[c] * (mc[li] - u);
                                 mc[li] = mm;
                                 xc[li] = xc[li] - u + eta * mm;
                             } else {
                                 const int64_t col = c0 + ccc;
-                                const TC rm = beta[c] * (rmc[li] - u);
+                                const TC rm = s_beta[c] * (rmc[li] - u);
                                 rmc[li] = rm;
                                 rxc[li] = rxc[li] - u + eta * rm;
                                 const TC wv = (col >= S0 && col < S0 + len) ? s_y[(col - S0) * KP + c] : (TC)0;
-                                const TC mm = beta[c] * (mc[li] - wv);
+                                const TC mm = s_beta[c] * (mc[li] - wv);
                                 mc[li] = mm;
                                 xc[li] = xc[li] - wv + eta * mm;
                             }
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             const bool ckpt = (ph == 2 * zeta - 1);
             if (CD) {
                 // publish my chunk of R_x for the next step; x too at checkpoints
-                TC *dst = Rxp[(t + 1) & 1];
+                TC *dst = RXP((t + 1) & 1);
                 for (int e = threadIdx.x; e < cw * KP; e += NT) {
                     const int cc = e / KP, c = e % KP;
                     if (c < k) dst[(size_t)(c0 + cc) * k + c] = rxc[e];
@@ -479,13 +479,13 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             if (!group_barrier(gs)) break;
             if (ckpt) {
                 if (s_need) {
-                    if (!true_residual_phase<TA, TC, KP>(sa, cm, g, gs, st, s_part, CD ? Rxp[t & 1] : (TC *)nullptr))
+                    if (!true_residual_phase<TA, TC, KP>(sa, cm, g, gs, st, s_part, CD ? RXP(t & 1) : (TC *)nullptr))
                         break;
                     if (CD) {
                         // the replaced residual becomes my chunk's R_x
                         for (int e = threadIdx.x; e < cw * KP; e += NT) {
                             const int cc = e / KP, c = e % KP;
-                            if (c < k) rxc[e] = __ldcg(Rxp[t & 1] + (size_t)(c0 + cc) * k + c);
+                            if (c < k) rxc[e] = __ldcg(RXP(t & 1) + (size_t)(c0 + cc) * k + c);
                         }
                     }
                 }
@@ -534,6 +534,9 @@ drain:
         out.active = cs.active; out.status = cs.status; out.res_est = cs.res_est; out.bn2 = cs.bn2;
         out.t = t;
     }
+#undef TILE
+#undef GINV
+#undef RXP
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -559,7 +562,7 @@ static EncodeTiledFn encode_fn() {
 }
 
 bool make_tmap_2d(void *out, const void *base, int dtype, uint64_t cols, uint64_t rows, uint64_t ld_elems,
-                  uint32_t box_cols, uint32_t box_rows) {
+                  uint32_t box_cols, uint32_t box_rows, bool swizzle128) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const size_t es = dtype == KPP_F64 ? 8 : (dtype == KPP_F32 ? 4 : 2);
@@ -571,7 +574,8 @@ bool make_tmap_2d(void *out, const void *base, int dtype, uint64_t cols, uint64_
     cuuint32_t box[2] = {box_cols, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn((CUtensorMap *)out, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }

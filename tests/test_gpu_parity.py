@@ -273,6 +273,10 @@ def test_tensor_core_gram_matches_fp64_gram(K, dtype, m, n, s):
     lam = 0.25
     Gt, used = K.block_gram(Ad, s, lam, engine=2)
     assert used == 2
+    if dtype == "f32":
+        Gs, used3 = K.block_gram(Ad, s, lam, engine=3)
+        assert used3 == 3
+        Gs = Gs.cpu().numpy()
     G64, used64 = K.block_gram(Ad, s, lam, engine=1)
     assert used64 == 1
     Gt, G64 = Gt.cpu().numpy(), G64.cpu().numpy()
@@ -287,6 +291,11 @@ def test_tensor_core_gram_matches_fp64_gram(K, dtype, m, n, s):
         np.testing.assert_allclose(_unpack_lower(G64, j, m, s), ref, rtol=1e-12, atol=1e-12 * scale.max())
         err = np.abs(_unpack_lower(Gt, j, m, s) - ref) / np.tril(scale)
         assert np.nanmax(err) <= tol, (j, float(np.nanmax(err)))
+        if dtype == "f32":
+            # split TF32: products good to ~2^-21; three MMAs per K-slice round into the FP32 accumulator,
+            # so three times the accumulation term above
+            err3 = np.abs(_unpack_lower(Gs, j, m, s) - ref) / np.tril(scale)
+            assert np.nanmax(err3) <= 3 * max(1e-6, (n / 16) * 2.0 ** -23) + 2.0 ** -19, (j, float(np.nanmax(err3)))
 
 
 def test_tensor_core_gram_refuses_unaligned_rows_and_auto_falls_back(K):
@@ -329,3 +338,56 @@ def test_true_residual_is_exact_fp64_of_stored_entries(K, dtype):
     got = K.rel_residual(dev(Ar, torch.bfloat16 if dtype == "bf16" else torch.float32), dev(b), dev(x))
     want = np.linalg.norm(b - Ar @ x) / np.linalg.norm(b)
     assert abs(got - want) <= 1e-12 * want
+
+
+def _wide_batch(nsys, m, n, s, k, dtype, seed=0):
+    As, Bs = [], []
+    for i in range(nsys):
+        A, B, _ = W.gaussian_rows(m, n, 2, 100.0, seed_A=seed + 10 * i, seed_b=seed + 10 * i + 1, k_rhs=k)
+        As.append(W.round_to_storage(A, dtype))
+        Bs.append(B)
+    return As, Bs
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("k", [1, 3])
+def test_streaming_batched_refinement_reaches_min_norm(K, dtype, k):
+    """Wide under-determined systems (the streaming kernel): FP64 refinement to 1e-8 per column, and the
+    result is the minimum-norm solution A^T (A A^T)^{-1} b (K++ from x0 = 0 stays in range(A^T))."""
+    nsys, m, n, s = 3, 96, 16384, 32
+    As, Bs = _wide_batch(nsys, m, n, s, k, dtype)
+    lam = W.row_outlier_lambda(As[0])
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    P = K.Partition(m, s)
+    Ad = [dev(a, tdt) for a in As]
+    Fs = [K.Factors(a, P, lam, 0) for a in Ad]
+    Xd = [dev(np.zeros((n, k))) for _ in range(nsys)]
+    reps = K.kpp_solve_batched(Ad, [dev(b) for b in Bs], Xd, P, Fs,
+                               K.params(lam=lam, tol=1e-8, refine=1, inner_tol=1e-4, seed=5))
+    for i in range(nsys):
+        Xmn = As[i].T @ np.linalg.solve(As[i] @ As[i].T, Bs[i])
+        for c in range(k):
+            r = reps[i * k + c]
+            assert r.status == K.OK and r.rel_res_true <= 1e-8, r.as_dict()
+            assert rel(Xd[i][:, c].cpu().numpy(), Xmn[:, c]) <= 1e-6
+
+
+def test_streaming_kernel_tracks_general_kernel_in_fp32(K):
+    """Same FP32 iteration through the streaming kernel and the general kernel: iterates agree to FP32
+    rounding after T steps (different but fixed summation orders)."""
+    nsys, m, n, s, k = 2, 64, 16384, 32, 3
+    As, Bs = _wide_batch(nsys, m, n, s, k, "f32", seed=100)
+    lam = W.row_outlier_lambda(As[0])
+    P = K.Partition(m, s)
+    Ad = [dev(a, torch.float32) for a in As]
+    Fs = [K.Factors(a, P, lam, 0) for a in Ad]
+    out = {}
+    for v in (1, 3):
+        K.set_kernel_variant(v)
+        Xd = [dev(np.zeros((n, k))) for _ in range(nsys)]
+        K.kpp_solve_batched(Ad, [dev(b) for b in Bs], Xd, P, Fs,
+                            K.params(lam=lam, tol=0.0, max_iters=37, refine=0, seed=9), allow_no_conv=True)
+        out[v] = [x.cpu().numpy() for x in Xd]
+    K.set_kernel_variant(3)
+    for i in range(nsys):
+        assert rel(out[3][i], out[1][i]) <= 2e-5
