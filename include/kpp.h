@@ -234,6 +234,59 @@ kpp_status kpp_block_gram(const kpp_matrix *A, int32_t s, double lambda, int32_t
  * Not thread-safe with concurrent solves.  Errors: KPP_ERR_ARG for another value. */
 kpp_status kpp_set_kernel_variant(int32_t variant);
 
+/* ------------------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over registered matrices (host runtime in the library).
+ * Requests arrive at any time and are admitted FIFO as soon as device memory under the budget allows:
+ * a request's panels and scratch and, on a matrix's first use, its memoised block factors (Sec. 4,
+ * Sec. 5.2), which then stay resident for later requests on that matrix (idle factors are evicted when
+ * the budget needs the room).  Admitted requests run concurrently, each on its own CUDA stream, so work
+ * that arrives while other solves run overlaps with them on the GPU.  Solves are deterministic: a
+ * request's result does not depend on the other requests in flight.
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct kpp_server_s *kpp_server_t;
+
+typedef struct {
+    int64_t completed;      /* requests finished (any status) */
+    int64_t failed;         /* requests finished with a status other than KPP_OK */
+    double p50_ms, p99_ms, max_ms;  /* submission -> completion latency percentiles */
+    double solves_per_s;    /* completed / (last completion - first submission) */
+    double span_s;
+    size_t peak_bytes;      /* largest device memory charged to the budget */
+    size_t budget_bytes;
+    int64_t reserved[4];
+} kpp_serving_stats;
+
+/* Create a server with a device-memory budget (bytes), `max_concurrent` solves in flight (1..64) and
+ * `grid_per_solve` CTAs per solve (0: automatic).  Uses the current CUDA device.  Errors: KPP_ERR_ARG. */
+kpp_status kpp_server_create(size_t hbm_budget_bytes, int32_t max_concurrent, int32_t grid_per_solve,
+                             kpp_server_t *out);
+/* Register a device matrix (caller-owned, must outlive the server) for mode 0 (K++) or 1 (CD++; square
+ * symmetric), block size s and regulariser lambda.  Factors are built on first use.  *matrix_id
+ * receives its index.  Errors: KPP_ERR_ARG. */
+kpp_status kpp_server_add_matrix(kpp_server_t sv, const kpp_matrix *A, int32_t s, double lambda, int32_t mode,
+                                 int32_t *matrix_id);
+/* Submit a request: B_host is rows x k (row-major FP64, copied before return), 1 <= k <= 32; p gives
+ * tol, seed, sys_id, refine, ... (p->lambda is taken from the matrix).  Returns immediately with
+ * *request_id.  KPP_ERR_BUDGET if the request alone cannot fit the budget (it is then complete with
+ * that status). */
+kpp_status kpp_server_submit(kpp_server_t sv, int32_t matrix_id, const double *B_host, int32_t k, const kpp_params *p,
+                             int64_t *request_id);
+/* Non-blocking: *done = 1 once the request finished; then X_host (cols x k FP64, may be NULL) and reps
+ * (k reports, may be NULL) are filled and the request's status is returned. */
+kpp_status kpp_server_poll(kpp_server_t sv, int64_t request_id, double *X_host, kpp_report *reps, int32_t *done);
+/* Block until no request is queued or running, at most timeout_s seconds (KPP_ERR_TIMEOUT). */
+kpp_status kpp_server_wait_all(kpp_server_t sv, double timeout_s);
+kpp_status kpp_server_stats(kpp_server_t sv, kpp_serving_stats *out);
+/* Stop the workers (after the running requests finish) and free the factors. */
+void kpp_server_destroy(kpp_server_t sv);
+
+/* Batched CD++ (Eq. 5.1, Alg. 3): as kpp_solve_batched, for square symmetric systems whose factors
+ * come from kpp_factor_blocks(mode 1); the k columns of a system share its block sequence and each has
+ * its own rho, residual estimate and stop test. */
+kpp_status cdpp_solve_batched(int32_t nsys, const kpp_matrix *A, const double *const *B, double *const *X, int32_t k,
+                              kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p, kpp_report *reps,
+                              void *stream);
+
 /* Library build information: "sm_103a; <compiler>; <date>". */
 const char *kpp_build_info(void);
 

@@ -391,7 +391,7 @@ static double default_eta(const kpp_params &p, int s, int64_t rows, int64_t cols
 static kpp_status worse(kpp_status a, kpp_status b) { return a != KPP_OK ? a : b; }
 
 // The solve of `nsys` systems with k right-hand sides each (FP64 b/x on the device).
-static kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
+kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
                                 kpp_partition_t P, const kpp_factors_t *F, const kpp_params *pp, kpp_report *reps,
                                 cudaStream_t st, bool cd) {
     clear_error();
@@ -578,6 +578,12 @@ static kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *con
     return worst;
 }
 
+kpp_status solve_systems_internal(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
+                                  kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p, kpp_report *reps,
+                                  cudaStream_t st, bool cd) {
+    return solve_systems(nsys, A, B, X, k, P, F, p, reps, st, cd);
+}
+
 }  // namespace kpp
 
 using namespace kpp;
@@ -757,6 +763,12 @@ kpp_status kpp_block_gram(const kpp_matrix *A, int32_t s, double lambda, int32_t
         return KPP_ERR_CUDA;
     }
     return KPP_OK;
+}
+
+kpp_status cdpp_solve_batched(int32_t nsys, const kpp_matrix *A, const double *const *B, double *const *X, int32_t k,
+                              kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p, kpp_report *reps,
+                              void *stream) {
+    return solve_systems(nsys, A, B, X, k, P, F, p, reps, (cudaStream_t)stream, true);
 }
 
 kpp_status kpp_rel_residual(const kpp_matrix *A, const double *b, const double *x, double *out_host, void *stream) {

@@ -40,6 +40,11 @@ bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st,
 // FP32 storage).  Returns the engine used, or -1.
 int block_gram(const kpp_matrix &A, int s, double lam, double *G, int engine, cudaStream_t st);
 
+// The solve behind kpp_solve / cdpp_solve / kpp_solve_batched (nsys systems, k right-hand sides each).
+kpp_status solve_systems_internal(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
+                                  kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p, kpp_report *reps,
+                                  cudaStream_t st, bool cd);
+
 // Number of SMs of the current device (cached).
 int sm_count();
 

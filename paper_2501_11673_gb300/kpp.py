@@ -31,7 +31,9 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NUMERIC, ERR_NO_CONVERGENCE, ER
 EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_partition", "kpp_partition_destroy",
            "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block",
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
-           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_block_gram", "kpp_build_info"]
+           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_block_gram", "kpp_server_create", "kpp_server_add_matrix",
+           "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_destroy",
+           "cdpp_solve_batched", "kpp_build_info"]
 
 
 class KppError(RuntimeError):
@@ -51,6 +53,16 @@ class Params(ctypes.Structure):
                 ("rho0", ctypes.c_double), ("eta", ctypes.c_double), ("grid", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("reserved1", ctypes.c_int64 * 4)]
+
+
+class ServingStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("solves_per_s", ctypes.c_double),
+                ("span_s", ctypes.c_double), ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("reserved", ctypes.c_int64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class Report(ctypes.Structure):
@@ -100,7 +112,19 @@ def load(path: str | None = None):
         lib.kpp_solve_batched.argtypes = [i32, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
                                           vp, ctypes.POINTER(vp), ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
         lib.kpp_sample_blocks.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i64, i64, i32, vp, vp]
+        lib.cdpp_solve_batched.argtypes = lib.kpp_solve_batched.argtypes
+        lib.cdpp_solve_batched.restype = ctypes.c_int
         lib.kpp_set_kernel_variant.argtypes = [i32]
+        lib.kpp_server_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)]
+        lib.kpp_server_add_matrix.argtypes = [vp, ctypes.POINTER(Matrix), i32, dbl, i32, ctypes.POINTER(i32)]
+        lib.kpp_server_submit.argtypes = [vp, i32, vp, i32, ctypes.POINTER(Params), ctypes.POINTER(i64)]
+        lib.kpp_server_poll.argtypes = [vp, i64, vp, ctypes.POINTER(Report), ctypes.POINTER(i32)]
+        lib.kpp_server_wait_all.argtypes = [vp, dbl]
+        lib.kpp_server_stats.argtypes = [vp, ctypes.POINTER(ServingStats)]
+        lib.kpp_server_destroy.argtypes = [vp]
+        for name in ("kpp_server_create", "kpp_server_add_matrix", "kpp_server_submit", "kpp_server_poll",
+                     "kpp_server_wait_all", "kpp_server_stats"):
+            getattr(lib, name).restype = ctypes.c_int
         lib.kpp_block_gram.argtypes = [ctypes.POINTER(Matrix), i32, dbl, i32, vp, ctypes.POINTER(i32), vp]
         lib.kpp_block_gram.restype = ctypes.c_int
         for name in ("kpp_set_kernel_variant", "cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
@@ -263,8 +287,9 @@ def cdpp_solve_noalloc(A, b, x, P: Partition, F: Factors, prm: Params, stream=No
 
 
 def kpp_solve_batched(As: list, Bs: list, Xs: list, P: Partition, Fs: list, prm: Params, stream=None,
-                      allow_no_conv: bool = False) -> list:
-    """Batched K++: systems i with A_i (rows x cols), B_i (rows x k) and X_i (cols x k), FP64 panels."""
+                      allow_no_conv: bool = False, cd: bool = False) -> list:
+    """Batched K++ (or CD++ with cd=True): systems i with A_i (rows x cols), B_i (rows x k) and X_i
+    (cols x k), FP64 panels."""
     n = len(As)
     k = Bs[0].shape[1] if Bs[0].dim() == 2 else 1
     mats = (Matrix * n)(*[matrix(a) for a in As])
@@ -272,7 +297,8 @@ def kpp_solve_batched(As: list, Bs: list, Xs: list, P: Partition, Fs: list, prm:
     xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Xs])
     fp = (ctypes.c_void_p * n)(*[f.handle.value for f in Fs])
     reps = (Report * (n * k))()
-    rc = load().kpp_solve_batched(n, mats, bp, xp, k, P.handle, fp, ctypes.byref(prm), reps, _stream_ptr(stream))
+    fn = load().cdpp_solve_batched if cd else load().kpp_solve_batched
+    rc = fn(n, mats, bp, xp, k, P.handle, fp, ctypes.byref(prm), reps, _stream_ptr(stream))
     _check(rc, allow=(ERR_NO_CONVERGENCE,) if allow_no_conv else ())
     return list(reps)
 
@@ -317,6 +343,65 @@ def block_gram(A, s: int, lam: float, engine: int = 0, stream=None):
     _check(load().kpp_block_gram(ctypes.byref(m), int(s), float(lam), int(engine), ctypes.c_void_p(G.data_ptr()),
                                  ctypes.byref(used), _stream_ptr(stream)))
     return G, used.value
+
+
+class Server:
+    """Continuous-batching solve server (kpp_server_*): admission by a device-memory budget, memoised
+    factors kept resident per registered matrix, concurrent solves on separate streams."""
+
+    def __init__(self, hbm_budget_bytes: int, max_concurrent: int = 8, grid_per_solve: int = 0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.kpp_server_create(int(hbm_budget_bytes), int(max_concurrent), int(grid_per_solve),
+                                           ctypes.byref(h)))
+        self.handle = h
+        self._mats = []
+
+    def add_matrix(self, A, s: int, lam: float, mode: int) -> int:
+        mid = ctypes.c_int32()
+        m = matrix(A)
+        _check(self._lib.kpp_server_add_matrix(self.handle, ctypes.byref(m), int(s), float(lam), int(mode),
+                                               ctypes.byref(mid)))
+        self._mats.append(A)  # the device matrix must outlive the server
+        return mid.value
+
+    def submit(self, matrix_id: int, B, prm: Params) -> int:
+        import numpy as np
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        k = 1 if B.ndim == 1 else B.shape[1]
+        rid = ctypes.c_int64()
+        rc = self._lib.kpp_server_submit(self.handle, int(matrix_id), ctypes.c_void_p(B.ctypes.data), k,
+                                         ctypes.byref(prm), ctypes.byref(rid))
+        _check(rc, allow=(ERR_BUDGET,))
+        return rid.value
+
+    def poll(self, request_id: int, cols: int, k: int):
+        """(done, status, X (cols x k) or None, reports or None)."""
+        import numpy as np
+        X = np.zeros((cols, k))
+        reps = (Report * k)()
+        done = ctypes.c_int32()
+        rc = self._lib.kpp_server_poll(self.handle, int(request_id), ctypes.c_void_p(X.ctypes.data), reps,
+                                       ctypes.byref(done))
+        if not done.value:
+            return False, None, None, None
+        return True, rc, X, list(reps)
+
+    def wait_all(self, timeout_s: float = 600.0):
+        _check(self._lib.kpp_server_wait_all(self.handle, float(timeout_s)))
+
+    def stats(self) -> dict:
+        st = ServingStats()
+        _check(self._lib.kpp_server_stats(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.kpp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 def set_kernel_variant(v: int) -> None:

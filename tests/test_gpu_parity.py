@@ -391,3 +391,27 @@ def test_streaming_kernel_tracks_general_kernel_in_fp32(K):
     K.set_kernel_variant(3)
     for i in range(nsys):
         assert rel(out[3][i], out[1][i]) <= 2e-5
+
+
+@pytest.mark.parametrize("n,s", [(200, 16), (192, 32)])
+def test_batched_cdpp_panels_match_single_rhs_oracle(K, variant, n, s):
+    """CD++ with right-hand-side panels (k = 3, two systems): every column against the oracle's
+    single-RHS CD++ run with the same Philox stream."""
+    nsys, k, lam = 2, 3, 1e-4
+    As, Bs = [], []
+    for i in range(nsys):
+        A, _, _ = W.spd(n, 5, 1e2, 1e3, 1.0, 5.0, seed_A=300 + i, seed_b=301 + i)
+        As.append(A)
+        Bs.append(np.random.default_rng(310 + i).standard_normal((n, k)))
+    P = K.Partition(n, s)
+    Ad = [dev(a) for a in As]
+    Fs = [K.Factors(a, P, lam, 1) for a in Ad]
+    Xd = [dev(np.zeros((n, k))) for _ in range(nsys)]
+    T = 2 * (-(-n // s)) * 4 + 5
+    K.kpp_solve_batched(Ad, [dev(b) for b in Bs], Xd, P, Fs, K.params(lam=lam, tol=0.0, max_iters=T, seed=6, sys_id=20),
+                        allow_no_conv=True, cd=True)
+    for i in range(nsys):
+        L = oracle.cdpp_factor(As[i], s, lam)
+        for c in range(k):
+            res = oracle.run(As[i], Bs[i][:, c], L, s, cd=True, lam=lam, tol=0.0, max_iters=T, seed=6, sys=20 + i)
+            assert rel(Xd[i][:, c].cpu().numpy(), res.x) <= 1e-10, (variant, i, c)
