@@ -75,7 +75,7 @@ typedef struct {
     int32_t adaptive_rho;  /* 1: adaptive rho (Eq. 5.3); 0: rho fixed at rho0 */
     double rho0;           /* initial rho (the paper starts from 0) or the fixed rho */
     double eta;            /* momentum step; NaN selects s / (2 min(rows, cols)) (Sec. 5.4) */
-    int32_t grid;          /* CTAs per system; 0 selects automatically */
+    int32_t grid;          /* CTAs per system; 0 selects automatically; KPP_GRID_TUNE (-1) autotunes */
     int32_t refine;        /* mixed precision: outer FP64 iterative refinement (F32/BF16 storage) */
     int32_t max_outer;     /* cap on refinement steps */
     int32_t reserved0;
@@ -286,6 +286,65 @@ void kpp_server_destroy(kpp_server_t sv);
 kpp_status cdpp_solve_batched(int32_t nsys, const kpp_matrix *A, const double *const *B, double *const *X, int32_t k,
                               kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p, kpp_report *reps,
                               void *stream);
+
+/* ---- Prepared batched solves (CUDA-graph capturable) ------------------------------------------
+ *
+ * A plan is the batched solve of kpp_solve_batched (mode 0, K++, Alg. 3 / Sec. 4) or
+ * cdpp_solve_batched (mode 1, CD++, Alg. 5 / Sec. 5) with its systems, buffers and launch shape fixed
+ * once.  The paper describes one solve at a time; batching the systems of one shape into one
+ * persistent launch, and making that launch replayable, is this library's addition.
+ *
+ * kpp_plan_create checks the arguments as kpp_solve_batched does, chooses the kernel and the CTAs
+ * per system (p->grid > 0: that many; 0: the built-in heuristic; KPP_GRID_TUNE (-1): the launch
+ * autotuner below), allocates every scratch buffer, builds the TMA descriptors, and synchronises
+ * `stream`.  A, B, X and F are bound to the plan: their device buffers must outlive it and keep their
+ * addresses; their contents may change between launches.  The plan owns its scratch (freed by
+ * kpp_plan_destroy).  Errors: those of kpp_solve_batched, KPP_ERR_OOM, KPP_ERR_UNSUPPORTED (the
+ * systems x CTAs do not fit co-resident).
+ *
+ * kpp_plan_launch enqueues one complete solve of every system on `stream`: kernels and memsets only
+ * (no allocation, no host synchronisation, no host copy), so it may be called while `stream` is being
+ * captured into a CUDA graph, and the graph replayed.  On entry X holds the initial guesses (zero for
+ * the default start); on completion it holds the solutions.  With F32 / BF16 storage and
+ * p->refine = 1 the FP64 refinement loop runs on the device: each of p->max_outer steps computes
+ * r = b - A x, stops the systems whose columns all satisfy |r| <= tol |b|, solves A d = r in FP32 for
+ * the rest and adds d to x; steps after every system has stopped do no work.  A system whose inner
+ * solve reports a device error stops there (its x keeps the last completed update).  Returns
+ * KPP_ERR_ARG (null plan) or KPP_ERR_CUDA / KPP_ERR_UNSUPPORTED when a launch cannot be enqueued.
+ *
+ * kpp_plan_report synchronises `stream`, then writes nsys * k reports (system-major) with the true
+ * FP64 relative residual of X, iterations, refinement steps, rho and the per-column status, and
+ * returns the first non-OK column status (KPP_OK when every column met the tolerance).  device_ms
+ * is 0: time plan launches with events on the caller's stream.
+ *
+ * kpp_plan_info returns the kernel (1 general, 2 small-block, 3 dataflow CD++, 4 streaming), the CTAs
+ * per system and the kernel generation limit the plan uses (any pointer may be NULL). */
+#define KPP_GRID_TUNE (-1)
+typedef struct kpp_plan_s *kpp_plan_t;
+kpp_status kpp_plan_create(int32_t nsys, const kpp_matrix *A, const double *const *B, double *const *X, int32_t k,
+                           kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p, int32_t mode, void *stream,
+                           kpp_plan_t *out);
+kpp_status kpp_plan_launch(kpp_plan_t plan, void *stream);
+kpp_status kpp_plan_report(kpp_plan_t plan, kpp_report *reps, void *stream);
+kpp_status kpp_plan_info(kpp_plan_t plan, int32_t *kernel, int32_t *grid, int32_t *variant);
+/* Waits for the device to go idle, then frees the plan's scratch.  NULL is ignored. */
+void kpp_plan_destroy(kpp_plan_t plan);
+
+/* ---- Launch autotuner ------------------------------------------------------------------------------
+ *
+ * p->grid = KPP_GRID_TUNE in kpp_plan_create, kpp_solve, cdpp_solve or the batched solves times short
+ * runs (about two sweeps over the blocks, no stop test, from x = 0 on the caller's right-hand sides)
+ * of the persistent kernel for the kernel generations allowed by kpp_set_kernel_variant and a few CTA
+ * counts around the heuristic's, and keeps the fastest time per step.  The choice is cached per
+ * (device, shape, dtype, s, k, mode, nsys, generation limit) for the life of the process.  The launch
+ * shape changes the order of floating-point sums, so a tuned solve matches an untuned one to rounding
+ * only; with the choice cached, repeated solves are bitwise identical.  The cache can be written to a
+ * text file (one "key variant grid" line per shape) and read back, e.g. at start-up.
+ * save/load errors: KPP_ERR_ARG (null path, unreadable or malformed file; nothing is loaded then). */
+int64_t kpp_tune_cache_size(void);
+void kpp_tune_cache_clear(void);
+kpp_status kpp_tune_cache_save(const char *path);
+kpp_status kpp_tune_cache_load(const char *path);
 
 /* Library build information: "sm_103a; <compiler>; <date>". */
 const char *kpp_build_info(void);

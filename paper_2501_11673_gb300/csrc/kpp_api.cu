@@ -14,16 +14,7 @@
 #include "kpp_internal.cuh"
 #include "kpp_runtime.h"
 #include "kpp_solve.h"
-
-struct kpp_partition_s {
-    int64_t rows;
-    int32_t s;
-    int64_t nb;
-};
-
-struct kpp_factors_s {
-    kpp::FactorSet f;
-};
+#include "kpp_launch.h"
 
 namespace kpp {
 
@@ -63,40 +54,8 @@ void FactorSet::release() {
     Ginv32 = nullptr;
 }
 
-static size_t dtype_size(int dt) { return dt == KPP_F64 ? 8 : (dt == KPP_F32 ? 4 : 2); }
-
-static bool matrix_ok(const kpp_matrix *A) {
-    return A && A->data && A->rows > 0 && A->cols > 0 && A->ld >= A->cols &&
-           (A->dtype == KPP_F64 || A->dtype == KPP_F32 || A->dtype == KPP_BF16);
-}
-
-#define CUDA_OR(call, code)                                                    \
-    do {                                                                       \
-        cudaError_t e_ = (call);                                               \
-        if (e_ != cudaSuccess) {                                               \
-            set_error("%s: %s", #call, cudaGetErrorString(e_));                \
-            rc = (e_ == cudaErrorMemoryAllocation) ? KPP_ERR_OOM : (code);     \
-            goto cleanup;                                                      \
-        }                                                                      \
-    } while (0)
-
-// Stream-ordered scratch that is freed when the object goes out of scope.
-struct Scratch {
-    cudaStream_t st;
-    std::vector<void *> ptrs;
-    explicit Scratch(cudaStream_t s) : st(s) {}
-    cudaError_t alloc(void **p, size_t bytes) {
-        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
-        if (e == cudaSuccess) ptrs.push_back(*p);
-        return e;
-    }
-    ~Scratch() {
-        for (void *p : ptrs) cudaFreeAsync(p, st);
-    }
-};
-
 // |A x - b|^2 and |b|^2 per column (deterministic: fixed grid, host sums in a fixed order).
-static kpp_status residual_norms(const kpp_matrix &A, int k, const double *b, const double *x, float *r32,
+kpp_status residual_norms(const kpp_matrix &A, int k, const double *b, const double *x, float *r32,
                                  std::vector<double> &res2, std::vector<double> *bn2, cudaStream_t st) {
     kpp_status rc = KPP_OK;
     const int grid = residual_grid();
@@ -122,30 +81,20 @@ cleanup:
     return rc;
 }
 
-// One system's buffers for a launch of the persistent kernel.
-struct SysInput {
-    const kpp_matrix *A;
-    const void *b;        // TC, rows x k
-    void *x;              // TC, cols x k
-    const FactorSet *F;
-    uint32_t sys_id;
-    SolveScalars *sc_host; // k entries, in/out
-};
-
-static int auto_grid(int64_t cols, int nsys) {
+int auto_grid(int64_t cols, int nsys) {
     // enough CTAs to spread the block rows, at most one CTA per SM for the whole launch
     int per = (int)std::min<int64_t>((cols + 31) / 32, 1024);
     int cap = std::max(1, sm_count() / std::max(1, nsys));
     return std::max(1, std::min(per, cap));
 }
 
-// Run the persistent kernel over nsys systems that share shape, dtype, s and k.
-static int g_variant = 3;
+int g_variant = 3;
 
-static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd, int k, int s, double eta,
-                                 double tol, int adaptive, int confirm, int64_t max_iters, uint64_t seed, int grid,
-                                 bool init_residual, int64_t t0, cudaStream_t st, float *ms_out, int *err_out) {
-    const bool use_v2 = g_variant >= 2;
+kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, int dtype, bool cd, int k,
+                                     int s, double eta, double tol, int adaptive, int confirm, int64_t max_iters,
+                                     uint64_t seed, int grid, bool init_residual, int64_t t0, bool t0_state,
+                                     int variant, Scratch &scr, cudaStream_t st) {
+    const bool use_v2 = variant >= 2;
     kpp_status rc = KPP_OK;
     const int nsys = (int)sys.size();
     const kpp_matrix &A0 = *sys[0].A;
@@ -161,7 +110,7 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     bool v2 = use_v2;
     for (int i = 0; v2 && i < nsys; ++i) v2 = solve2_eligible(*sys[i].A, s, CW, KP, f64, cd, G);
     // CD++ dataflow kernel: same eligibility as v2, plus the memoised W for FP64
-    bool v3 = cd && v2 && g_variant >= 3;
+    bool v3 = cd && v2 && variant >= 3;
     for (int i = 0; v3 && i < nsys; ++i) {
         if (f64 && !sys[i].F->W) v3 = false;
         const size_t tas = f64 ? 8 : dtype_size(dtype);
@@ -169,7 +118,7 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     }
     if (v3) v2 = false;
     // wide FP32 / BF16 K++ systems: the streaming kernel (column chunks too wide for the small-block one)
-    bool v4 = !f64 && !cd && g_variant >= 2 && !v2 && KP <= 8 && s >= 2 && s <= 256;
+    bool v4 = !f64 && !cd && variant >= 2 && !v2 && KP <= 8 && s >= 2 && s <= 256;
     if (v4) {
         const int64_t TK = stream_tk(dtype);
         for (int i = 0; v4 && i < nsys; ++i) {
@@ -193,8 +142,9 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
             }
         }
     }
-    Common cm{};
-    cm.rows = A0.rows;  // (filled after the kernel choice below)
+    Common &cm = L.cm;
+    cm = Common{};
+    cm.rows = A0.rows;
     cm.cols = A0.cols;
     cm.s = s;
     cm.nb = nb;
@@ -210,60 +160,62 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
     cm.max_iters = max_iters;
     cm.seed = seed;
     cm.timeout_ns = 2000000000ull;
+    cm.t0_state = t0_state ? 1 : 0;
+    L.kind = v4 ? 4 : v3 ? 3 : v2 ? 2 : 1;
+    L.dtype = dtype;
+    L.KP = KP;
+    L.nsys = nsys;
+    L.k = k;
+    L.cd = cd;
+    L.f64 = f64;
+    L.init_residual = init_residual;
+    L.t0 = t0;
+    L.tcs = tcs;
+    L.vec_n = (size_t)A0.cols * k;
+    L.vec_r = (size_t)A0.rows * k;
+    L.args.assign(nsys, SysArgs{});
+    L.mails.assign(nsys, nullptr);
 
     const size_t smem = solve_smem_bytes(s, KP, CW, tcs);
-    if (!v2 && !v3 && !v4 && smem > 220 * 1024) {
+    if (L.kind == 1 && smem > 220 * 1024) {
         set_error("shared memory %zu B exceeds the per-CTA limit (s=%d, k=%d, chunk=%lld)", smem, s, k, (long long)CW);
         return KPP_ERR_UNSUPPORTED;
     }
-    Scratch scr(st);
-    std::vector<SysArgs> args(nsys);
-    SysArgs *d_args = nullptr;
-    void *d_sys2 = nullptr;
     std::vector<unsigned char> h2;
-    unsigned *bars = nullptr;
-    int *errs = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    std::vector<int> herr(nsys, 0);
-    const size_t vec_n = (size_t)A0.cols * k, vec_r = (size_t)A0.rows * k;
-    CUDA_OR(scr.alloc((void **)&bars, nsys * sizeof(unsigned)), KPP_ERR_CUDA);
-    CUDA_OR(scr.alloc((void **)&errs, nsys * sizeof(int)), KPP_ERR_CUDA);
-    CUDA_OR(cudaMemsetAsync(bars, 0, nsys * sizeof(unsigned), st), KPP_ERR_CUDA);
-    CUDA_OR(cudaMemsetAsync(errs, 0, nsys * sizeof(int), st), KPP_ERR_CUDA);
+    CUDA_OR(scr.alloc((void **)&L.bars, nsys * sizeof(unsigned)), KPP_ERR_CUDA);
+    CUDA_OR(scr.alloc((void **)&L.errs, nsys * sizeof(int)), KPP_ERR_CUDA);
     for (int i = 0; i < nsys; ++i) {
-        SysArgs &a = args[i];
+        SysArgs &a = L.args[i];
         a.A = sys[i].A->data;
         a.lda = sys[i].A->ld;
         a.b = sys[i].b;
         a.x = sys[i].x;
         a.Ginv = f64 ? (const void *)sys[i].F->Ginv : (const void *)sys[i].F->Ginv32;
-        CUDA_OR(scr.alloc(&a.m, vec_n * tcs), KPP_ERR_CUDA);
-        CUDA_OR(cudaMemsetAsync(a.m, 0, vec_n * tcs, st), KPP_ERR_CUDA);
+        CUDA_OR(scr.alloc(&a.m, L.vec_n * tcs), KPP_ERR_CUDA);
         if (cd) {
             // v2 keeps two published copies of R_x (steps of even / odd index); v1 and v3 one
-            CUDA_OR(scr.alloc(&a.Rx, (v2 ? 2 : 1) * vec_r * tcs), KPP_ERR_CUDA);
-            CUDA_OR(scr.alloc(&a.Rm, vec_r * tcs), KPP_ERR_CUDA);
-            CUDA_OR(cudaMemsetAsync(a.Rm, 0, vec_r * tcs, st), KPP_ERR_CUDA);
-            if (!init_residual) {  // x0 = 0: R_x = -b
-                void *dst = (v2 && (t0 & 1)) ? (void *)((char *)a.Rx + vec_r * tcs) : a.Rx;
-                CUDA_OR(launch_negate_copy(vec_r, a.b, dst, f64, st), KPP_ERR_CUDA);
-            }
+            CUDA_OR(scr.alloc(&a.Rx, (L.kind == 2 ? 2 : 1) * L.vec_r * tcs), KPP_ERR_CUDA);
+            CUDA_OR(scr.alloc(&a.Rm, L.vec_r * tcs), KPP_ERR_CUDA);
         } else {
             a.Rx = a.Rm = nullptr;
         }
-        CUDA_OR(scr.alloc(&a.part, (v2 || v4 ? 2 : 1) * (size_t)G * s * KP * tcs), KPP_ERR_CUDA);
+        CUDA_OR(scr.alloc(&a.part, (L.kind == 2 || L.kind == 4 ? 2 : 1) * (size_t)G * s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc(&a.rbuf, (size_t)s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc(&a.ybuf, (size_t)s * KP * tcs), KPP_ERR_CUDA);
         CUDA_OR(scr.alloc((void **)&a.rpart, (size_t)G * KP * sizeof(double)), KPP_ERR_CUDA);
-        CUDA_OR(scr.alloc((void **)&a.sc, (size_t)k * sizeof(SolveScalars)), KPP_ERR_CUDA);
-        CUDA_OR(cudaMemcpyAsync(a.sc, sys[i].sc_host, (size_t)k * sizeof(SolveScalars), cudaMemcpyHostToDevice, st),
-                KPP_ERR_CUDA);
-        a.bar = bars + i;
-        a.err = errs + i;
+        if (sys[i].sc_dev) {
+            a.sc = sys[i].sc_dev;
+        } else {
+            CUDA_OR(scr.alloc((void **)&a.sc, (size_t)k * sizeof(SolveScalars)), KPP_ERR_CUDA);
+            CUDA_OR(cudaMemcpyAsync(a.sc, sys[i].sc_host, (size_t)k * sizeof(SolveScalars), cudaMemcpyHostToDevice, st),
+                    KPP_ERR_CUDA);
+        }
+        a.bar = L.bars + i;
+        a.err = L.errs + i;
         a.sys_id = sys[i].sys_id;
         a.t0 = t0;
     }
-    if (v4) {
+    if (L.kind == 4) {
         const size_t sb = sys4_bytes();
         h2.assign(sb * nsys, 0);
         for (int i = 0; i < nsys; ++i) {
@@ -271,48 +223,28 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
             const kpp_matrix &Ai = *sys[i].A;
             if (!make_tmap_2d(tm, Ai.data, dtype, Ai.cols, Ai.rows, Ai.ld, (uint32_t)stream_tk(dtype), (uint32_t)s, true)) {
                 set_error("cuTensorMapEncodeTiled failed for system %d", i);
-                rc = KPP_ERR_CUDA;
-                goto cleanup;
+                return KPP_ERR_CUDA;
             }
-            const SysArgs &a = args[i];
+            const SysArgs &a = L.args[i];
             sys4_fill(h2.data() + sb * i, tm, (const float *)a.b, (float *)a.x, (float *)a.m, (const float *)a.Ginv,
                       (float *)a.part, a.rpart, a.sc, a.bar, a.err, a.sys_id, a.t0);
         }
-        CUDA_OR(scr.alloc(&d_sys2, sb * nsys), KPP_ERR_CUDA);
-        if ((uintptr_t)d_sys2 & 127) {
-            set_error("descriptor buffer not 128-byte aligned");
-            rc = KPP_ERR_CUDA;
-            goto cleanup;
-        }
-        CUDA_OR(cudaMemcpyAsync(d_sys2, h2.data(), sb * nsys, cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
-        CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
-    } else if (v3) {
+    } else if (L.kind == 3) {
         const size_t sb = sys3_bytes();
-        const size_t mb = cd3_mail_bytes(s, KP, f64);
+        L.mail_bytes = cd3_mail_bytes(s, KP, f64);
         h2.assign(sb * nsys, 0);
         for (int i = 0; i < nsys; ++i) {
             alignas(128) unsigned char tm[128];
             const void *src = f64 ? (const void *)sys[i].F->W : sys[i].A->data;
             const int64_t ld = f64 ? sys[i].A->cols : sys[i].A->ld;
-            void *mail = nullptr;
-            CUDA_OR(scr.alloc(&mail, mb), KPP_ERR_CUDA);
-            CUDA_OR(cudaMemsetAsync(mail, 0, mb, st), KPP_ERR_CUDA);
+            CUDA_OR(scr.alloc(&L.mails[i], L.mail_bytes), KPP_ERR_CUDA);
             if (!make_tmap_2d(tm, src, dtype, sys[i].A->cols, sys[i].A->rows, ld, (uint32_t)CW, (uint32_t)s)) {
                 set_error("cuTensorMapEncodeTiled failed for system %d", i);
-                rc = KPP_ERR_CUDA;
-                goto cleanup;
+                return KPP_ERR_CUDA;
             }
-            sys3_fill(h2.data() + sb * i, args[i], tm, mail);
+            sys3_fill(h2.data() + sb * i, L.args[i], tm, L.mails[i]);
         }
-        CUDA_OR(scr.alloc(&d_sys2, sb * nsys), KPP_ERR_CUDA);
-        if ((uintptr_t)d_sys2 & 127) {
-            set_error("descriptor buffer not 128-byte aligned");
-            rc = KPP_ERR_CUDA;
-            goto cleanup;
-        }
-        CUDA_OR(cudaMemcpyAsync(d_sys2, h2.data(), sb * nsys, cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
-        CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
-    } else if (v2) {
+    } else if (L.kind == 2) {
         const size_t sb = sys2_bytes();
         h2.assign(sb * nsys, 0);
         for (int i = 0; i < nsys; ++i) {
@@ -320,44 +252,93 @@ static kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd,
             if (!make_tmap_2d(tm, sys[i].A->data, dtype, sys[i].A->cols, sys[i].A->rows, sys[i].A->ld, (uint32_t)CW,
                               (uint32_t)std::min(s, 256))) {
                 set_error("cuTensorMapEncodeTiled failed for system %d", i);
-                rc = KPP_ERR_CUDA;
-                goto cleanup;
+                return KPP_ERR_CUDA;
             }
-            sys2_fill(h2.data() + sb * i, args[i], tm);
+            sys2_fill(h2.data() + sb * i, L.args[i], tm);
         }
-        CUDA_OR(scr.alloc(&d_sys2, sb * nsys), KPP_ERR_CUDA);
-        if ((uintptr_t)d_sys2 & 127) {  // tensor maps must be 64-byte aligned in memory
+    }
+    if (L.kind >= 2) {
+        CUDA_OR(scr.alloc(&L.d_sys2, h2.size()), KPP_ERR_CUDA);
+        if ((uintptr_t)L.d_sys2 & 127) {  // tensor maps must be 64-byte aligned in memory
             set_error("descriptor buffer not 128-byte aligned");
-            rc = KPP_ERR_CUDA;
-            goto cleanup;
+            return KPP_ERR_CUDA;
         }
-        CUDA_OR(cudaMemcpyAsync(d_sys2, h2.data(), sb * nsys, cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
+        CUDA_OR(cudaMemcpyAsync(L.d_sys2, h2.data(), h2.size(), cudaMemcpyHostToDevice, st), KPP_ERR_CUDA);
         CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);  // h2 is pageable and local
     } else {
-        CUDA_OR(scr.alloc((void **)&d_args, nsys * sizeof(SysArgs)), KPP_ERR_CUDA);
-        CUDA_OR(cudaMemcpyAsync(d_args, args.data(), nsys * sizeof(SysArgs), cudaMemcpyHostToDevice, st),
+        CUDA_OR(scr.alloc((void **)&L.d_args, nsys * sizeof(SysArgs)), KPP_ERR_CUDA);
+        CUDA_OR(cudaMemcpyAsync(L.d_args, L.args.data(), nsys * sizeof(SysArgs), cudaMemcpyHostToDevice, st),
                 KPP_ERR_CUDA);
+        CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
     }
-    CUDA_OR(cudaEventCreate(&e0), KPP_ERR_CUDA);
-    CUDA_OR(cudaEventCreate(&e1), KPP_ERR_CUDA);
-    CUDA_OR(cudaEventRecord(e0, st), KPP_ERR_CUDA);
+cleanup:
+    return rc;
+}
+
+// Reset the per-launch state and launch the kernel (graph-capturable).
+kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st) {
+    kpp_status rc = KPP_OK;
+    CUDA_OR(cudaMemsetAsync(L.bars, 0, L.nsys * sizeof(unsigned), st), KPP_ERR_CUDA);
+    CUDA_OR(cudaMemsetAsync(L.errs, 0, L.nsys * sizeof(int), st), KPP_ERR_CUDA);
+    for (int i = 0; i < L.nsys; ++i) {
+        const SysArgs &a = L.args[i];
+        CUDA_OR(cudaMemsetAsync(a.m, 0, L.vec_n * L.tcs, st), KPP_ERR_CUDA);
+        if (L.cd) {
+            CUDA_OR(cudaMemsetAsync(a.Rm, 0, L.vec_r * L.tcs, st), KPP_ERR_CUDA);
+            if (!L.init_residual) {  // x0 = 0: R_x = -b (in the copy the first step reads)
+                if (L.kind == 2 && L.cm.t0_state) {
+                    // the first step is only known on the device: fill both published copies
+                    CUDA_OR(launch_negate_copy(L.vec_r, a.b, a.Rx, L.f64, st), KPP_ERR_CUDA);
+                    CUDA_OR(launch_negate_copy(L.vec_r, a.b, (char *)a.Rx + L.vec_r * L.tcs, L.f64, st), KPP_ERR_CUDA);
+                } else {
+                    void *dst = (L.kind == 2 && (L.t0 & 1)) ? (void *)((char *)a.Rx + L.vec_r * L.tcs) : a.Rx;
+                    CUDA_OR(launch_negate_copy(L.vec_r, a.b, dst, L.f64, st), KPP_ERR_CUDA);
+                }
+            }
+        }
+        if (L.kind == 3) CUDA_OR(cudaMemsetAsync(L.mails[i], 0, L.mail_bytes, st), KPP_ERR_CUDA);
+    }
     {
-        cudaError_t le = v4   ? launch_stream(dtype, d_sys2, nsys, cm, KP, st)
-                         : v3 ? launch_cd3(dtype, d_sys2, nsys, cm, KP, st)
-                         : v2 ? launch_solve2(dtype, cd, d_sys2, nsys, cm, KP, st)
-                              : launch_solve(dtype, f64, cd, d_args, nsys, cm, KP, st);
+        cudaError_t le = L.kind == 4   ? launch_stream(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
+                         : L.kind == 3 ? launch_cd3(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
+                         : L.kind == 2 ? launch_solve2(L.dtype, L.cd, L.d_sys2, L.nsys, L.cm, L.KP, st)
+                                       : launch_solve(L.dtype, L.f64, L.cd, L.d_args, L.nsys, L.cm, L.KP, st);
         if (le == cudaErrorCooperativeLaunchTooLarge) {
-            set_error("%d systems x %d CTAs do not fit co-resident on this GPU", nsys, G);
-            rc = KPP_ERR_UNSUPPORTED;
-            goto cleanup;
+            set_error("%d systems x %d CTAs do not fit co-resident on this GPU", L.nsys, L.cm.G);
+            return KPP_ERR_UNSUPPORTED;
         }
         CUDA_OR(le, KPP_ERR_CUDA);
     }
+cleanup:
+    return rc;
+}
+
+// Run the persistent kernel over nsys systems that share shape, dtype, s and k (one shot).
+kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd, int k, int s, double eta,
+                                 double tol, int adaptive, int confirm, int64_t max_iters, uint64_t seed, int grid,
+                                 bool init_residual, int64_t t0, cudaStream_t st, float *ms_out, int *err_out,
+                                 int variant, int *kind_out, int *G_out) {
+    kpp_status rc = KPP_OK;
+    const int nsys = (int)sys.size();
+    Scratch scr(st);
+    PersistentLaunch L;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<int> herr(nsys, 0);
+    rc = prepare_persistent(L, sys, dtype, cd, k, s, eta, tol, adaptive, confirm, max_iters, seed, grid,
+                            init_residual, t0, false, variant < 0 ? g_variant : variant, scr, st);
+    if (rc != KPP_OK) return rc;
+    if (kind_out) *kind_out = L.kind;
+    if (G_out) *G_out = L.cm.G;
+    CUDA_OR(cudaEventCreate(&e0), KPP_ERR_CUDA);
+    CUDA_OR(cudaEventCreate(&e1), KPP_ERR_CUDA);
+    CUDA_OR(cudaEventRecord(e0, st), KPP_ERR_CUDA);
+    rc = enqueue_persistent(L, st);
+    if (rc != KPP_OK) goto cleanup;
     CUDA_OR(cudaEventRecord(e1, st), KPP_ERR_CUDA);
     for (int i = 0; i < nsys; ++i)
-        CUDA_OR(cudaMemcpyAsync(sys[i].sc_host, args[i].sc, (size_t)k * sizeof(SolveScalars), cudaMemcpyDeviceToHost, st),
+        CUDA_OR(cudaMemcpyAsync(sys[i].sc_host, L.args[i].sc, (size_t)k * sizeof(SolveScalars), cudaMemcpyDeviceToHost, st),
                 KPP_ERR_CUDA);
-    CUDA_OR(cudaMemcpyAsync(herr.data(), errs, nsys * sizeof(int), cudaMemcpyDeviceToHost, st), KPP_ERR_CUDA);
+    CUDA_OR(cudaMemcpyAsync(herr.data(), L.errs, nsys * sizeof(int), cudaMemcpyDeviceToHost, st), KPP_ERR_CUDA);
     CUDA_OR(cudaStreamSynchronize(st), KPP_ERR_CUDA);
     if (ms_out) cudaEventElapsedTime(ms_out, e0, e1);
     for (int i = 0; i < nsys; ++i) {
@@ -373,7 +354,7 @@ cleanup:
     return rc;
 }
 
-static void init_scalars(std::vector<SolveScalars> &sc, int k, double rho0) {
+void init_scalars(std::vector<SolveScalars> &sc, int k, double rho0) {
     sc.assign(k, SolveScalars{});
     for (int c = 0; c < k; ++c) {
         sc[c].rho = rho0;
@@ -383,18 +364,15 @@ static void init_scalars(std::vector<SolveScalars> &sc, int k, double rho0) {
     }
 }
 
-static double default_eta(const kpp_params &p, int s, int64_t rows, int64_t cols) {
+double default_eta(const kpp_params &p, int s, int64_t rows, int64_t cols) {
     if (!std::isnan(p.eta)) return p.eta;
     return (double)s / (2.0 * (double)std::min(rows, cols));
 }
 
 static kpp_status worse(kpp_status a, kpp_status b) { return a != KPP_OK ? a : b; }
 
-// The solve of `nsys` systems with k right-hand sides each (FP64 b/x on the device).
-kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
-                                kpp_partition_t P, const kpp_factors_t *F, const kpp_params *pp, kpp_report *reps,
-                                cudaStream_t st, bool cd) {
-    clear_error();
+kpp_status validate_systems(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
+                            kpp_partition_t P, const kpp_factors_t *F, const kpp_params *pp, bool cd) {
     if (nsys < 1 || !A || !B || !X || !P || !F || !pp || k < 1 || k > 32) {
         set_error("invalid argument (nsys=%d, k=%d)", nsys, k);
         return KPP_ERR_ARG;
@@ -421,10 +399,31 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
             return KPP_ERR_ARG;
         }
     }
+    return KPP_OK;
+}
+
+// The solve of `nsys` systems with k right-hand sides each (FP64 b/x on the device).
+kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
+                                kpp_partition_t P, const kpp_factors_t *F, const kpp_params *pp, kpp_report *reps,
+                                cudaStream_t st, bool cd) {
+    clear_error();
+    {
+        kpp_status v = validate_systems(nsys, A, B, X, k, P, F, pp, cd);
+        if (v != KPP_OK) return v;
+    }
+    const kpp_params p = *pp;
+    const int s = P->s;
     const int dtype = A[0].dtype;
     const int64_t rows = A[0].rows, cols = A[0].cols;
     const double eta = default_eta(p, s, rows, cols);
     kpp_status rc = KPP_OK;
+    // launch shape: the caller's grid, the heuristic (0), or the autotuner (negative)
+    TuneChoice tune;
+    tune.grid = p.grid;
+    if (p.grid < 0) {
+        kpp_status tr = tune_launch(nsys, A, B, k, P, F, p, cd, st, tune);
+        if (tr != KPP_OK) return tr;
+    }
     std::vector<std::vector<SolveScalars>> sc(nsys);
     std::vector<int> errs(nsys, 0);
     std::vector<SysInput> in(nsys);
@@ -439,8 +438,8 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
     if (dtype == KPP_F64) {
         // plain FP64 path: the kernel iterates directly on the caller's b and x
         for (int i = 0; i < nsys; ++i) in[i] = SysInput{&A[i], B[i], X[i], &F[i]->f, p.sys_id + (uint32_t)i, sc[i].data()};
-        rc = run_persistent(in, dtype, cd, k, s, eta, p.tol, p.adaptive_rho, 1, p.max_iters, p.seed, p.grid,
-                            /*init_residual=*/true, 0, st, &ms, errs.data());
+        rc = run_persistent(in, dtype, cd, k, s, eta, p.tol, p.adaptive_rho, 1, p.max_iters, p.seed, tune.grid,
+                            /*init_residual=*/true, 0, st, &ms, errs.data(), tune.variant);
         for (int i = 0; i < nsys; ++i) {
             dev_ms[i] = ms;
             iters[i] = sc[i][0].t;
@@ -466,8 +465,8 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
                 CUDA_OR(launch_f64_to_f32(nc, X[i], d32[i], st), KPP_ERR_CUDA);
                 in[i] = SysInput{&A[i], b32[i], d32[i], &F[i]->f, p.sys_id + (uint32_t)i, sc[i].data()};
             }
-            rc = run_persistent(in, dtype, cd, k, s, eta, p.tol, p.adaptive_rho, 0, p.max_iters, p.seed, p.grid,
-                                true, 0, st, &ms, errs.data());
+            rc = run_persistent(in, dtype, cd, k, s, eta, p.tol, p.adaptive_rho, 0, p.max_iters, p.seed, tune.grid,
+                                true, 0, st, &ms, errs.data(), tune.variant);
             for (int i = 0; i < nsys; ++i) {
                 // x = double(x32): overwrite through the axpy of (x32 - x) is not exact; copy via zero + axpy
                 CUDA_OR(cudaMemsetAsync(X[i], 0, nc * sizeof(double), st), KPP_ERR_CUDA);
@@ -513,8 +512,8 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
                 }
                 std::vector<int> e2(act.size(), 0);
                 kpp_status ri = run_persistent(act, dtype, cd, k, s, eta, p.inner_tol, p.adaptive_rho, 0,
-                                               t_global + p.max_iters, p.seed, p.grid, false, t_global, st, nullptr,
-                                               e2.data());
+                                               t_global + p.max_iters, p.seed, tune.grid, false, t_global, st, nullptr,
+                                               e2.data(), tune.variant);
                 int64_t tmax = t_global;
                 for (size_t q = 0; q < act.size(); ++q) {
                     const int i = idx[q];

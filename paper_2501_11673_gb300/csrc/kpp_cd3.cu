@@ -145,7 +145,13 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
     const int cw = (int)(c1 - c0);
     const int CWs = (int)cm.CW;
     const int zeta = nb;
-    int64_t t = sa.t0;
+    int64_t t = cm.t0_state ? sa.sc[0].t : sa.t0;
+    int64_t t_end = cm.t0_state ? t + cm.max_iters : cm.max_iters;
+    if (cm.t0_state) {  // a system whose columns are all done does not iterate (t stays put)
+        int any = 0;
+        for (int c = 0; c < cm.k; ++c) any |= sa.sc[c].active;
+        if (!any) t_end = t;
+    }
 
     if (threadIdx.x < KP) {
         const int c = threadIdx.x;
@@ -260,13 +266,13 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
             }
         };
 
-        if (threadIdx.x == 0 && t < cm.max_iters) {
+        if (threadIdx.x == 0 && t < t_end) {
             issue(t, (int)(t & 1));
-            if (t + 1 < cm.max_iters) issue(t + 1, (int)((t + 1) & 1));
+            if (t + 1 < t_end) issue(t + 1, (int)((t + 1) & 1));
         }
-        if (t < cm.max_iters) publish(t);
+        if (t < t_end) publish(t);
 
-        while (t < cm.max_iters) {
+        while (t < t_end) {
             const int bf = (int)(t & 1);
             const int j = draw_block(cm.seed, t, sa.sys_id, nb);
             const int64_t S0 = (int64_t)j * s;
@@ -404,9 +410,9 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
                     __syncthreads();
                 }
             }
-            if (threadIdx.x == 0 && t + 2 < cm.max_iters) issue(t + 2, bf);
+            if (threadIdx.x == 0 && t + 2 < t_end) issue(t + 2, bf);
             // hand r_{t+1} to the other CTAs as early as possible
-            if (t + 1 < cm.max_iters) publish(t + 1);
+            if (t + 1 < t_end) publish(t + 1);
 
             const int64_t ph = t % (2 * (int64_t)zeta);
             const bool ckpt = (ph == 2 * zeta - 1);
@@ -445,7 +451,7 @@ __global__ void __launch_bounds__(NT, 1) cd3_kernel(const Sys3 *__restrict__ sys
                     }
                     __syncthreads();
                     // republish r_t (already published from the old R_x) and let everyone see it
-                    if (t < cm.max_iters) publish(t);
+                    if (t < t_end) publish(t);
                     if (!group_barrier(gs)) break;
                 }
                 if (threadIdx.x < k && st[threadIdx.x].active) checkpoint_column(st[threadIdx.x], cm, zeta);

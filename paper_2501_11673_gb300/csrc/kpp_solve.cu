@@ -56,6 +56,14 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SysArgs *__restrict_
     __shared__ int s_stop, s_need;
 
     GroupSync gs{sa.bar, sa.err, 0u, (unsigned)cm.G, cm.timeout_ns};
+    // first and end step (read before the first group barrier: CTA 0 rewrites sc at the end)
+    const int64_t t_begin = cm.t0_state ? sa.sc[0].t : sa.t0;
+    int64_t t_end = cm.t0_state ? t_begin + cm.max_iters : cm.max_iters;
+    if (cm.t0_state) {  // a system whose columns are all done does not iterate (t stays put)
+        int any = 0;
+        for (int c = 0; c < k; ++c) any |= sa.sc[c].active;
+        if (!any) t_end = t_begin;
+    }
 
     // my column chunk (aligned to 32-byte sectors of A)
     const int64_t c0 = min64((int64_t)g * cm.CW, cols);
@@ -103,8 +111,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SysArgs *__restrict_
 
     {
         const int zeta = nb;
-        int64_t t = sa.t0;
-        while (t < cm.max_iters) {
+        int64_t t = t_begin;
+        while (t < t_end) {
             // ---- sample the block (every CTA draws the same j) ----
             const int j = draw_block(cm.seed, t, sa.sys_id, nb);
             const int64_t S0 = (int64_t)j * s;
@@ -359,7 +367,9 @@ template <typename TA>
 __global__ void __launch_bounds__(256) residual_kernel(const TA *__restrict__ A, int64_t lda, int64_t rows,
                                                        int64_t cols, int k, const double *__restrict__ b,
                                                        const double *__restrict__ x, float *__restrict__ r32,
-                                                       double *__restrict__ part /* gridDim.x x k */) {
+                                                       double *__restrict__ part /* gridDim.x x k */,
+                                                       const int *__restrict__ skip) {
+    if (skip && *skip) return;  // the system is already done (batched plans)
     constexpr int V = Vec16<TA>::n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     extern __shared__ double xs[];
@@ -452,12 +462,12 @@ __global__ void __launch_bounds__(256) residual_kernel(const TA *__restrict__ A,
 
 template <typename TA>
 static void launch_res_t(const kpp_matrix &A, int k, const double *b, const double *x, float *r32, double *part,
-                         int grid, cudaStream_t st) {
+                         int grid, cudaStream_t st, const int *skip) {
     const bool sm = (k == 1) && x && A.cols <= RES_SMEM_COLS;
     const size_t smem = sm ? (size_t)A.cols * sizeof(double) : 0;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(residual_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    residual_kernel<TA><<<grid, 256, smem, st>>>((const TA *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part);
+    residual_kernel<TA><<<grid, 256, smem, st>>>((const TA *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part, skip);
 }
 
 __global__ void axpy_f32_to_f64_kernel(int64_t n, const float *__restrict__ d, double *__restrict__ x) {
@@ -539,11 +549,11 @@ cudaError_t launch_residual(const kpp_matrix &A, int k, const double *b, const d
 }
 
 cudaError_t launch_residual_grid(const kpp_matrix &A, int k, const double *b, const double *x, float *r32,
-                                 double *part, int grid, cudaStream_t st) {
+                                 double *part, int grid, cudaStream_t st, const int *skip) {
     switch (A.dtype) {
-        case KPP_F64: launch_res_t<double>(A, k, b, x, r32, part, grid, st); break;
-        case KPP_F32: launch_res_t<float>(A, k, b, x, r32, part, grid, st); break;
-        default: launch_res_t<__nv_bfloat16>(A, k, b, x, r32, part, grid, st);
+        case KPP_F64: launch_res_t<double>(A, k, b, x, r32, part, grid, st, skip); break;
+        case KPP_F32: launch_res_t<float>(A, k, b, x, r32, part, grid, st, skip); break;
+        default: launch_res_t<__nv_bfloat16>(A, k, b, x, r32, part, grid, st, skip);
     }
     return cudaGetLastError();
 }

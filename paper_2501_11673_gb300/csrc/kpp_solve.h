@@ -50,6 +50,7 @@ struct Common {
     int64_t max_iters;
     uint64_t seed;
     uint64_t timeout_ns;
+    int t0_state;          // 1: start at sc[0].t (written by the previous launch) and run max_iters more steps
 };
 
 size_t solve_smem_bytes(int s, int KP, int64_t CW, size_t tc_size);
@@ -61,8 +62,9 @@ cudaError_t launch_sample_blocks(uint64_t seed, uint32_t sys, int64_t t0, int64_
                                  cudaStream_t st);
 cudaError_t launch_residual(const kpp_matrix &A, int k, const double *b, const double *x, float *r32, double *part,
                             cudaStream_t st);
+// skip (device, may be null): the kernel returns at once when *skip != 0
 cudaError_t launch_residual_grid(const kpp_matrix &A, int k, const double *b, const double *x, float *r32,
-                                 double *part, int grid, cudaStream_t st);
+                                 double *part, int grid, cudaStream_t st, const int *skip = nullptr);
 cudaError_t launch_axpy(int64_t n, const float *d, double *x, cudaStream_t st);
 cudaError_t launch_f64_to_f32(int64_t n, const double *a, float *o, cudaStream_t st);
 cudaError_t launch_negate_copy(size_t n, const void *src, void *dst, bool f64, cudaStream_t st);

@@ -115,7 +115,13 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
     const int cw = (int)(c1 - c0);
     const int CWs = (int)cm.CW;  // leading dimension of the shared tile
     const int zeta = nb;
-    int64_t t = sa.t0;
+    int64_t t = cm.t0_state ? sa.sc[0].t : sa.t0;
+    int64_t t_end = cm.t0_state ? t + cm.max_iters : cm.max_iters;
+    if (cm.t0_state) {  // a system whose columns are all done does not iterate (t stays put)
+        int any = 0;
+        for (int c = 0; c < cm.k; ++c) any |= sa.sc[c].active;
+        if (!any) t_end = t;
+    }
     TC *const Rx0 = (TC *)sa.Rx;  // two published copies of R_x: Rx0 + parity * rows * k
 #define RXP(par) (Rx0 + (size_t)(par) * rows * k)
 
@@ -255,18 +261,18 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             s_keep[threadIdx.x] = (TC)((threadIdx.x < k && st[threadIdx.x].active) ? 1 : 0);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && t < cm.max_iters) {
+        if (threadIdx.x == 0 && t < t_end) {
             issue(t, (int)(t & 1));
-            if (t + 1 < cm.max_iters) issue(t + 1, (int)((t + 1) & 1));
+            if (t + 1 < t_end) issue(t + 1, (int)((t + 1) & 1));
             if (DY) issue_rows(t);
         }
-        if (!CD && t < cm.max_iters) {
+        if (!CD && t < t_end) {
             if (!wait_buf((int)(t & 1))) goto drain;
             partial(t);
             if (!group_barrier(gs)) goto drain;
         }
 
-        while (t < cm.max_iters) {
+        while (t < t_end) {
             const int bf = (int)(t & 1);
             const int j = draw_block(cm.seed, t, sa.sys_id, nb);
             const int64_t S0 = (int64_t)j * s;
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
                         for (int c = 0; c < KP; ++c) ybuf[(size_t)a * KP + c] = acc[c];
                 }
                 __syncthreads();
-                if (threadIdx.x == 0 && t + 1 < cm.max_iters) issue_rows(t + 1);
+                if (threadIdx.x == 0 && t + 1 < t_end) issue_rows(t + 1);
                 if (!group_barrier(gs)) break;
                 for (int e = threadIdx.x; e < len * KP; e += NT) s_y[e] = __ldcg(ybuf + e);
                 __syncthreads();
@@ -433,7 +439,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
                 }
             }
             // buffer bf is free: prefetch step t+2 into it
-            if (threadIdx.x == 0 && t + 2 < cm.max_iters) issue(t + 2, bf);
+            if (threadIdx.x == 0 && t + 2 < t_end) issue(t + 2, bf);
             const int64_t ph = t % (2 * (int64_t)zeta);
             const bool ckpt = (ph == 2 * zeta - 1);
             if (CD) {
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             t += 1;
             if (!CD) {
                 // next block's partial residual from the updated chunk
-                if (t < cm.max_iters) {
+                if (t < t_end) {
                     if (!wait_buf((int)(t & 1))) break;
                     partial(t);
                 }

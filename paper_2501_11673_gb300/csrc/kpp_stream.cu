@@ -97,7 +97,13 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
     const int64_t c1 = min64(c0 + cm.CW, cols);
     const int nt = (int)((c1 - c0) / TK);  // whole tiles (cols and CW are multiples of TK)
     const int zeta = nb;
-    const int64_t t0 = sys.t0;
+    const int64_t t0 = cm.t0_state ? sys.sc[0].t : sys.t0;
+    int64_t t_end = cm.t0_state ? t0 + cm.max_iters : cm.max_iters;
+    if (cm.t0_state) {  // a system whose columns are all done does not iterate (t stays put)
+        int any = 0;
+        for (int c = 0; c < cm.k; ++c) any |= sys.sc[c].active;
+        if (!any) t_end = t0;
+    }
 
     if (tid < KP) {
         ColState cs = {};
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
         // X / M slices were last written by bulk stores of this CTA, waited for before every refill.
         auto issue = [&](int64_t q) {
             const int64_t t = t0 + q / (2 * nt);
-            if (t >= cm.max_iters) return;
+            if (t >= t_end) return;
             const int pass = (int)((q / nt) & 1);
             const int jt = (int)(q % nt);
             const int stg = (int)(q % ST_STAGES);
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
                 if (q < 2 * nt) issue(q);
         int64_t q = 0;
         int64_t t = t0;
-        while (t < cm.max_iters) {
+        while (t < t_end) {
             const int j = draw_block(cm.seed, t, sys.sys_id, nb);
             const int64_t S0 = (int64_t)j * s;
             const int len = (int)min64(s, rows - S0);

@@ -33,7 +33,10 @@ EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_par
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
            "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_block_gram", "kpp_server_create", "kpp_server_add_matrix",
            "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_destroy",
-           "cdpp_solve_batched", "kpp_build_info"]
+           "cdpp_solve_batched", "kpp_plan_create", "kpp_plan_launch", "kpp_plan_report", "kpp_plan_info",
+           "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
+           "kpp_tune_cache_load", "kpp_build_info"]
+GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
 
 class KppError(RuntimeError):
@@ -129,6 +132,20 @@ def load(path: str | None = None):
         lib.kpp_block_gram.restype = ctypes.c_int
         for name in ("kpp_set_kernel_variant", "cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
                      "kpp_solve_host", "kpp_rel_residual", "kpp_solve_batched"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib.kpp_plan_create.argtypes = [i32, ctypes.POINTER(Matrix), ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
+                                        vp, ctypes.POINTER(vp), ctypes.POINTER(Params), i32, vp, ctypes.POINTER(vp)]
+        lib.kpp_plan_launch.argtypes = [vp, vp]
+        lib.kpp_plan_report.argtypes = [vp, ctypes.POINTER(Report), vp]
+        lib.kpp_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.kpp_plan_destroy.argtypes = [vp]
+        lib.kpp_plan_destroy.restype = None
+        lib.kpp_tune_cache_size.restype = i64
+        lib.kpp_tune_cache_clear.restype = None
+        lib.kpp_tune_cache_save.argtypes = [ctypes.c_char_p]
+        lib.kpp_tune_cache_load.argtypes = [ctypes.c_char_p]
+        for name in ("kpp_plan_create", "kpp_plan_launch", "kpp_plan_report", "kpp_plan_info", "kpp_tune_cache_save",
+                     "kpp_tune_cache_load"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -301,6 +318,65 @@ def kpp_solve_batched(As: list, Bs: list, Xs: list, P: Partition, Fs: list, prm:
     rc = fn(n, mats, bp, xp, k, P.handle, fp, ctypes.byref(prm), reps, _stream_ptr(stream))
     _check(rc, allow=(ERR_NO_CONVERGENCE,) if allow_no_conv else ())
     return list(reps)
+
+
+class Plan:
+    """A prepared batched solve (kpp_plan_create): systems, scratch and launch shape fixed once.
+    launch() enqueues the whole solve with kernels and memsets only, so it can be captured into a
+    torch.cuda.CUDAGraph and replayed; report() synchronises and returns nsys * k reports."""
+
+    def __init__(self, As: list, Bs: list, Xs: list, P: Partition, Fs: list, prm: Params, cd: bool = False,
+                 stream=None):
+        self._lib = load()
+        n = len(As)
+        self.nsys = n
+        self.k = Bs[0].shape[1] if Bs[0].dim() == 2 else 1
+        self._keep = (As, Bs, Xs, P, Fs)  # the plan holds their device addresses
+        mats = (Matrix * n)(*[matrix(a) for a in As])
+        bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in Bs])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Xs])
+        fp = (ctypes.c_void_p * n)(*[f.handle.value for f in Fs])
+        self.handle = ctypes.c_void_p()
+        _check(self._lib.kpp_plan_create(n, mats, bp, xp, self.k, P.handle, fp, ctypes.byref(prm), 1 if cd else 0,
+                                         _stream_ptr(stream), ctypes.byref(self.handle)))
+
+    def launch(self, stream=None) -> None:
+        _check(self._lib.kpp_plan_launch(self.handle, _stream_ptr(stream)))
+
+    def report(self, stream=None, allow_no_conv: bool = False) -> list:
+        reps = (Report * (self.nsys * self.k))()
+        rc = self._lib.kpp_plan_report(self.handle, reps, _stream_ptr(stream))
+        _check(rc, allow=(ERR_NO_CONVERGENCE,) if allow_no_conv else ())
+        return list(reps)
+
+    def info(self) -> dict:
+        kern, grid, var = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.kpp_plan_info(self.handle, ctypes.byref(kern), ctypes.byref(grid), ctypes.byref(var)))
+        return {"kernel": kern.value, "grid": grid.value, "variant": var.value}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self._lib.kpp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def tune_cache_size() -> int:
+    return int(load().kpp_tune_cache_size())
+
+
+def tune_cache_clear() -> None:
+    load().kpp_tune_cache_clear()
+
+
+def tune_cache_save(path: str) -> None:
+    _check(load().kpp_tune_cache_save(str(path).encode()))
+
+
+def tune_cache_load(path: str) -> None:
+    _check(load().kpp_tune_cache_load(str(path).encode()))
 
 
 def solve_host(A_np, b_np, x_np, s: int, mode: int, prm: Params, stream=None) -> Report:

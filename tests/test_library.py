@@ -52,3 +52,31 @@ def test_host_only_entry_points(lib):
 
 def test_build_targets_sm_103a_only():
     assert kbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_plan_handles_and_tune_cache_on_the_host(lib, tmp_path):
+    """Null plan handles are refused without touching the device; the autotuner cache file round-trips
+    and a malformed file loads nothing."""
+    assert lib.kpp_plan_launch(None, None) == kpp.ERR_ARG
+    assert lib.kpp_plan_report(None, None, None) == kpp.ERR_ARG
+    assert lib.kpp_plan_info(None, None, None, None) == kpp.ERR_ARG
+    lib.kpp_plan_destroy(None)
+    kpp.tune_cache_clear()
+    assert kpp.tune_cache_size() == 0
+    good = tmp_path / "cache.txt"
+    good.write_text("# comment\nsm103-n152:r4096:c4096:d0:s64:k1:m1:n1:v3 3 96\nsm103-n152:r10:c10:d1:s2:k1:m0:n1:v3 2 1\n")
+    kpp.tune_cache_load(good)
+    assert kpp.tune_cache_size() == 2
+    out = tmp_path / "out.txt"
+    kpp.tune_cache_save(out)
+    lines = [ln for ln in out.read_text().splitlines() if not ln.startswith("#")]
+    assert sorted(lines) == sorted(["sm103-n152:r4096:c4096:d0:s64:k1:m1:n1:v3 3 96",
+                                    "sm103-n152:r10:c10:d1:s2:k1:m0:n1:v3 2 1"])
+    kpp.tune_cache_clear()
+    bad = tmp_path / "bad.txt"
+    bad.write_text("key 3 96\nkey2 7 1\n")  # generation 7 does not exist
+    with pytest.raises(kpp.KppError):
+        kpp.tune_cache_load(bad)
+    assert kpp.tune_cache_size() == 0
+    with pytest.raises(kpp.KppError):
+        kpp.tune_cache_load(tmp_path / "missing.txt")
