@@ -1,21 +1,31 @@
 #!/usr/bin/env python
 """Benchmark of the Kaczmarz++ / CD++ block-step library on one GB300 (or N, one rank per GPU).
 
-A step is one complete solve through the C ABI: the factor phase (kpp_factor_blocks: memoised
-per-block Cholesky factors) and the iteration (cdpp_solve / kpp_solve) to |Ax-b|/|b| <= 1e-8,
-confirmed by the FP64 true residual.  Inputs are resident in HBM before the timed region; L2 is
-flushed (512 MiB write) between steps, and the flush is outside each step's event pair.
+A step is one complete solve through the C ABI: the factor phase (memoised per-block factors,
+kpp_factor_blocks) and the iteration to |Ax-b|/|b| <= 1e-8, confirmed by the FP64 true residual.
+Inputs are resident in HBM before the timed region; L2 is flushed (512 MiB write) between steps,
+outside each step's event pair.
 
-Workloads (synthetic, seeded; see paper_2501_11673_gb300/workloads.py):
-  cdpp4096 (default): CD++ FP64 on SPD n=4096, 50 outliers 1e2..1e4 over U[1,10], s=64, lambda=1e-4
-  kpp2000:            K++ FP64 on 2000x200 LS, 10 outliers 1e2..1e3 over U[1,2], s=20, lambda=1e-3
+Workloads (synthetic and seeded; recipes in paper_2501_11673_gb300/workloads.py):
+  cdpp4096 (default)  CD++ FP64, dense SPD n=4096, 50 outliers 1e2..1e4 over U[1,10], s=64, lambda=1e-4
+  kpp2000             K++ FP64, 2000x200 consistent LS, 10 outliers 1e2..1e3 over U[1,2], s=20, lambda=1e-3
+  mixed262144         K++ on 262144x4096 LS stored BF16 (--storage f32 for FP32), 100 outliers 10..1000
+                      over U[0.5,1], s=512, lambda=1e-3, FP32 iterations + FP64 refinement, b = A x*
+                      (--noisy: b = A x* + 1e-6 N(0,I); the attained residual is reported, no tolerance)
+  batched64           64 systems 2048x65536 FP32 (20 rows x100), 8 right-hand sides each, s=256,
+                      lambda = 1e-3 median |a_i|^2, refinement; one autotuned plan replayed as a CUDA graph
+  serving             1024 CD++ requests, Poisson arrivals (2 ms mean gap) over a catalog of 32 SPD matrices
+                      (n log-uniform 512..8192, BF16 / FP32), k = 1..32, refinement, 120 GiB budget
+  cdpp4096-f32 / -bf16  the cdpp4096 system stored FP32 / BF16 with FP64 refinement
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a bounded sample of
+the same workload instead (rank 0 only).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -32,6 +42,17 @@ if ROOT not in sys.path:
 from paper_2501_11673_gb300 import workloads as W  # noqa: E402
 
 METRIC = "time-to-1e-8 rel. residual & block-iters/s"
+SERVING_METRIC = "solves/s + p99 latency"
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the same
+# kernel build and workload (the summaries under profiles/ give the commands).  Absent: not captured.
+NCU_TRAFFIC_PER_LAUNCH = {
+    "cd3_kernel/cdpp4096": 6.700243e9 + 15.2768e6,  # profiles/cd3_kernel_cdpp4096.md
+}
+
+
+def _log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
 def _peaks():
@@ -42,31 +63,9 @@ def _peaks():
         return {}
 
 
-def workload(name: str):
-    if name == "cdpp4096":
-        sy = W.cdpp_fp64_spd()
-        desc = ("CD++ FP64, dense SPD n=4096 = U diag(sigma) U^T (U Haar; 50 outliers log-spaced 1e2..1e4 + "
-                "4046 ~U[1,10]), b~N(0,I), s=64 contiguous, lambda=1e-4, tol=1e-8, x0=0")
-        return sy, True, desc
-    if name == "kpp2000":
-        sy = W.kpp_fp64_2000x200()
-        desc = ("K++ FP64, 2000x200 consistent LS A=Z D V^T (10 outliers 1e2..1e3 + 190 ~U[1,2]), s=20, "
-                "lambda=1e-3, tol=1e-8, x0=0")
-        return sy, False, desc
-    raise SystemExit(f"unknown workload {name}")
-
-
-def per_iter_cost(sy, cd: bool):
-    """Algorithmic FP64 flops and HBM bytes of one block iteration (k = 1)."""
-    m, n = sy.A.shape
-    s = sy.s
-    if cd:
-        flops = 2 * s * n + 2 * s * s + 10 * n + 2 * s
-        byts = 8 * (s * n + s * s + 8 * n + s)
-    else:
-        flops = 4 * s * n + 2 * s * s + 6 * n + 2 * s
-        byts = 8 * (s * n + s * s + 4 * n + 2 * s)
-    return flops, byts
+def fp64_peak_gflops(peaks):
+    """FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x the maximum SM clock."""
+    return 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
 
 
 class ClockSampler:
@@ -125,19 +124,576 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------------------------------------
+# Oracle samples (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------------------------
+
+def _oracle_iter_rate(A, b, L, s, cd, lam, seed, budget_s, it0=64):
+    """Block iterations per second of the oracle as it stands (one host thread, no stop test), on a
+    sample grown until it takes about a quarter of `budget_s`."""
+    import oracle
+    it = it0
+    while True:
+        t0 = time.perf_counter()
+        oracle.run(A, b, L, s, cd=cd, lam=lam, tol=0.0, max_iters=it, seed=seed, confirm=False)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or it >= (1 << 22):
+            return it / dt, it, dt
+        it *= 4
+
+
+def _oracle_factors(A, s, lam, cd):
+    """All-block factors by the oracle (small systems)."""
+    import oracle
+    return oracle.cdpp_factor(A, s, lam) if cd else oracle.kpp_factor(A, s, lam)
+
+
+def _factors_numpy_gram(A, s, lam):
+    """K++ factors for a large sample: block Grams by numpy, Cholesky by the oracle (factor phase is
+    not part of the timed oracle sample)."""
+    import oracle
+    m = A.shape[0]
+    nb = -(-m // s)
+    L = np.zeros((nb, s, s))
+    for j in range(nb):
+        As = A[j * s:(j + 1) * s]
+        ln = As.shape[0]
+        L[j].reshape(-1)[:ln * ln] = oracle.cholesky(As @ As.T + lam * np.eye(ln)).reshape(-1)
+    return L
+
+
+# ---------------------------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------------------------
+
+class Workload:
+    unit = "block-iters/s"
+    metric = METRIC
+    dtype = "f64"
+    kernel = ""
+
+    def setup(self, kpp, torch, rank):
+        raise NotImplementedError
+
+    def step(self) -> dict:
+        """One step; returns units (the metric's numerator), ok, and what the roofline needs."""
+        raise NotImplementedError
+
+    def roofline(self, steps, peaks) -> dict:
+        raise NotImplementedError
+
+    def e2e(self):
+        return None
+
+    def cpu_baseline(self, budget_s):
+        return None
+
+    def extra(self, steps) -> dict:
+        return {}
+
+
+def _hbm_roof(kernel, byts_per_launch, launch_ms, peaks, traffic_key, per_iter, extra=None):
+    ach = byts_per_launch / (launch_ms / 1e3) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+           "traffic": NCU_TRAFFIC_PER_LAUNCH.get(traffic_key), "launch_ms": launch_ms, "per_iter": per_iter,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    out.update(extra or {})
+    return out
+
+
+class SingleFP64(Workload):
+    """One FP64 system, factor + solve per step (CD++ n=4096, or K++ 2000x200)."""
+
+    def __init__(self, name):
+        self.name = name
+        self.cd = name.startswith("cdpp4096")
+        if self.cd:
+            self.sy = W.cdpp_fp64_spd()
+            self.desc = ("CD++ FP64, dense SPD n=4096 = U diag(sigma) U^T (U Haar; 50 outliers log-spaced 1e2..1e4 + "
+                         "4046 ~U[1,10]), b~N(0,I), s=64 contiguous, lambda=1e-4, tol=1e-8, x0=0")
+            self.kernel = "cd3_kernel"
+        else:
+            self.sy = W.kpp_fp64_2000x200()
+            self.desc = ("K++ FP64, 2000x200 consistent LS A=Z D V^T (10 outliers 1e2..1e3 + 190 ~U[1,2]), s=20, "
+                         "lambda=1e-3, tol=1e-8, x0=0")
+            self.kernel = "solve2_kernel"
+        self.seed = 1 if self.cd else 0
+
+    def setup(self, kpp, torch, rank):
+        self.kpp, self.torch = kpp, torch
+        sy = self.sy
+        m, n = sy.A.shape
+        self.Ad = torch.as_tensor(sy.A, device="cuda")
+        self.bd = torch.as_tensor(sy.b, device="cuda")
+        self.x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        self.P = kpp.Partition(m, sy.s)
+        self.prm = kpp.params(lam=sy.lam, tol=sy.tol, seed=self.seed, sys_id=rank)
+        self.solve = kpp.cdpp_solve if self.cd else kpp.kpp_solve
+
+    def step(self):
+        kpp = self.kpp
+        self.x.zero_()
+        F = kpp.Factors(self.Ad, self.P, self.sy.lam, 1 if self.cd else 0)
+        rep = self.solve(self.Ad, self.bd, self.x, self.P, F, self.prm)
+        del F
+        return {"units": rep.iters, "ok": rep.status == kpp.OK and rep.rel_res_true <= self.sy.tol,
+                "kernel_ms": rep.kernel_ms, "kernel_launches": rep.launches, "iters": rep.iters,
+                "outer": rep.outer, "rel_res": rep.rel_res_true}
+
+    def per_iter(self):
+        """Algorithmic FP64 flops and bytes of one block iteration (k = 1)."""
+        m, n = self.sy.A.shape
+        s = self.sy.s
+        if self.cd:
+            # u = W_S^T r_S from the memoised W = G^-1 A_S (s x n), R_x and R_m read + written, x_S, r_S
+            return 2 * s * n + 2 * s * s + 10 * n + 2 * s, 8 * (s * n + s * s + 8 * n + s)
+        # r = A_S x (s x n), w = A_S^T y (second read of A_S from L2), x and m read + written
+        return 4 * s * n + 2 * s * s + 6 * n + 2 * s, 8 * (s * n + s * s + 4 * n + 2 * s)
+
+    def roofline(self, steps, peaks):
+        flops, byts = self.per_iter()
+        iters = statistics.mean(st["iters"] for st in steps)
+        kms = statistics.mean(st["kernel_ms"] for st in steps)
+        launches = statistics.mean(st["kernel_launches"] for st in steps)
+        per_launch_ms = kms / max(launches, 1)
+        ach = iters / launches * flops / (per_launch_ms / 1e3) / 1e9
+        achb = iters / launches * byts / (per_launch_ms / 1e3) / 1e9
+        pk = fp64_peak_gflops(peaks)
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        return {"kernel": self.kernel, "bound": "alu", "achieved": ach, "peak": pk, "unit": "GFLOP/s",
+                "frac": ach / pk, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(f"{self.kernel}/{self.name}"),
+                "launch_ms": per_launch_ms, "per_iter": {"flops": flops, "bytes": byts},
+                "peak_source": "derived: FP64 FMA pipe, 152 SMs x 2 FMA/clk x 2 flop x sm_max_mhz "
+                               "(MEASURED_PEAKS.json sm_max_mhz)",
+                "hbm_view": {"achieved": achb, "peak": hbm, "unit": "GB/s", "frac": achb / hbm,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
+
+    def e2e(self):
+        kpp = self.kpp
+        A_h = np.ascontiguousarray(self.sy.A)
+        b_h = self.sy.b.copy()
+        n = A_h.shape[1]
+        ets = []
+        for _ in range(2):
+            x_h = np.zeros(n)
+            t0 = time.perf_counter()
+            rep = kpp.solve_host(A_h, b_h, x_h, self.sy.s, 1 if self.cd else 0, self.prm)
+            ets.append(time.perf_counter() - t0)
+            assert rep.status == kpp.OK
+        return {"value": rep.iters / ets[-1], "unit": self.unit,
+                "h2d_bytes_per_step": A_h.nbytes + b_h.nbytes + x_h.nbytes, "d2h_bytes_per_step": x_h.nbytes,
+                "time_to_tol_ms": 1e3 * ets[-1], "note": "host (pageable) buffers through kpp_solve_host"}
+
+    def cpu_baseline(self, budget_s):
+        L = _oracle_factors(self.sy.A, self.sy.s, self.sy.lam, self.cd)
+        v, it, dt = _oracle_iter_rate(self.sy.A, self.sy.b, L, self.sy.s, self.cd, self.sy.lam, self.seed,
+                                      budget_s, it0=256)
+        return {"value": v, "unit": self.unit, "cores": 1, "kind": "oracle",
+                "sample": f"{it} block iterations of the same workload, FP64 C oracle, one host thread "
+                          f"({dt:.1f} s; factor phase excluded)"}
+
+
+class MixedSPD(SingleFP64):
+    """The cdpp4096 system stored FP32 / BF16 with FP32 iterations and FP64 refinement."""
+
+    def __init__(self, storage):
+        super().__init__("cdpp4096")
+        self.storage = storage
+        self.name = f"cdpp4096-{storage}"
+        self.dtype = "f32"
+        self.desc = (f"CD++ on the n=4096 SPD system of the default workload stored {storage.upper()} "
+                     "(the stored matrix is the system), FP32 iterations + FP64 refinement (inner tol 1e-3), s=64, "
+                     "lambda=1e-4, tol 1e-8, x0=0")
+
+    def setup(self, kpp, torch, rank):
+        super().setup(kpp, torch, rank)
+        self.Ad = self.Ad.to(torch.float32 if self.storage == "f32" else torch.bfloat16)
+        self.prm = kpp.params(lam=self.sy.lam, tol=self.sy.tol, seed=1, sys_id=rank, refine=1, inner_tol=1e-3)
+
+    def per_iter_bytes(self):
+        n, s = self.sy.A.shape[1], self.sy.s
+        esz = 4 if self.storage == "f32" else 2
+        return s * n * esz + s * s * 4 + 4 * (8 * n + s)
+
+    def roofline(self, steps, peaks):
+        byts = self.per_iter_bytes()
+        iters = statistics.mean(st["iters"] for st in steps)
+        kms = statistics.mean(st["kernel_ms"] for st in steps)
+        launches = statistics.mean(st["kernel_launches"] for st in steps)
+        return _hbm_roof(self.kernel, iters * byts / launches, kms / launches, peaks, f"{self.kernel}/{self.name}",
+                         {"bytes": byts})
+
+    def extra(self, steps):
+        return {"outer_steps": steps[-1]["outer"]}
+
+    def e2e(self):
+        return None
+
+    def cpu_baseline(self, budget_s):
+        return None
+
+
+class MixedLS(Workload):
+    """K++ on a 262144 x 4096 LS stored BF16 / FP32, FP32 iterations + FP64 refinement."""
+
+    kernel = "solve2_kernel"
+
+    def __init__(self, storage="bf16", noisy=False, m=262144, n=4096, s=512):
+        self.storage, self.noisy = storage, noisy
+        self.m, self.n, self.s = m, n, s
+        self.lam = 1e-3
+        self.tol = 1e-8
+        self.dtype = "f32"
+        noise = ("b = A_stored x* + 1e-6 N(0,I) (noisy variant: attained residual reported, no tolerance)"
+                 if noisy else "b = A_stored x* (noise-free headline)")
+        self.desc = (f"K++ mixed precision, {m}x{n} LS A=Z D V^T stored {storage.upper()} (Z~N(0,1/m), V Haar, "
+                     f"100 outliers log-spaced 10..1000 + U[0.5,1]), {noise}, s={s}, lambda=1e-3, "
+                     "FP32 iterations + FP64 refinement (inner tol 1e-3), tol 1e-8, x0=0")
+
+    def setup(self, kpp, torch, rank):
+        self.kpp, self.torch = kpp, torch
+        self.A, self.b, self.x_star, _ = W.torch_lowrank_ls(self.m, self.n, 100, 10.0, 1000.0, 0.5, 1.0,
+                                                           seed=2 + 1000 * rank, dtype=self.storage,
+                                                           noise=1e-6 if self.noisy else 0.0)
+        self.x = torch.zeros(self.n, dtype=torch.float64, device="cuda")
+        self.P = kpp.Partition(self.m, self.s)
+        self.prm = kpp.params(lam=self.lam, tol=self.tol, refine=1, inner_tol=1e-3, seed=0, sys_id=rank,
+                              max_outer=4 if self.noisy else 20, max_iters=20000 if self.noisy else 1000000)
+
+    def step(self):
+        kpp = self.kpp
+        self.x.zero_()
+        F = kpp.Factors(self.A, self.P, self.lam, 0)
+        rep = kpp.kpp_solve(self.A, self.b, self.x, self.P, F, self.prm, allow_no_conv=self.noisy)
+        del F
+        ok = rep.rel_res_true <= self.tol if not self.noisy else math.isfinite(rep.rel_res_true)
+        return {"units": rep.iters, "ok": ok, "kernel_ms": rep.kernel_ms, "kernel_launches": rep.launches,
+                "iters": rep.iters, "outer": rep.outer, "rel_res": rep.rel_res_true}
+
+    def per_iter_bytes(self):
+        esz = 2 if self.storage == "bf16" else 4
+        s, n = self.s, self.n
+        # A_S once, G_S^-1 (FP32), x and m read + written (FP32), r_S and y
+        return s * n * esz + s * s * 4 + 4 * n * 4 + 2 * s * 4
+
+    def roofline(self, steps, peaks):
+        byts = self.per_iter_bytes()
+        iters = statistics.mean(st["iters"] for st in steps)
+        kms = statistics.mean(st["kernel_ms"] for st in steps)
+        launches = statistics.mean(st["kernel_launches"] for st in steps)
+        return _hbm_roof(self.kernel, iters * byts / launches, kms / launches, peaks,
+                         f"{self.kernel}/mixed262144-{self.storage}", {"bytes": byts})
+
+    def extra(self, steps):
+        x_err = float(((self.x - self.x_star).norm() / self.x_star.norm()).item())
+        out = {"outer_steps": steps[-1]["outer"], "x_rel_err_vs_x_star": x_err}
+        if self.noisy:
+            out["attained_rel_res"] = steps[-1]["rel_res"]
+        return out
+
+    def e2e(self):
+        """Host buffers (pinned) in and out around the public calls: A, b to the device, factor, solve, x back."""
+        kpp, torch = self.kpp, self.torch
+        A_h = self.A.cpu().pin_memory()
+        b_h = self.b.cpu().pin_memory()
+        x_h = torch.zeros(self.n, dtype=torch.float64).pin_memory()
+        ets = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A = A_h.to("cuda", non_blocking=True)
+            b = b_h.to("cuda", non_blocking=True)
+            x = torch.zeros(self.n, dtype=torch.float64, device="cuda")
+            F = kpp.Factors(A, self.P, self.lam, 0)
+            rep = kpp.kpp_solve(A, b, x, self.P, F, self.prm, allow_no_conv=self.noisy)
+            x_h.copy_(x)
+            ets.append(time.perf_counter() - t0)
+            del F, A
+        return {"value": rep.iters / ets[-1], "unit": self.unit,
+                "h2d_bytes_per_step": A_h.numel() * A_h.element_size() + b_h.numel() * 8,
+                "d2h_bytes_per_step": self.n * 8, "time_to_tol_ms": 1e3 * ets[-1],
+                "note": "pinned host buffers copied in and out around kpp_factor_blocks + kpp_solve"}
+
+    def cpu_baseline(self, budget_s):
+        """Oracle iterations on the first 16 blocks (8192 rows x 4096) of the stored matrix widened to
+        FP64: the same per-iteration work (s x n); factor phase excluded."""
+        rows = 16 * self.s
+        A = np.ascontiguousarray(self.A[:rows].double().cpu().numpy())
+        b = np.ascontiguousarray(self.b[:rows].cpu().numpy())
+        L = _factors_numpy_gram(A, self.s, self.lam)
+        v, it, dt = _oracle_iter_rate(A, b, L, self.s, False, self.lam, 0, budget_s, it0=16)
+        return {"value": v, "unit": self.unit, "cores": 1, "kind": "oracle",
+                "sample": f"{it} FP64 oracle block iterations (s={self.s}, n={self.n}) on the first {rows} rows of "
+                          f"the stored matrix widened to FP64, one host thread ({dt:.1f} s; factor phase excluded)"}
+
+
+class Batched(Workload):
+    """64 under-determined FP32 systems with 8-column panels: factors, then one autotuned plan per step,
+    captured into a CUDA graph and replayed."""
+
+    kernel = "stream_kernel"
+
+    def __init__(self, nsys=64, m=2048, n=65536, k=8, s=256):
+        self.nsys, self.m, self.n, self.k, self.s = nsys, m, n, k, s
+        self.tol = 1e-8
+        self.dtype = "f32"
+        self.desc = (f"{nsys} under-determined min-norm K++ systems, each {m}x{n} FP32 i.i.d. N(0,1) with 20 seeded "
+                     f"rows x100, {k} right-hand sides ~N(0,I) each, s={s}, lambda=1e-3 median |a_i|^2, FP32 "
+                     "iterations + FP64 refinement (inner tol 1e-3), tol 1e-8 per column; one plan (autotuned CTAs "
+                     "per system) captured in a CUDA graph and replayed")
+
+    def setup(self, kpp, torch, rank):
+        self.kpp, self.torch = kpp, torch
+        self.A, self.B = [], []
+        for i in range(self.nsys):
+            A, B, _ = W.torch_gaussian_rows(self.m, self.n, 20, 100.0, seed=3000 + 1000 * rank + i, k_rhs=self.k)
+            self.A.append(A)
+            self.B.append(B)
+        rn = (self.A[0].double() ** 2).sum(dim=1)
+        self.lam = 1e-3 * float(torch.median(rn).item())
+        self.X = [torch.zeros(self.n, self.k, dtype=torch.float64, device="cuda") for _ in range(self.nsys)]
+        self.P = kpp.Partition(self.m, self.s)
+        self.prm = kpp.params(lam=self.lam, tol=self.tol, refine=1, inner_tol=1e-3, seed=0, sys_id=rank * 4096,
+                              grid=kpp.GRID_TUNE)
+        self.cap_stream = torch.cuda.Stream()
+
+    def step(self):
+        kpp, torch = self.kpp, self.torch
+        cur = torch.cuda.current_stream()
+        F = [kpp.Factors(a, self.P, self.lam, 0) for a in self.A]
+        plan = kpp.Plan(self.A, self.B, self.X, self.P, F, self.prm, stream=cur)
+        n0 = kpp.launch_count()
+        g = torch.cuda.CUDAGraph()
+        self.cap_stream.wait_stream(cur)
+        with torch.cuda.graph(g, stream=self.cap_stream):
+            plan.launch(torch.cuda.current_stream())
+        graph_launches = kpp.launch_count() - n0
+        for x in self.X:
+            x.zero_()
+        g.replay()
+        reps = plan.report(stream=cur)
+        self.info = plan.info()
+        plan.close()
+        del g, F
+        it = [reps[i * self.k].iters for i in range(self.nsys)]
+        ok = all(r.status == kpp.OK and r.rel_res_true <= self.tol for r in reps)
+        return {"units": sum(it), "ok": ok, "iters": sum(it), "max_iters": max(it),
+                "outer": max(reps[i * self.k].outer for i in range(self.nsys)),
+                "graph_launches": graph_launches, "rel_res": max(r.rel_res_true for r in reps)}
+
+    def per_iter_bytes(self):
+        s, n, k = self.s, self.n, self.k
+        # A_S once (the second pass re-reads it from L2), X and M panels read + written, G_S^-1 (FP32)
+        return s * n * 4 + 4 * n * k * 4 + s * s * 4
+
+    def measure_kernel(self, peaks):
+        """The stream kernel's launch duration is not separable inside a replayed graph: time one more
+        launch of it (same systems, tuned grid, a fixed 64 steps) with events around the launch."""
+        kpp, torch = self.kpp, self.torch
+        F = [kpp.Factors(a, self.P, self.lam, 0) for a in self.A]
+        X = [torch.zeros_like(x) for x in self.X]
+        T = 64
+        prm = kpp.params(lam=self.lam, tol=0.0, refine=0, max_iters=T, seed=0, grid=self.info["grid"])
+        reps = kpp.kpp_solve_batched(self.A, self.B, X, self.P, F, prm, allow_no_conv=True)
+        kms = reps[0].kernel_ms
+        self._roof = _hbm_roof(self.kernel, self.per_iter_bytes() * self.nsys * T, kms, peaks,
+                               f"{self.kernel}/batched64", {"bytes": self.per_iter_bytes()},
+                               {"measured_on": f"one launch of {T} steps x {self.nsys} systems at the tuned grid "
+                                               f"({self.info['grid']} CTAs per system)"})
+        del F, X
+
+    def roofline(self, steps, peaks):
+        self.measure_kernel(peaks)
+        return self._roof
+
+    def extra(self, steps):
+        return {"plan": self.info, "max_system_iters": steps[-1]["max_iters"], "outer_steps": steps[-1]["outer"],
+                "worst_rel_res": steps[-1]["rel_res"],
+                "gpu_launches_note": "host-side launches plus the captured graph's kernels (one replay per step)"}
+
+    def e2e(self):
+        """Right-hand sides in from pinned host memory and solutions out, around factor + plan + replay
+        (the 32 GiB of A stay resident)."""
+        kpp, torch = self.kpp, self.torch
+        B_h = [b.cpu().pin_memory() for b in self.B]
+        X_h = [torch.zeros(self.n, self.k, dtype=torch.float64).pin_memory() for _ in range(self.nsys)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b, bh in zip(self.B, B_h):
+            b.copy_(bh, non_blocking=True)
+        st = self.step()
+        for x, xh in zip(self.X, X_h):
+            xh.copy_(x)
+        dt = time.perf_counter() - t0
+        assert st["ok"]
+        return {"value": st["units"] / dt, "unit": self.unit,
+                "h2d_bytes_per_step": sum(b.numel() * 8 for b in B_h),
+                "d2h_bytes_per_step": sum(x.numel() * 8 for x in X_h), "time_to_tol_ms": 1e3 * dt,
+                "note": "B in / X out through pinned host memory; A resident in HBM"}
+
+    def cpu_baseline(self, budget_s):
+        """Oracle iterations on system 0, right-hand side 0 (FP32 entries widened to FP64); factor phase
+        excluded."""
+        A = np.ascontiguousarray(self.A[0].double().cpu().numpy())
+        b = np.ascontiguousarray(self.B[0][:, 0].cpu().numpy())
+        L = _factors_numpy_gram(A, self.s, self.lam)
+        v, it, dt = _oracle_iter_rate(A, b, L, self.s, False, self.lam, 0, budget_s, it0=8)
+        return {"value": v, "unit": self.unit, "cores": 1, "kind": "oracle",
+                "sample": f"{it} FP64 oracle block iterations of system 0, one right-hand side, one host thread "
+                          f"({dt:.1f} s; factor phase excluded; the GPU counts one iteration per system for its "
+                          f"{self.k}-column panel)"}
+
+
+class Serving(Workload):
+    """Continuous-batching CD++ server fed by a Poisson request stream."""
+
+    unit = "solves/s"
+    metric = SERVING_METRIC
+    kernel = "cd3_kernel"
+
+    def __init__(self, n_req=1024, n_mats=32, budget=120 << 30, max_concurrent=16, grid_per_solve=0):
+        self.n_req, self.n_mats, self.budget = n_req, n_mats, budget
+        self.max_concurrent, self.grid = max_concurrent, grid_per_solve
+        self.dtype = "f32"
+        self.desc = (f"{n_req} CD++ requests, Poisson arrivals (mean gap 2 ms), catalog of {n_mats} dense SPD "
+                     "matrices built as the n=4096 workload (n log-uniform in [512,8192], even ids BF16, odd FP32), "
+                     "k ~ U{1..32} right-hand sides ~N(0,I), s=64, lambda=1e-4, FP32 iterations + FP64 "
+                     f"refinement, tol 1e-8, HBM budget {budget >> 30} GiB, up to {max_concurrent} concurrent solves "
+                     "(CTAs per solve chosen per request, admitted launches never exceed the SM count), factors "
+                     "memoised per matrix across requests")
+
+    def setup(self, kpp, torch, rank):
+        self.kpp, self.torch = kpp, torch
+        self.sizes = W.serving_catalog(self.n_mats)
+        self.mats = []
+        self.bf16_to_f32 = []
+        for i, n in enumerate(self.sizes):
+            dt = "bf16" if i % 2 == 0 else "f32"
+            A, _ = W.torch_spd(n, 50, 1e2, 1e4, 1.0, 10.0, seed=7000 + i, dtype=dt)
+            if dt == "bf16" and not W.stays_spd(A, 0.1):
+                # the BF16-rounded matrix is not SPD (min eigenvalue below 0.1): store this one FP32
+                dt = "f32"
+                A, _ = W.torch_spd(n, 50, 1e2, 1e4, 1.0, 10.0, seed=7000 + i, dtype=dt)
+                self.bf16_to_f32.append(i)
+            self.mats.append((n, dt, A))
+        self.reqs = W.serving_requests(self.n_req, self.n_mats, 2.0, 1, 32, seed=6000 + rank)
+        self.B = [np.random.default_rng(seed).standard_normal((self.sizes[mid], k))
+                  for (_, mid, k, seed) in self.reqs]
+        self.sv = kpp.Server(self.budget, max_concurrent=self.max_concurrent, grid_per_solve=self.grid)
+        self.ids = [self.sv.add_matrix(A, 64, 1e-4, 1) for (_, _, A) in self.mats]
+        _log(f"serving: catalog of {len(self.mats)} matrices and {len(self.reqs)} requests ready")
+
+    def step(self):
+        kpp = self.kpp
+        self.sv.reset_stats()
+        t0 = time.perf_counter()
+        rids = []
+        for (arr_ms, mid, k, seed), B in zip(self.reqs, self.B):
+            wait = t0 + arr_ms / 1e3 - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            prm = kpp.params(tol=1e-8, refine=1, inner_tol=1e-3, seed=seed, sys_id=seed)
+            rids.append(self.sv.submit(self.ids[mid], B, prm))
+        _log(f"serving: {len(rids)} requests submitted in {time.perf_counter() - t0:.2f} s")
+        self.sv.wait_all(1800.0)
+        st = self.sv.stats()
+        _log(f"serving: done in {time.perf_counter() - t0:.2f} s, p50 {st['p50_ms']:.1f} ms, p99 {st['p99_ms']:.1f} ms")
+        byts, iters, worst = 0, 0, 0.0
+        for rid, (_, mid, k, _) in zip(rids, self.reqs):
+            n = self.sizes[mid]
+            done, rc, _, reps = self.sv.poll(rid, n, k)
+            esz = 2 if self.mats[mid][1] == "bf16" else 4
+            it = reps[0].iters
+            iters += it
+            worst = max(worst, max(r.rel_res_true for r in reps))
+            byts += it * (64 * n * esz + 64 * 64 * 4 + 4 * n * k * 4)
+        return {"units": st["completed"], "ok": st["failed"] == 0 and st["completed"] == self.n_req,
+                "span_s": st["span_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                "solves_per_s": st["solves_per_s"], "peak_bytes": st["peak_bytes"], "alg_bytes": byts,
+                "iters": iters, "rel_res": worst}
+
+    def roofline(self, steps, peaks):
+        last = steps[-1]
+        ach = last["alg_bytes"] / last["span_s"] / 1e9
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        return {"kernel": "every solve kernel of the mix (device level)", "bound": "hbm", "achieved": ach,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "note": "algorithmic bytes of all requests' block iterations / serving span (arrivals included)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+
+    def extra(self, steps):
+        last = steps[-1]
+        return {"p50_ms": last["p50_ms"], "p99_ms": last["p99_ms"], "max_ms": last["max_ms"],
+                "server_solves_per_s": last["solves_per_s"], "peak_bytes": last["peak_bytes"],
+                "block_iters": last["iters"], "requests": self.n_req,
+                "bf16_not_spd_stored_f32": [(i, self.sizes[i]) for i in self.bf16_to_f32]}
+
+    def e2e(self):
+        # every request already enters as a host panel and leaves as one: the metric is end to end
+        return None
+
+    def cpu_baseline(self, budget_s):
+        """Oracle CD++ solves (FP64, one column, to 1e-8) of the first requests with n <= 2048, until about
+        budget_s of CPU time; reported per request of the stream's mean width k."""
+        import oracle
+        t_used, cols = 0.0, 0
+        for (_, mid, k, seed), B in zip(self.reqs, self.B):
+            n, dt, A = self.mats[mid]
+            if n > 2048:
+                continue
+            Ah = np.ascontiguousarray(A.double().cpu().numpy())
+            L = oracle.cdpp_factor(Ah, 64, 1e-4)
+            t0 = time.perf_counter()
+            r = oracle.run(Ah, np.ascontiguousarray(B[:, 0]), L, 64, cd=True, lam=1e-4, tol=1e-8,
+                           max_iters=2000000, seed=seed, sys=seed)
+            t_used += time.perf_counter() - t0
+            cols += 1
+            assert r.rel_res_true <= 1e-8
+            if t_used > budget_s:
+                break
+        mean_k = statistics.mean(k for (_, _, k, _) in self.reqs)
+        v = cols / t_used / mean_k
+        return {"value": v, "unit": self.unit, "cores": 1, "kind": "oracle",
+                "sample": f"{cols} single-column FP64 oracle CD++ solves to 1e-8 of the first requests with "
+                          f"n <= 2048 ({t_used:.1f} s, one host thread); value = columns/s / mean k ({mean_k:.1f})"}
+
+
+def make_workload(args):
+    if args.workload in ("cdpp4096", "kpp2000"):
+        return SingleFP64(args.workload)
+    if args.workload == "mixed262144":
+        return MixedLS(args.storage, args.noisy)
+    if args.workload == "batched64":
+        return Batched()
+    if args.workload == "serving":
+        return Serving(n_req=args.requests)
+    if args.workload in ("cdpp4096-f32", "cdpp4096-bf16"):
+        return MixedSPD(args.workload.split("-")[1])
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+# ---------------------------------------------------------------------------------------------
+# Arms
+# ---------------------------------------------------------------------------------------------
+
 def run_reference(args, rank: int):
     """The FP64 CPU oracle on the host cores, each step a bounded sample of the same workload."""
     if rank != 0:
         return
     import oracle
-    sy, cd, desc = workload(args.workload)
-    n = sy.A.shape[1]
-    L = oracle.cdpp_factor(sy.A, sy.s, sy.lam) if cd else oracle.kpp_factor(sy.A, sy.s, sy.lam)
+    wl = make_workload(args)
+    if type(wl) is not SingleFP64:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the FP64 workloads "
+                          "(cdpp4096, kpp2000); the other workloads report it as cpu_baseline"}), flush=True)
+        return
+    sy, cd = wl.sy, wl.cd
+    L = _oracle_factors(sy.A, sy.s, sy.lam, cd)
     sample_iters = args.ref_iters
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = oracle.run(sy.A, sy.b, L, sy.s, cd=cd, lam=sy.lam, tol=0.0, max_iters=sample_iters, seed=1 if cd else 0)
+        r = oracle.run(sy.A, sy.b, L, sy.s, cd=cd, lam=sy.lam, tol=0.0, max_iters=sample_iters, seed=wl.seed)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -147,26 +703,10 @@ def run_reference(args, rank: int):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "block-iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc},
+            "config": {"workload": wl.desc},
             "cpu_baseline": {"value": v, "unit": "block-iters/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "block-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def cpu_baseline(sy, cd: bool, budget_s: float):
-    """The oracle as it stands, single-threaded, on a bounded sample (iterations, not the whole solve)."""
-    import oracle
-    L = oracle.cdpp_factor(sy.A, sy.s, sy.lam) if cd else oracle.kpp_factor(sy.A, sy.s, sy.lam)
-    it = 256
-    while True:
-        t0 = time.perf_counter()
-        oracle.run(sy.A, sy.b, L, sy.s, cd=cd, lam=sy.lam, tol=0.0, max_iters=it, seed=1 if cd else 0)
-        dt = time.perf_counter() - t0
-        if dt > budget_s / 4 or it >= (1 << 22):
-            break
-        it *= 4
-    return {"value": it / dt, "unit": "block-iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{it} block iterations of the same workload, FP64 C oracle, one host thread ({dt:.1f} s)"}
 
 
 def main():
@@ -175,7 +715,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cdpp4096", choices=["cdpp4096", "kpp2000"])
+    ap.add_argument("--workload", default="cdpp4096",
+                    choices=["cdpp4096", "kpp2000", "mixed262144", "batched64", "serving", "cdpp4096-f32",
+                             "cdpp4096-bf16"])
+    ap.add_argument("--storage", default="bf16", choices=["bf16", "f32"], help="mixed262144 storage type")
+    ap.add_argument("--noisy", action="store_true", help="mixed262144: b = A x* + 1e-6 N(0,I)")
+    ap.add_argument("--requests", type=int, default=1024, help="serving: requests per step")
+    ap.add_argument("--host-qr", action="store_true",
+                    help="Haar factors by a host QR (ncu cannot load torch's device linear algebra)")
     ap.add_argument("--ref-iters", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -204,101 +751,74 @@ def main():
         dist.barrier()
     kpp.load()
 
-    sy, cd, desc = workload(args.workload)
-    m, n = sy.A.shape
+    W.HOST_QR = args.host_qr
+    wl = make_workload(args)
+    wl.setup(kpp, torch, rank)
     stream = torch.cuda.current_stream()
-    Ad = torch.as_tensor(sy.A, device="cuda")
-    bd = torch.as_tensor(sy.b, device="cuda")
-    x = torch.zeros(n, dtype=torch.float64, device="cuda")
-    P = kpp.Partition(m, sy.s)
-    prm = kpp.params(lam=sy.lam, tol=sy.tol, seed=1 if cd else 0, sys_id=rank)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    solve = kpp.cdpp_solve if cd else kpp.kpp_solve
 
-    def step():
-        x.zero_()
-        F = kpp.Factors(Ad, P, sy.lam, 1 if cd else 0)
-        rep = solve(Ad, bd, x, P, F, prm)
-        del F
-        return rep
-
+    _log(f"{args.workload}: set up")
     for _ in range(args.warmup):
-        step()
+        wl.step()
     torch.cuda.synchronize()
-    step_ms, kern_ms, iters, reps = [], [], [], []
+    _log(f"{args.workload}: {args.warmup} warm-up steps done")
+    step_ms, steps = [], []
     with ClockSampler(local) as clk:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        n0 = kpp.launch_count()
         for _ in range(args.steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            rep = step()
+            st = wl.step()
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-            kern_ms.append(rep.device_ms)
-            iters.append(rep.iters)
-            reps.append(rep)
+            steps.append(st)
         torch.cuda.synchronize()
+        launches = kpp.launch_count() - n0
         if dist:
             dist.barrier()
+    assert all(st["ok"] for st in steps), steps
     total_ms = sum(step_ms)
-    total_iters = sum(iters)
+    total_units = sum(st["units"] for st in steps)
     if dist:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-        it = torch.tensor([total_iters], device="cuda", dtype=torch.float64)
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        total_iters = int(it.item())
-    value = total_iters / (total_ms / 1e3)
-    assert all(r.status == kpp.OK and r.rel_res_true <= sy.tol for r in reps), [r.as_dict() for r in reps]
-
-    flops, byts = per_iter_cost(sy, cd)
+        u = torch.tensor([total_units], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_units = int(u.item())
+    value = total_units / (total_ms / 1e3)
     peaks = _peaks()
-    mean_iters = statistics.mean(iters)
-    kms = statistics.mean(kern_ms)
-    fp64_peak = 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9  # GFLOP/s: 2 FP64 FMA/clk/SM
-    ach_flops = mean_iters * flops / (kms / 1e3) / 1e9
-    ach_bytes = mean_iters * byts / (kms / 1e3) / 1e9
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    roof = {"kernel": "cd3_kernel" if cd else "solve2_kernel", "bound": "alu", "achieved": ach_flops, "peak": fp64_peak, "unit": "GFLOP/s",
-            "frac": ach_flops / fp64_peak, "traffic": None,
-            "per_iter": {"flops": flops, "bytes": byts},
-            "hbm_view": {"achieved": ach_bytes, "peak": hbm, "unit": "GB/s", "frac": ach_bytes / hbm,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
-            "peak_source": "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x sm_max_mhz (derived)"}
 
-    line = {"metric": METRIC, "value": value, "unit": "block-iters/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": wl.metric, "value": value, "unit": wl.unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "parallelism": f"replicas x{world}",
+            "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
+            "config": {"workload": wl.desc, "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (512 MiB write, outside the step events)",
-                       "step": "factor phase + solve to 1e-8 + FP64 residual confirmation"},
-            "time_to_tol_ms": statistics.mean(step_ms), "iters_to_tol": mean_iters,
-            "solve_kernel_ms": kms, "rel_res_true": reps[-1].rel_res_true,
-            "gpu_launches": 5 * args.steps, "roofline": roof, "clocks": clk.summary()}
-
+                       "step": "the whole request stream through the server" if isinstance(wl, Serving)
+                       else "factor phase + solve to 1e-8 + FP64 residual confirmation"},
+            "time_to_tol_ms": statistics.mean(step_ms), "gpu_launches": launches,
+            "roofline": wl.roofline(steps, peaks), "clocks": clk.summary()}
+    if "iters" in steps[-1]:
+        line["iters_to_tol"] = statistics.mean(st["iters"] for st in steps)
+    if "kernel_ms" in steps[-1]:
+        line["solve_kernel_ms"] = statistics.mean(st["kernel_ms"] for st in steps)
+    if "rel_res" in steps[-1]:
+        line["rel_res_true"] = steps[-1]["rel_res"]
+    line.update(wl.extra(steps))
     if rank == 0 and not args.no_e2e:
-        # end to end through the host-buffer entry point: copies in, factor, solve, copy back
-        A_h = np.ascontiguousarray(sy.A)
-        b_h = sy.b.copy()
-        ets = []
-        for i in range(2):
-            x_h = np.zeros(n)
-            t0 = time.perf_counter()
-            rep = kpp.solve_host(A_h, b_h, x_h, sy.s, 1 if cd else 0, prm)
-            ets.append(time.perf_counter() - t0)
-            assert rep.status == kpp.OK
-        line["e2e"] = {"value": rep.iters / ets[-1], "unit": "block-iters/s",
-                       "h2d_bytes_per_step": A_h.nbytes + b_h.nbytes + x_h.nbytes,
-                       "d2h_bytes_per_step": x_h.nbytes, "time_to_tol_ms": 1e3 * ets[-1],
-                       "note": "host (pageable) buffers through kpp_solve_host"}
+        e = wl.e2e()
+        if e:
+            line["e2e"] = e
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sy, cd, args.cpu_budget)
+        cb = wl.cpu_baseline(args.cpu_budget)
+        if cb:
+            line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -93,7 +93,9 @@ typedef struct {
     int32_t status;        /* kpp_status of the solve */
     int32_t bad_block;     /* first block whose factorisation failed, else -1 */
     double device_ms;      /* device time of the solve (CUDA events on `stream`) */
-    int64_t reserved[4];
+    double kernel_ms;      /* of which inside the persistent iteration kernel's launches */
+    int64_t launches;      /* launches of the persistent iteration kernel */
+    int64_t reserved[2];
 } kpp_report;
 
 /* Defaults: lambda 0, tol 1e-8, max_iters 10^6, seed 0, adaptive rho from 0, eta NaN (s/(2 min)),
@@ -277,6 +279,9 @@ kpp_status kpp_server_poll(kpp_server_t sv, int64_t request_id, double *X_host, 
 /* Block until no request is queued or running, at most timeout_s seconds (KPP_ERR_TIMEOUT). */
 kpp_status kpp_server_wait_all(kpp_server_t sv, double timeout_s);
 kpp_status kpp_server_stats(kpp_server_t sv, kpp_serving_stats *out);
+/* Start a new statistics window: latencies, completed / failed counts, the first-submission time and
+ * the peak are reset (requests already submitted stay pollable).  Errors: KPP_ERR_ARG (null server). */
+kpp_status kpp_server_reset_stats(kpp_server_t sv);
 /* Stop the workers (after the running requests finish) and free the factors. */
 void kpp_server_destroy(kpp_server_t sv);
 
@@ -345,6 +350,10 @@ int64_t kpp_tune_cache_size(void);
 void kpp_tune_cache_clear(void);
 kpp_status kpp_tune_cache_save(const char *path);
 kpp_status kpp_tune_cache_load(const char *path);
+
+/* Number of kernel launches this library has issued in the process so far (every launch site counts
+ * once; a captured graph's replays are not counted).  Host only, never fails. */
+uint64_t kpp_launch_count(void);
 
 /* Library build information: "sm_103a; <compiler>; <date>". */
 const char *kpp_build_info(void);

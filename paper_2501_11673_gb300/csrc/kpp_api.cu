@@ -4,6 +4,7 @@
 // persistent solve kernel, the FP64 iterative-refinement loop of the mixed-precision form, and the
 // report.  Every arithmetic step of the method runs in the kernels of kpp_solve.cu / kpp_factor.cu /
 // kpp_gram_tc.cu.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -29,6 +30,9 @@ void set_error(const char *fmt, ...) {
     g_last_error = buf;
 }
 void clear_error() { g_last_error.clear(); }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int sm_count() {
     static int cached[64] = {0};
@@ -276,7 +280,7 @@ cleanup:
 }
 
 // Reset the per-launch state and launch the kernel (graph-capturable).
-kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st) {
+kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
     kpp_status rc = KPP_OK;
     CUDA_OR(cudaMemsetAsync(L.bars, 0, L.nsys * sizeof(unsigned), st), KPP_ERR_CUDA);
     CUDA_OR(cudaMemsetAsync(L.errs, 0, L.nsys * sizeof(int), st), KPP_ERR_CUDA);
@@ -298,6 +302,7 @@ kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st) {
         }
         if (L.kind == 3) CUDA_OR(cudaMemsetAsync(L.mails[i], 0, L.mail_bytes, st), KPP_ERR_CUDA);
     }
+    if (ev0) CUDA_OR(cudaEventRecord(ev0, st), KPP_ERR_CUDA);
     {
         cudaError_t le = L.kind == 4   ? launch_stream(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
                          : L.kind == 3 ? launch_cd3(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
@@ -309,6 +314,7 @@ kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st) {
         }
         CUDA_OR(le, KPP_ERR_CUDA);
     }
+    if (ev1) CUDA_OR(cudaEventRecord(ev1, st), KPP_ERR_CUDA);
 cleanup:
     return rc;
 }
@@ -331,10 +337,8 @@ kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd, int k,
     if (G_out) *G_out = L.cm.G;
     CUDA_OR(cudaEventCreate(&e0), KPP_ERR_CUDA);
     CUDA_OR(cudaEventCreate(&e1), KPP_ERR_CUDA);
-    CUDA_OR(cudaEventRecord(e0, st), KPP_ERR_CUDA);
-    rc = enqueue_persistent(L, st);
+    rc = enqueue_persistent(L, st, e0, e1);  // events around the kernel launch itself
     if (rc != KPP_OK) goto cleanup;
-    CUDA_OR(cudaEventRecord(e1, st), KPP_ERR_CUDA);
     for (int i = 0; i < nsys; ++i)
         CUDA_OR(cudaMemcpyAsync(sys[i].sc_host, L.args[i].sc, (size_t)k * sizeof(SolveScalars), cudaMemcpyDeviceToHost, st),
                 KPP_ERR_CUDA);
@@ -428,7 +432,8 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
     std::vector<int> errs(nsys, 0);
     std::vector<SysInput> in(nsys);
     std::vector<double> dev_ms(nsys, 0.0);
-    std::vector<int64_t> iters(nsys, 0), outer(nsys, 0);
+    std::vector<int64_t> iters(nsys, 0), outer(nsys, 0), nlaunch(nsys, 0);
+    std::vector<double> kern_ms(nsys, 0.0);
     for (int i = 0; i < nsys; ++i) init_scalars(sc[i], k, p.rho0);
     float ms = 0.f;
     // refinement: the last outer check already holds |r|^2 and |b|^2 of the returned x
@@ -442,6 +447,8 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
                             /*init_residual=*/true, 0, st, &ms, errs.data(), tune.variant);
         for (int i = 0; i < nsys; ++i) {
             dev_ms[i] = ms;
+            kern_ms[i] = ms;
+            nlaunch[i] = 1;
             iters[i] = sc[i][0].t;
         }
     } else {
@@ -465,9 +472,12 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
                 CUDA_OR(launch_f64_to_f32(nc, X[i], d32[i], st), KPP_ERR_CUDA);
                 in[i] = SysInput{&A[i], b32[i], d32[i], &F[i]->f, p.sys_id + (uint32_t)i, sc[i].data()};
             }
+            float kms = 0.f;
             rc = run_persistent(in, dtype, cd, k, s, eta, p.tol, p.adaptive_rho, 0, p.max_iters, p.seed, tune.grid,
-                                true, 0, st, &ms, errs.data(), tune.variant);
+                                true, 0, st, &kms, errs.data(), tune.variant);
             for (int i = 0; i < nsys; ++i) {
+                kern_ms[i] = kms;
+                nlaunch[i] = 1;
                 // x = double(x32): overwrite through the axpy of (x32 - x) is not exact; copy via zero + axpy
                 CUDA_OR(cudaMemsetAsync(X[i], 0, nc * sizeof(double), st), KPP_ERR_CUDA);
                 CUDA_OR(launch_axpy(nc, d32[i], X[i], st), KPP_ERR_CUDA);
@@ -511,13 +521,16 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
                     outer[i] += 1;
                 }
                 std::vector<int> e2(act.size(), 0);
+                float kms = 0.f;
                 kpp_status ri = run_persistent(act, dtype, cd, k, s, eta, p.inner_tol, p.adaptive_rho, 0,
-                                               t_global + p.max_iters, p.seed, tune.grid, false, t_global, st, nullptr,
+                                               t_global + p.max_iters, p.seed, tune.grid, false, t_global, st, &kms,
                                                e2.data(), tune.variant);
                 int64_t tmax = t_global;
                 for (size_t q = 0; q < act.size(); ++q) {
                     const int i = idx[q];
                     errs[i] = e2[q];
+                    kern_ms[i] += kms;
+                    nlaunch[i] += 1;
                     iters[i] += sc[i][0].t - t_global;
                     tmax = std::max<int64_t>(tmax, sc[i][0].t);
                     CUDA_OR(launch_axpy(nc, d32[i], X[i], st), KPP_ERR_CUDA);
@@ -570,6 +583,8 @@ kpp_status solve_systems(int nsys, const kpp_matrix *A, const double *const *B, 
                 r.status = cs;
                 r.bad_block = -1;
                 r.device_ms = dev_ms[i];
+                r.kernel_ms = kern_ms[i];
+                r.launches = nlaunch[i];
             }
         }
     }
@@ -627,6 +642,8 @@ const char *kpp_last_error(void) { return g_last_error.c_str(); }
 
 #define KPP_STR2(x) #x
 #define KPP_STR(x) KPP_STR2(x)
+uint64_t kpp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 const char *kpp_build_info(void) {
     return "sm_103a; nvcc " KPP_STR(__CUDACC_VER_MAJOR__) "." KPP_STR(__CUDACC_VER_MINOR__) "; " __DATE__;
 }

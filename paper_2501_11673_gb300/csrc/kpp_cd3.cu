@@ -532,6 +532,7 @@ static cudaError_t launch3_t(const void *d_sys, int nsys, const Common &cm, cuda
     Common c = cm;
     const Sys3 *p = (const Sys3 *)d_sys;
     void *args[] = {(void *)&p, (void *)&c};
+    note_launch();
     return cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)(nsys * cm.G)), dim3(NT), args, smem, st);
 }
 

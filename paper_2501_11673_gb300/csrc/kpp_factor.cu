@@ -368,12 +368,14 @@ static void launch_gram(const void *A, int64_t lda, int64_t rows, int64_t cols, 
     const int64_t nb = (rows + s - 1) / s;
     const int tiles = (s + 31) / 32;
     dim3 grid((unsigned)nb, tiles, tiles);
+    note_launch();
     gram_f64_kernel<TA><<<grid, 256, 0, st>>>((const TA *)A, lda, rows, cols, s, lam, G);
 }
 
 template <typename TA>
 static void launch_principal(const void *A, int64_t lda, int64_t n, int s, double lam, double *G, cudaStream_t st) {
     const int64_t nb = (n + s - 1) / s;
+    note_launch();
     principal_block_kernel<TA><<<(unsigned)nb, 256, 0, st>>>((const TA *)A, lda, n, s, lam, G);
 }
 
@@ -435,15 +437,18 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     KPP_TRY(cudaGetLastError());
     KPP_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(CHOL_PB * s * sizeof(double))));
+    note_launch();
     cholesky_kernel<<<(unsigned)nb, CHOL_NT, CHOL_PB * s * sizeof(double), st>>>(rows, s, G, F.L, bad);
     KPP_TRY(cudaGetLastError());
     if (A.dtype == KPP_F64) {
         const int sm64 = 4 * IT * ITP * (int)sizeof(double);
         KPP_TRY(cudaFuncSetAttribute(inverse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
+        note_launch();
         inverse_kernel<double><<<(unsigned)nb, INV_NT, sm64, st>>>(rows, s, F.L, Linv, F.Ginv);
     } else {
         const int sm32 = 4 * IT * ITP * (int)sizeof(float);
         KPP_TRY(cudaFuncSetAttribute(inverse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32));
+        note_launch();
         inverse_kernel<float><<<(unsigned)nb, INV_NT, sm32, st>>>(rows, s, F.L, (float *)Linv, F.Ginv32);
     }
     KPP_TRY(cudaGetLastError());
@@ -460,6 +465,7 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     if (rc == KPP_OK && mode == 1 && A.dtype == KPP_F64) {
         KPP_TRY(cudaMalloc(&F.W, (size_t)rows * rows * sizeof(double)));
         dim3 grid((unsigned)nb, (unsigned)((rows + 63) / 64));
+        note_launch();
         cd_w_kernel<<<grid, 256, 0, st>>>((const double *)A.data, A.ld, rows, s, F.Ginv, F.W);
         KPP_TRY(cudaGetLastError());
     }

@@ -317,6 +317,7 @@ bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st,
         const int smem = mode == 2 ? 2 * 2 * TC_STAGE_BYTES + 1024 : TC_SMEM;
         ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
         if (ok) {
+            note_launch();
             kern<<<(unsigned)tl.size(), 128, smem, st>>>(tm, A.rows, A.cols, s, lam, d_tiles, G, d_err);
             ok = cudaGetLastError() == cudaSuccess;
         }

@@ -114,7 +114,9 @@ kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, i
                               double eta, double tol, int adaptive, int confirm, int64_t max_iters, uint64_t seed,
                               int grid, bool init_residual, int64_t t0, bool t0_state, int variant, Scratch &scr,
                               cudaStream_t st);
-kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st);
+// ev0 / ev1 (optional): recorded on `st` right before and after the kernel launch.
+kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                              cudaEvent_t ev1 = nullptr);
 
 // prepare + enqueue + copy the scalars back (synchronises).  variant < 0: the global limit.
 kpp_status run_persistent(std::vector<SysInput> &sys, int dtype, bool cd, int k, int s, double eta, double tol,

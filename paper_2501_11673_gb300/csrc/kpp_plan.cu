@@ -408,6 +408,7 @@ kpp_status kpp_plan_launch(kpp_plan_t pl, void *stream) {
     kpp_status rc = KPP_OK;
     const int nsys = pl->nsys, k = pl->k;
     const size_t nr = (size_t)pl->A[0].rows * k, nc = (size_t)pl->A[0].cols * k;
+    note_launch();
     plan_reset_kernel<<<1, 256, 0, st>>>(nsys, k, pl->sc, pl->sc0, pl->ps, pl->t_global);
     CUDA_OR(cudaGetLastError(), KPP_ERR_CUDA);
     if (pl->form == 0) {
@@ -437,6 +438,7 @@ kpp_status kpp_plan_launch(kpp_plan_t pl, void *stream) {
                                                  pl->bn2_part + (size_t)i * pl->RG * k, pl->RG, st),
                             KPP_ERR_CUDA);
             }
+            note_launch();
             plan_check_kernel<<<1, 128, 0, st>>>(nsys, k, pl->RG, pl->res_part, pl->bn2_part, pl->res2, pl->bn2,
                                                  o == 0, o == max_outer, pl->p.tol, pl->ps, pl->sc, pl->t_global);
             CUDA_OR(cudaGetLastError(), KPP_ERR_CUDA);
@@ -444,11 +446,13 @@ kpp_status kpp_plan_launch(kpp_plan_t pl, void *stream) {
             for (int i = 0; i < nsys; ++i) CUDA_OR(cudaMemsetAsync(pl->d32[i], 0, nc * sizeof(float), st), KPP_ERR_CUDA);
             rc = enqueue_persistent(pl->L, st);
             if (rc != KPP_OK) goto cleanup;
+            note_launch();
             plan_post_kernel<<<1, 32, 0, st>>>(nsys, k, pl->ps, pl->sc, pl->L.errs, pl->t_global);
             CUDA_OR(cudaGetLastError(), KPP_ERR_CUDA);
             {
                 const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(nc + 255) / 256,
                                                                            std::max(1, 2 * sm_count() / nsys)));
+                note_launch();
                 plan_axpy_kernel<<<dim3(gx, nsys), 256, 0, st>>>(nsys, (int64_t)nc, pl->d_d32, pl->d_X, pl->ps);
                 CUDA_OR(cudaGetLastError(), KPP_ERR_CUDA);
             }

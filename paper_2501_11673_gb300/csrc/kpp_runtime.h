@@ -48,4 +48,7 @@ kpp_status solve_systems_internal(int nsys, const kpp_matrix *A, const double *c
 // Number of SMs of the current device (cached).
 int sm_count();
 
+// Kernel launches issued by the library (every launch site calls note_launch; kpp_launch_count).
+void note_launch();
+
 }  // namespace kpp

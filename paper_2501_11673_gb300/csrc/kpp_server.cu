@@ -23,6 +23,7 @@
 
 #include "kpp_internal.cuh"
 #include "kpp_runtime.h"
+#include "kpp_solve.h"
 
 struct kpp_partition_s {
     int64_t rows;
@@ -58,6 +59,7 @@ struct Request {
     std::vector<double> X;  // cols x k (result)
     std::vector<kpp_report> reps;
     size_t bytes = 0;       // device bytes charged while admitted
+    int grid = 0;           // CTAs of its persistent launch (charged against the SM count)
     clk::time_point t_submit, t_done;
     int32_t state = 0;      // 0 queued, 1 running, 2 done
     kpp_status status = KPP_OK;
@@ -79,12 +81,14 @@ struct kpp_server_s {
     std::deque<std::shared_ptr<Request>> queue;     // waiting for admission
     std::deque<std::shared_ptr<Request>> ready;     // admitted, waiting for a worker
     size_t used = 0, peak = 0;
+    int ctas_used = 0;      // CTAs of the admitted requests' launches (at most the SM count)
     int64_t next_id = 0;
     int64_t n_done = 0;
     bool stop = false;
     std::vector<std::thread> workers;
     int64_t running = 0;  // admitted and not yet finished
     clk::time_point t_first{}, t_last{};
+    clk::time_point t_reset{};  // statistics cover requests finished after this point
     bool have_first = false;
     std::vector<double> latencies_ms;
 };
@@ -97,6 +101,26 @@ size_t request_bytes(const Matrix &m, int k) {
     const size_t rows = (size_t)m.A.rows, cols = (size_t)m.A.cols;
     const size_t vec = (rows + cols) * (size_t)k;
     return vec * 8 * 2 + vec * 4 * 6 + (size_t)m.s * 256 * 32 * 8 + (1u << 20);
+}
+
+// CTAs for one request's persistent launch: the fewest whose column chunk still fits the dataflow
+// (CD++) or small-block (K++) kernel, so that requests stay narrow and many run side by side.  Falls
+// back to the SM count (the general kernel then takes any chunk).
+int serve_grid(const Matrix &m, int k) {
+    const int sms = kpp::sm_count();
+    const int KP = k <= 1 ? 1 : (k <= 8 ? 8 : 32);
+    const bool f64 = m.A.dtype == KPP_F64;
+    const int tas = (int)dsize(m.A.dtype), tcs = f64 ? 8 : 4;
+    const int64_t sector = 32 / tas, cols = m.A.cols;
+    for (int G = std::max<int64_t>(1, (cols + 255) / 256); G <= sms; ++G) {
+        int64_t CW = (cols + G - 1) / G;
+        CW = (CW + sector - 1) / sector * sector;
+        const int Gu = (int)((cols + CW - 1) / CW);
+        if (!kpp::solve2_eligible(m.A, m.s, CW, KP, f64, m.mode == 1, Gu)) continue;
+        if (m.mode == 1 && kpp::cd3_smem_bytes(m.s, CW, KP, f64 ? 8 : tas, tcs, f64) > 200 * 1024) continue;
+        return Gu;
+    }
+    return sms;
 }
 
 size_t factor_bytes(const Matrix &m) {
@@ -129,7 +153,7 @@ void run_request(kpp_server_s *sv, const std::shared_ptr<Request> &r) {
         cudaMemsetAsync(dX, 0, cols * k * 8, st);
         kpp_params p = r->p;
         p.lambda = m.lambda;
-        if (sv->grid > 0 && p.grid == 0) p.grid = sv->grid;
+        if (p.grid == 0) p.grid = r->grid;
         const double *Bp[1] = {dB};
         double *Xp[1] = {dX};
         r->reps.assign(k, kpp_report{});
@@ -150,6 +174,7 @@ void run_request(kpp_server_s *sv, const std::shared_ptr<Request> &r) {
     r->t_done = clk::now();
     r->state = 2;
     sv->used -= r->bytes;
+    sv->ctas_used -= r->grid;
     m.users -= 1;
     sv->running -= 1;
     sv->n_done += 1;
@@ -165,6 +190,8 @@ void admit_locked(kpp_server_s *sv) {
         Matrix &m = *sv->mats[r->mat];
         size_t need = r->bytes;
         if (!m.F && m.factor_bytes == 0) need += factor_bytes(m);
+        // co-residency: the admitted launches together never ask for more CTAs than there are SMs
+        if (sv->ctas_used > 0 && sv->ctas_used + r->grid > kpp::sm_count()) return;
         if (sv->used + need > sv->budget) {
             // evict idle factors (least recently registered first) to make room
             for (auto &mp : sv->mats) {
@@ -184,6 +211,7 @@ void admit_locked(kpp_server_s *sv) {
             sv->used += m.factor_bytes;
         }
         sv->used += r->bytes;
+        sv->ctas_used += r->grid;
         sv->peak = std::max(sv->peak, sv->used);
         m.users += 1;
         sv->running += 1;
@@ -277,6 +305,7 @@ kpp_status kpp_server_submit(kpp_server_t sv, int32_t matrix_id, const double *B
     r->p = *p;
     r->B.assign(B_host, B_host + (size_t)m.A.rows * k);
     r->bytes = request_bytes(m, k);
+    r->grid = sv->grid > 0 ? sv->grid : serve_grid(m, k);
     r->t_submit = clk::now();
     if (!sv->have_first) {
         sv->t_first = r->t_submit;
@@ -357,8 +386,20 @@ kpp_status kpp_server_stats(kpp_server_t sv, kpp_serving_stats *out) {
     }
     int64_t failed = 0;
     for (auto &kv : sv->reqs)
-        if (kv.second->state == 2 && kv.second->status != KPP_OK) ++failed;
+        if (kv.second->state == 2 && kv.second->status != KPP_OK && kv.second->t_done >= sv->t_reset) ++failed;
     out->failed = failed;
+    return KPP_OK;
+}
+
+kpp_status kpp_server_reset_stats(kpp_server_t sv) {
+    clear_error();
+    if (!sv) return KPP_ERR_ARG;
+    std::lock_guard<std::mutex> g(sv->mu);
+    sv->latencies_ms.clear();
+    sv->n_done = 0;
+    sv->have_first = false;
+    sv->peak = sv->used;
+    sv->t_reset = clk::now();
     return KPP_OK;
 }
 

@@ -467,6 +467,7 @@ static void launch_res_t(const kpp_matrix &A, int k, const double *b, const doub
     const size_t smem = sm ? (size_t)A.cols * sizeof(double) : 0;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(residual_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
     residual_kernel<TA><<<grid, 256, smem, st>>>((const TA *)A.data, A.ld, A.rows, A.cols, k, b, x, r32, part, skip);
 }
 
@@ -499,6 +500,7 @@ static cudaError_t launch_solve_t(const SysArgs *d_sys, int nsys, const Common &
     if ((int64_t)per_sm * sm_count() < (int64_t)nsys * cm.G) return cudaErrorCooperativeLaunchTooLarge;
     Common c = cm;
     void *args[] = {(void *)&d_sys, (void *)&c};
+    note_launch();
     return cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)(nsys * cm.G)), dim3(NT), args, smem, st);
 }
 
@@ -537,7 +539,10 @@ __global__ void sample_blocks_kernel(uint64_t seed, uint32_t sys, int64_t t0, in
 
 cudaError_t launch_sample_blocks(uint64_t seed, uint32_t sys, int64_t t0, int64_t count, int32_t nb, int32_t *out,
                                  cudaStream_t st) {
-    if (count > 0) sample_blocks_kernel<<<2 * sm_count(), 256, 0, st>>>(seed, sys, t0, count, nb, out);
+    if (count > 0) {
+        note_launch();
+        sample_blocks_kernel<<<2 * sm_count(), 256, 0, st>>>(seed, sys, t0, count, nb, out);
+    }
     return cudaGetLastError();
 }
 
@@ -559,6 +564,7 @@ cudaError_t launch_residual_grid(const kpp_matrix &A, int k, const double *b, co
 }
 
 cudaError_t launch_axpy(int64_t n, const float *d, double *x, cudaStream_t st) {
+    note_launch();
     axpy_f32_to_f64_kernel<<<2 * sm_count(), 256, 0, st>>>(n, d, x);
     return cudaGetLastError();
 }
@@ -570,12 +576,14 @@ __global__ void negate_copy_kernel(int64_t n, const T *__restrict__ a, T *__rest
 }
 
 cudaError_t launch_negate_copy(size_t n, const void *src, void *dst, bool f64, cudaStream_t st) {
+    note_launch();
     if (f64) negate_copy_kernel<double><<<2 * sm_count(), 256, 0, st>>>((int64_t)n, (const double *)src, (double *)dst);
     else negate_copy_kernel<float><<<2 * sm_count(), 256, 0, st>>>((int64_t)n, (const float *)src, (float *)dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_f64_to_f32(int64_t n, const double *a, float *o, cudaStream_t st) {
+    note_launch();
     f64_to_f32_kernel<<<2 * sm_count(), 256, 0, st>>>(n, a, o);
     return cudaGetLastError();
 }

@@ -623,6 +623,7 @@ static cudaError_t launch2_t(const void *d_sys, int nsys, const Common &cm, cuda
     Common c = cm;
     const Sys2 *p = (const Sys2 *)d_sys;
     void *args[] = {(void *)&p, (void *)&c};
+    note_launch();
     return cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)(nsys * cm.G)), dim3(NT), args, smem, st);
 }
 

@@ -493,6 +493,7 @@ static cudaError_t launch_st(const void *d_sys, int nsys, const Common &cm, cuda
     Common c = cm;
     const Sys4 *p = (const Sys4 *)d_sys;
     void *args[] = {(void *)&p, (void *)&c};
+    note_launch();
     return cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)(nsys * cm.G)), dim3(256), args, smem, st);
 }
 

@@ -32,10 +32,10 @@ EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_par
            "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block",
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
            "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_block_gram", "kpp_server_create", "kpp_server_add_matrix",
-           "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_destroy",
+           "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_reset_stats", "kpp_server_destroy",
            "cdpp_solve_batched", "kpp_plan_create", "kpp_plan_launch", "kpp_plan_report", "kpp_plan_info",
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
-           "kpp_tune_cache_load", "kpp_build_info"]
+           "kpp_tune_cache_load", "kpp_launch_count", "kpp_build_info"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
 
@@ -71,7 +71,8 @@ class ServingStats(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("outer", ctypes.c_int64), ("rel_res_true", ctypes.c_double),
                 ("rel_res_est", ctypes.c_double), ("rho_final", ctypes.c_double), ("status", ctypes.c_int32),
-                ("bad_block", ctypes.c_int32), ("device_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
+                ("bad_block", ctypes.c_int32), ("device_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -125,6 +126,8 @@ def load(path: str | None = None):
         lib.kpp_server_wait_all.argtypes = [vp, dbl]
         lib.kpp_server_stats.argtypes = [vp, ctypes.POINTER(ServingStats)]
         lib.kpp_server_destroy.argtypes = [vp]
+        lib.kpp_server_reset_stats.argtypes = [vp]
+        lib.kpp_server_reset_stats.restype = ctypes.c_int
         for name in ("kpp_server_create", "kpp_server_add_matrix", "kpp_server_submit", "kpp_server_poll",
                      "kpp_server_wait_all", "kpp_server_stats"):
             getattr(lib, name).restype = ctypes.c_int
@@ -141,6 +144,7 @@ def load(path: str | None = None):
         lib.kpp_plan_destroy.argtypes = [vp]
         lib.kpp_plan_destroy.restype = None
         lib.kpp_tune_cache_size.restype = i64
+        lib.kpp_launch_count.restype = ctypes.c_uint64
         lib.kpp_tune_cache_clear.restype = None
         lib.kpp_tune_cache_save.argtypes = [ctypes.c_char_p]
         lib.kpp_tune_cache_load.argtypes = [ctypes.c_char_p]
@@ -363,6 +367,11 @@ class Plan:
         self.close()
 
 
+def launch_count() -> int:
+    """Kernel launches the library has issued in this process."""
+    return int(load().kpp_launch_count())
+
+
 def tune_cache_size() -> int:
     return int(load().kpp_tune_cache_size())
 
@@ -470,6 +479,9 @@ class Server:
         st = ServingStats()
         _check(self._lib.kpp_server_stats(self.handle, ctypes.byref(st)))
         return st.as_dict()
+
+    def reset_stats(self) -> None:
+        _check(self._lib.kpp_server_reset_stats(self.handle))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -177,10 +177,19 @@ def serving_requests(n_req: int = 1024, n_mats: int = 32, mean_gap_ms: float = 2
 # Same recipes as above; the stored (rounded) matrix is the system and b is formed in FP64 from it.
 # ---------------------------------------------------------------------------------------------
 
+HOST_QR = False  # factor the Gaussian matrix of torch_haar on the host (see torch_haar)
+
+
 def torch_haar(n: int, gen, device: str = "cuda"):
+    """Haar orthogonal matrix from a seeded device Gaussian.  With HOST_QR the QR factorisation runs on
+    the host (the same Gaussian; for profilers under which torch's device linear algebra cannot load)."""
     import torch
     g = torch.randn(n, n, generator=gen, device=device, dtype=torch.float64)
-    q, r = torch.linalg.qr(g)
+    if HOST_QR:
+        q, r = torch.linalg.qr(g.cpu())
+        q, r = q.to(device), r.to(device)
+    else:
+        q, r = torch.linalg.qr(g)
     return q * torch.sign(torch.diagonal(r))[None, :]
 
 
@@ -245,3 +254,12 @@ def torch_spd(n: int, n_out: int, out_lo: float, out_hi: float, bulk_lo: float, 
     A = A.to(tdt)
     A = 0.5 * (A + A.T)  # symmetric again after rounding (exact: a + a = 2a, halving is exact)
     return A.contiguous(), sig
+
+
+def stays_spd(A, margin: float) -> bool:
+    """Whether the stored matrix (widened to FP64) minus margin * I is positive definite: rounding a
+    matrix with a wide spectrum to BF16 can push its smallest eigenvalues below zero."""
+    import torch
+    Ad = A.double()
+    Ad.diagonal().sub_(margin)
+    return int(torch.linalg.cholesky_ex(Ad)[1].item()) == 0
