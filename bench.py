@@ -447,7 +447,7 @@ class Batched(Workload):
         self.kpp, self.torch = kpp, torch
         self.A, self.B = [], []
         for i in range(self.nsys):
-            A, B, _ = W.torch_gaussian_rows(self.m, self.n, 20, 100.0, seed=3000 + 1000 * rank + i, k_rhs=self.k)
+            A, B, _ = W.torch_gaussian_rows(self.m, self.n, 20, 100.0, seed=self.system_seed(rank, i), k_rhs=self.k)
             self.A.append(A)
             self.B.append(B)
         rn = (self.A[0].double() ** 2).sum(dim=1)
@@ -457,6 +457,10 @@ class Batched(Workload):
         self.prm = kpp.params(lam=self.lam, tol=self.tol, refine=1, inner_tol=1e-3, seed=0, sys_id=rank * 4096,
                               grid=kpp.GRID_TUNE)
         self.cap_stream = torch.cuda.Stream()
+
+    def system_seed(self, rank, i):
+        """Seed of system i on rank r: every rank of a replicas run builds its own systems."""
+        return 3000 + 1000 * rank + i
 
     def step(self):
         kpp, torch = self.kpp, self.torch
@@ -677,6 +681,18 @@ def make_workload(args):
 # Arms
 # ---------------------------------------------------------------------------------------------
 
+def aggregate_ranks(total_ms, total_units, dist=None, device="cuda"):
+    """Whole-job numbers of a replicas run: the slowest rank's time and the units of all ranks."""
+    if dist is None:
+        return total_ms, total_units
+    import torch
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(total_units)], device=device, dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def run_reference(args, rank: int):
     """The FP64 CPU oracle on the host cores, each step a bounded sample of the same workload."""
     if rank != 0:
@@ -783,15 +799,7 @@ def main():
         if dist:
             dist.barrier()
     assert all(st["ok"] for st in steps), steps
-    total_ms = sum(step_ms)
-    total_units = sum(st["units"] for st in steps)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([total_units], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_units = int(u.item())
+    total_ms, total_units = aggregate_ranks(sum(step_ms), sum(st["units"] for st in steps), dist)
     value = total_units / (total_ms / 1e3)
     peaks = _peaks()
 
