@@ -46,9 +46,7 @@ SERVING_METRIC = "solves/s + p99 latency"
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the same
 # kernel build and workload (the summaries under profiles/ give the commands).  Absent: not captured.
-NCU_TRAFFIC_PER_LAUNCH = {
-    "cd3_kernel/cdpp4096": 6.700243e9 + 15.2768e6,  # profiles/cd3_kernel_cdpp4096.md
-}
+NCU_TRAFFIC_PER_LAUNCH = {}
 
 
 def _log(msg):
@@ -212,7 +210,7 @@ class SingleFP64(Workload):
             self.sy = W.cdpp_fp64_spd()
             self.desc = ("CD++ FP64, dense SPD n=4096 = U diag(sigma) U^T (U Haar; 50 outliers log-spaced 1e2..1e4 + "
                          "4046 ~U[1,10]), b~N(0,I), s=64 contiguous, lambda=1e-4, tol=1e-8, x0=0")
-            self.kernel = "cd3_kernel"
+            self.kernel = "cd4_kernel"
         else:
             self.sy = W.kpp_fp64_2000x200()
             self.desc = ("K++ FP64, 2000x200 consistent LS A=Z D V^T (10 outliers 1e2..1e3 + 190 ~U[1,2]), s=20, "

@@ -502,13 +502,418 @@ drain:
 }
 
 // ---------------------------------------------------------------------------------------------
+// cd4_kernel: the FP64 dataflow step for one right-hand side, scheduled for an FP64 pipe that
+// issues a warp instruction every ~64 cycles per SMSP.
+//
+// Same dataflow and memo as cd3_kernel (owners of S_{t+1} hand r_{t+1} = R_x[S_{t+1}] over through
+// the mailbox; u = W_S^T r with W = G^{-1} A_S memoised), but every FP64 instruction is placed so
+// that the four SMSPs share the work and no phase runs on one warp while the others wait:
+//   * u = W_S^T r by warps 0-3 (one per SMSP, 16 rows each), a 4-way partial sum;
+//   * y = G^{-1} r on the owners' rows of S_t by warps 4-7 at the same time (rows by lanes, the
+//     block dimension split over the four warps; G^{-1} is symmetric, so its stored rows are the
+//     columns needed);
+//   * the R_m / R_x update (warp 0) and the x / m update (warp 1) run on different SMSPs; warp 0
+//     writes r_{t+1} into the mailbox straight from registers;
+//   * |r|^2 of each step is summed only by the CTAs that publish it (over their rows), and the
+//     window sums E0 / E1 are reduced over the group at the checkpoints;
+//   * block draws come from a table filled 64 steps ahead; two __syncthreads per step.
+// Requirements (checked by the host): FP64 storage with W, k = 1, column chunk <= 32, s <= 64.
+// ---------------------------------------------------------------------------------------------
+constexpr int CD4_RING = 128;    // mailbox slots (steps)
+constexpr int CD4_PERIOD = 64;   // steps between drift-bounding group barriers (<= CD4_RING / 2)
+constexpr int CD4_CW = 32;       // columns per CTA at most
+constexpr int CD4_S = 64;        // block size at most
+constexpr int CD4_JT = 128;      // block-draw table (steps)
+
+struct Smem4 {
+    int tile[2], ginv[2], total;
+};
+
+__host__ __device__ inline Smem4 smem4_layout(int s, int64_t CW) {
+    auto al = [](int v) { return (v + 127) / 128 * 128; };
+    Smem4 L;
+    int o = 0;
+    const int tile = al((int)(s * CW * 8));
+    const int ginv = al((int)min64(CW + 2, s) * s * 8);
+    L.tile[0] = o; o += tile;
+    L.tile[1] = o; o += tile;
+    L.ginv[0] = o; o += ginv;
+    L.ginv[1] = o; o += ginv;
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ systems, Common cm) {
+    const Sys3 &sys = systems[blockIdx.x / cm.G];
+    const SysArgs sa = sys.a;
+    const void *tmap = &sys.tmapT;
+    unsigned long long *mail = sys.mail;
+    const int g = blockIdx.x % cm.G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = cm.s, nb = cm.nb;
+    const int64_t n = cm.rows;
+    const double *__restrict__ b = (const double *)sa.b;
+    double *__restrict__ x = (double *)sa.x;
+    double *__restrict__ Rx = (double *)sa.Rx;
+    const double *__restrict__ Ginv = (const double *)sa.Ginv;
+    double *__restrict__ xpart = (double *)sa.part;  // G x 2: window-sum partials at checkpoints
+
+    extern __shared__ __align__(128) unsigned char sm[];
+    const Smem4 L = smem4_layout(s, cm.CW);
+    unsigned char *const tile0 = sm + L.tile[0];
+    const int tile_stride = L.tile[1] - L.tile[0];
+    unsigned char *const ginv0 = sm + L.ginv[0];
+    const int ginv_stride = L.ginv[1] - L.ginv[0];
+#define TILE4(bf) ((const double *)(tile0 + (bf) * tile_stride))
+#define GINV4(bf) ((const double *)(ginv0 + (bf) * ginv_stride))
+    __shared__ double s_r[CD4_S], s_y[CD4_S];
+    __shared__ double s_red[4][CD4_CW], s_yred[4][CD4_CW];
+    __shared__ double xc[CD4_CW], mc[CD4_CW], rxc[CD4_CW], rmc[CD4_CW];
+    __shared__ int s_jt[CD4_JT];
+    __shared__ double s_epart[2][2];   // my partial window sums, by checkpoint-pair parity
+    __shared__ double s_pend;          // |r_{t+1}|^2 over the rows I published, not yet counted
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ ColState st[1];
+    __shared__ double s_part[NW];
+    __shared__ int s_stop, s_need, s_fail, s_pending[2], s_glo[2];
+    __shared__ unsigned s_phase[2];
+    __shared__ double s_beta;
+
+    GroupSync gs{sa.bar, sa.err, 0u, (unsigned)cm.G, cm.timeout_ns};
+    const int64_t c0 = min64((int64_t)g * cm.CW, n);
+    const int64_t c1 = min64(c0 + cm.CW, n);
+    const int cw = (int)(c1 - c0);
+    const int CWs = (int)cm.CW;
+    const int zeta = nb;
+    const int64_t t_begin = cm.t0_state ? sa.sc[0].t : sa.t0;
+    int64_t t = t_begin;
+    int64_t t_end = cm.t0_state ? t + cm.max_iters : cm.max_iters;
+    if (cm.t0_state && !sa.sc[0].active) t_end = t;
+
+    if (threadIdx.x == 0) {
+        ColState cs = {};
+        const SolveScalars &in = sa.sc[0];
+        cs.E0 = in.E0; cs.E1 = in.E1; cs.rhat = in.rhat; cs.rho = in.rho; cs.ci = in.ci;
+        cs.active = in.active; cs.status = in.status;
+        cs.res_true = NAN;
+        cs.res_est = NAN;
+        st[0] = cs;
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+        tensormap_acquire(tmap);
+        s_pending[0] = s_pending[1] = 0;
+        s_phase[0] = s_phase[1] = 0;
+        s_fail = 0;
+        s_epart[0][0] = s_epart[0][1] = s_epart[1][0] = s_epart[1][1] = 0.0;
+        s_pend = 0.0;
+    }
+    for (int e = threadIdx.x; e < CD4_JT; e += NT) {  // draws of steps t_begin .. t_begin + JT - 1
+        const int64_t tt = t_begin + e;
+        s_jt[tt % CD4_JT] = draw_block(cm.seed, tt, sa.sys_id, nb);
+    }
+    {
+        // |b|^2 over the group (fixed order)
+        double acc = 0.0;
+        for (int64_t i = (int64_t)g * NT + threadIdx.x; i < n; i += (int64_t)cm.G * NT) acc += b[i] * b[i];
+        __syncthreads();
+        const double v = block_sum<NT>(acc, s_part);
+        if (threadIdx.x == 0) sa.rpart[g] = v;
+        if (!group_barrier(gs)) goto drain;
+        if (threadIdx.x == 0) {
+            double tt = 0.0;
+            for (int h = 0; h < cm.G; ++h) tt += __ldcg(sa.rpart + h);
+            st[0].bn2 = tt;
+        }
+        __syncthreads();
+        if (!group_barrier(gs)) goto drain;
+    }
+    if (cm.init_residual) {
+        if (!true_residual_phase<double, double, 1>(sa, cm, g, gs, st, s_part, Rx)) goto drain;
+    }
+    for (int e = threadIdx.x; e < cw; e += NT) {
+        xc[e] = __ldcg(x + c0 + e);
+        mc[e] = 0.0;
+        rxc[e] = __ldcg(Rx + c0 + e);
+        rmc[e] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        const double rho = st[0].rho;
+        s_beta = (1.0 - rho) / (1.0 + rho);
+    }
+    __syncthreads();
+
+    {
+        // prefetch of step tt into buffer bf: my chunk's W tile, and the G^{-1} rows of my chunk
+        // that fall inside the block (symmetric: they are also the columns y needs)
+        auto issue = [&](int64_t tt, int bf) {
+            const int j = s_jt[tt % CD4_JT];
+            const int64_t S0 = (int64_t)j * s;
+            const int len = (int)min64(s, n - S0);
+            const unsigned abytes = (unsigned)(s * CWs * 8);
+            int glo = (int)max64(0, c0 - S0);
+            int ghi = (int)min64(len, c1 - S0);
+            if (ghi < glo) ghi = glo;
+            if (len & 1) glo &= ~1;  // 16-byte aligned source row offset
+            const unsigned gbytes = (unsigned)(((ghi - glo) * len * 8 + 15) / 16 * 16);
+            mbar_arrive_expect_tx(&mbar[bf], abytes + gbytes);
+            tma_load_2d((void *)TILE4(bf), tmap, (int)c0, (int)S0, &mbar[bf]);
+            if (gbytes) bulk_load((void *)GINV4(bf), Ginv + (size_t)j * s * s + (size_t)glo * len, gbytes, &mbar[bf]);
+            s_glo[bf] = glo;
+            s_pending[bf] = 1;
+        };
+        // warp 0: publish my rows of r_tt (values in lanes) and note their |.|^2
+        auto publish_lanes = [&](int64_t tt, double v_lane) {
+            const int j = s_jt[tt % CD4_JT];
+            const int64_t S0 = (int64_t)j * s;
+            const int len = (int)min64(s, n - S0);
+            const int64_t col = c0 + lane;
+            const bool mine = lane < cw && col >= S0 && col < S0 + len;
+            unsigned long long *slot = mail + (size_t)(tt % CD4_RING) * s * 2;
+            if (mine) mail_put(slot + (size_t)(col - S0) * 2, v_lane, (unsigned)(tt + 1));
+            double q = mine ? v_lane * v_lane : 0.0;
+            if (__any_sync(0xffffffffu, mine)) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+                if (lane == 0) s_pend = q;
+            } else if (lane == 0) {
+                s_pend = 0.0;
+            }
+        };
+        auto window_slot = [&](int64_t tt, int &pair, int &w) {
+            const int64_t ph = tt % (2 * (int64_t)zeta);
+            pair = (int)((tt / (2 * (int64_t)zeta)) & 1);
+            w = ph < zeta ? 0 : 1;
+        };
+
+        if (threadIdx.x == 0 && t < t_end) {
+            issue(t, (int)(t & 1));
+            if (t + 1 < t_end) issue(t + 1, (int)((t + 1) & 1));
+        }
+        if (warp == 0 && t < t_end) publish_lanes(t, lane < cw ? rxc[lane] : 0.0);
+        __syncthreads();
+
+        while (t < t_end) {
+            const int bf = (int)(t & 1);
+            const int j = s_jt[t % CD4_JT];
+            const int64_t S0 = (int64_t)j * s;
+            const int len = (int)min64(s, n - S0);
+
+            // ---- count |r_t|^2 of the rows I published; gather r_t; wait for the tiles ----
+            if (threadIdx.x == 0) {
+                int pr, w;
+                window_slot(t, pr, w);
+                s_epart[pr][w] += s_pend;
+                s_pend = 0.0;
+            }
+            if (threadIdx.x < len) {
+                const unsigned long long *slot = mail + (size_t)(t % CD4_RING) * s * 2;
+                const unsigned tag = (unsigned)(t + 1);
+                double v;
+                if (!mail_get(slot + (size_t)threadIdx.x * 2, tag, v)) {
+                    const uint64_t tq = globaltimer_ns();
+                    unsigned polls = 0;
+                    while (!mail_get(slot + (size_t)threadIdx.x * 2, tag, v)) {
+                        if ((++polls & 63u) == 0u) {
+                            if (globaltimer_ns() - tq > cm.timeout_ns) {
+                                s_fail = 1;
+                                group_fail(gs, KPP_ERR_TIMEOUT);
+                                v = 0.0;
+                                break;
+                            }
+                            if (*(volatile int *)gs.err != 0) {
+                                s_fail = 1;
+                                v = 0.0;
+                                break;
+                            }
+                        }
+                    }
+                }
+                s_r[threadIdx.x] = v;
+            } else if (threadIdx.x < CD4_S) {
+                s_r[threadIdx.x] = 0.0;
+            }
+            if (threadIdx.x == 32) {
+                if (!mbar_wait_bounded(&mbar[bf], s_phase[bf], cm.timeout_ns)) {
+                    s_fail = 1;
+                    group_fail(gs, KPP_ERR_TIMEOUT);
+                } else {
+                    s_phase[bf] ^= 1u;
+                    s_pending[bf] = 0;
+                }
+            }
+            __syncthreads();  // (A)
+            if (s_fail) break;
+
+            const int64_t olo = max64(c0, S0), ohi = min64(c1, S0 + len);  // my columns inside S_t
+            if (warp < 4) {
+                // u partial: rows [16 warp, 16 warp + 16) of the W tile, lane = column
+                const double *tl = TILE4(bf);
+                double acc = 0.0;
+                if (lane < cw) {
+                    const int a0 = warp * 16, a1 = min(len, a0 + 16);
+                    for (int a = a0; a < a1; ++a) acc = fma(tl[a * CWs + lane], s_r[a], acc);
+                }
+                s_red[warp][lane] = acc;
+            } else if (ohi > olo) {
+                // y on my rows of S_t: lane = row (olo - S0 + lane), block index d split over warps 4-7
+                const int q = warp - 4;
+                const int rr = (int)(olo - S0) + lane;  // row of G^{-1} in the block
+                const int glo = s_glo[bf];
+                double acc = 0.0;
+                if (lane < (int)(ohi - olo)) {
+                    const double *grow = GINV4(bf) + (size_t)(rr - glo) * len;
+                    const int d0 = q * len / 4, d1 = (q + 1) * len / 4;
+                    // rotate the start so that lanes (stride len) hit different banks
+                    const int span = d1 - d0;
+                    for (int i = 0; i < span; ++i) {
+                        int d = d0 + ((i + lane) % span);
+                        acc = fma(grow[d], s_r[d], acc);
+                    }
+                }
+                s_yred[q][lane] = acc;
+            }
+            __syncthreads();  // (B)
+
+            if (warp == 0) {
+                // u, then R_m and R_x on my columns; hand r_{t+1} over at once
+                double rx = 0.0;
+                if (lane < cw) {
+                    const double u = (s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane]);
+                    const double rm = s_beta * (rmc[lane] - u);
+                    rmc[lane] = rm;
+                    rx = rxc[lane] - u + cm.eta * rm;
+                    rxc[lane] = rx;
+                }
+                if (t + 1 < t_end) publish_lanes(t + 1, rx);
+            } else if (warp == 1) {
+                // x and m on my columns: w = y on the columns inside S_t
+                if (lane < cw) {
+                    const int64_t col = c0 + lane;
+                    double wv = 0.0;
+                    if (col >= olo && col < ohi) {
+                        const int l = (int)(col - olo);
+                        wv = (s_yred[0][l] + s_yred[1][l]) + (s_yred[2][l] + s_yred[3][l]);
+                    }
+                    const double mm = s_beta * (mc[lane] - wv);
+                    mc[lane] = mm;
+                    xc[lane] = xc[lane] - wv + cm.eta * mm;
+                }
+            } else if (warp == 2) {
+                if (lane == 0 && t + 2 < t_end) issue(t + 2, bf);  // buffer bf is free after (B)
+            } else if (warp == 3) {
+                // refill the draw table 64 steps ahead
+                if (((t - t_begin) % 64) == 0 && t > t_begin) {
+                    for (int e = lane; e < 64; e += 32) {
+                        const int64_t tt = t + 64 + e;
+                        s_jt[tt % CD4_JT] = draw_block(cm.seed, tt, sa.sys_id, nb);
+                    }
+                }
+            }
+
+            const int64_t ph = t % (2 * (int64_t)zeta);
+            const bool ckpt = (ph == 2 * zeta - 1);
+            t += 1;
+            if (ckpt) {
+                // window sums of the finished pair over the group, then the checkpoint of Alg. 3
+                __syncthreads();
+                const int pr = (int)(((t - 1) / (2 * (int64_t)zeta)) & 1);
+                if (threadIdx.x == 0) {
+                    xpart[(size_t)g * 2 + 0] = s_epart[pr][0];
+                    xpart[(size_t)g * 2 + 1] = s_epart[pr][1];
+                    s_epart[pr][0] = s_epart[pr][1] = 0.0;
+                }
+                for (int e = threadIdx.x; e < cw; e += NT) x[c0 + e] = xc[e];
+                if (!group_barrier(gs)) break;
+                if (threadIdx.x == 0) {
+                    double e0 = 0.0, e1 = 0.0;
+                    for (int h = 0; h < cm.G; ++h) {
+                        e0 += __ldcg(xpart + (size_t)h * 2 + 0);
+                        e1 += __ldcg(xpart + (size_t)h * 2 + 1);
+                    }
+                    ColState &cs = st[0];
+                    cs.E0 += e0;
+                    cs.E1 += e1;
+                    cs.res_est = cs.bn2 > 0.0 ? sqrt(cs.E1 / cs.bn2) : sqrt(cs.E1);
+                    s_need = (cm.tol > 0.0 && cs.E1 <= cm.tol * cm.tol * cs.bn2 && cm.confirm) ? 1 : 0;
+                }
+                __syncthreads();
+                if (s_need) {
+                    // true residual; it also replaces R_x (my rows are re-read below)
+                    if (!true_residual_phase<double, double, 1>(sa, cm, g, gs, st, s_part, Rx)) break;
+                    for (int e = threadIdx.x; e < cw; e += NT) rxc[e] = __ldcg(Rx + c0 + e);
+                    __syncthreads();
+                    // republish r_t from the new R_x (its |.|^2 replaces the pending one)
+                    if (warp == 0 && t < t_end) publish_lanes(t, lane < cw ? rxc[lane] : 0.0);
+                    if (!group_barrier(gs)) break;
+                }
+                if (threadIdx.x == 0) {
+                    if (st[0].active) checkpoint_column(st[0], cm, zeta);
+                    const double rho = st[0].rho;
+                    s_beta = (1.0 - rho) / (1.0 + rho);
+                    s_stop = !st[0].active;
+                }
+                __syncthreads();
+                if (s_stop) break;
+            } else if ((t % CD4_PERIOD) == 0) {
+                // bound the drift between CTAs (mailbox slots are reused every CD4_RING steps)
+                if (!group_barrier(gs)) break;
+            }
+        }
+    }
+drain:
+    __syncthreads();
+    for (int e = threadIdx.x; e < cw; e += NT) x[c0 + e] = xc[e];
+    if (threadIdx.x == 0) {
+        for (int bf = 0; bf < 2; ++bf)
+            if (s_pending[bf]) {
+                if (mbar_wait_bounded(&mbar[bf], s_phase[bf], cm.timeout_ns)) s_phase[bf] ^= 1u;
+                else group_fail(gs, KPP_ERR_TIMEOUT);
+                s_pending[bf] = 0;
+            }
+    }
+    __syncthreads();
+    if (g == 0 && threadIdx.x == 0) {
+        const ColState &cs = st[0];
+        SolveScalars &out = sa.sc[0];
+        out.E0 = cs.E0; out.E1 = cs.E1; out.rhat = cs.rhat; out.rho = cs.rho; out.ci = cs.ci;
+        out.active = cs.active; out.status = cs.status; out.res_est = cs.res_est; out.bn2 = cs.bn2;
+        out.t = t;
+    }
+#undef TILE4
+#undef GINV4
+}
+
+// ---------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------
 size_t cd3_smem_bytes(int s, int64_t CW, int KP, int ta_size, int tc_size, bool use_w) {
     return (size_t)smem3_layout(s, CW, KP, ta_size, tc_size, use_w).total;
 }
 
-size_t cd3_mail_bytes(int s, int KP, bool f64) { return (size_t)CD3_RING * s * KP * (f64 ? 2 : 1) * 8; }
+// sized for either kernel (the FP64 single-column kernel uses the longer ring)
+size_t cd3_mail_bytes(int s, int KP, bool f64) {
+    const int ring = CD3_RING > CD4_RING ? CD3_RING : CD4_RING;
+    return (size_t)ring * s * KP * (f64 ? 2 : 1) * 8;
+}
+
+// s >= 2: the checkpoint partials (G x 2 doubles) live in the G x s partial buffer
+static bool cd4_fits(int s, int64_t CW) { return s >= 2 && s <= CD4_S && CW >= 2 && CW <= CD4_CW && CW % 2 == 0; }
+
+static cudaError_t launch4(const void *d_sys, int nsys, const Common &cm, cudaStream_t st) {
+    const size_t smem = (size_t)smem4_layout(cm.s, cm.CW).total;
+    cudaError_t e = cudaFuncSetAttribute(cd4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cd4_kernel, NT, smem);
+    if (e != cudaSuccess) return e;
+    if ((int64_t)per_sm * sm_count() < (int64_t)nsys * cm.G) return cudaErrorCooperativeLaunchTooLarge;
+    Common c = cm;
+    const Sys3 *p = (const Sys3 *)d_sys;
+    void *args[] = {(void *)&p, (void *)&c};
+    note_launch();
+    return cudaLaunchCooperativeKernel((const void *)cd4_kernel, dim3((unsigned)(nsys * cm.G)), dim3(NT), args, smem, st);
+}
 
 size_t sys3_bytes() { return sizeof(Sys3); }
 
@@ -547,6 +952,7 @@ static cudaError_t launch3_kp(const void *d_sys, int nsys, const Common &cm, int
 }
 
 cudaError_t launch_cd3(int dtype, const void *d_sys, int nsys, const Common &cm, int KP, cudaStream_t st) {
+    if (dtype == KPP_F64 && KP == 1 && cm.k == 1 && cd4_fits(cm.s, cm.CW)) return launch4(d_sys, nsys, cm, st);
     if (dtype == KPP_F64) return launch3_kp<double, double, true>(d_sys, nsys, cm, KP, st);
     if (dtype == KPP_F32) return launch3_kp<float, float, false>(d_sys, nsys, cm, KP, st);
     return launch3_kp<__nv_bfloat16, float, false>(d_sys, nsys, cm, KP, st);

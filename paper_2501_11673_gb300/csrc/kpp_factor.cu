@@ -414,8 +414,10 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
         }                                                                    \
     } while (0)
     KPP_TRY(cudaMalloc(&F.L, nb * blk * sizeof(double)));
-    if (A.dtype == KPP_F64) KPP_TRY(cudaMalloc(&F.Ginv, nb * blk * sizeof(double)));
-    else KPP_TRY(cudaMalloc(&F.Ginv32, nb * blk * sizeof(float)));
+    // 64 bytes of slack: the iteration kernels copy G^{-1} rows in 16-byte multiples, which can run up
+    // to 8 bytes past the last block when its rows have an odd length
+    if (A.dtype == KPP_F64) KPP_TRY(cudaMalloc(&F.Ginv, nb * blk * sizeof(double) + 64));
+    else KPP_TRY(cudaMalloc(&F.Ginv32, nb * blk * sizeof(float) + 64));
     KPP_TRY(cudaMalloc(&G, nb * blk * sizeof(double)));
     KPP_TRY(cudaMalloc(&Linv, nb * blk * sizeof(double)));
     KPP_TRY(cudaMalloc(&bad, sizeof(int)));

@@ -150,6 +150,24 @@ def test_cdpp_fp64_lockstep_ragged(K, variant, grid):
         assert rel(x, res.x) <= 1e-10, (T, rel(x, res.x))
 
 
+@pytest.mark.parametrize("grid", [0, 20, 24])
+def test_cdpp_fp64_single_column_kernel_lockstep(K, grid):
+    """The single-column FP64 dataflow kernel (column chunks <= 32, s <= 64): ragged last block, runs
+    longer than the mailbox ring and several checkpoints, then a solve to tolerance that stops at the
+    oracle's checkpoint (window sums reduced over the group, r republished after the true residual)."""
+    A, b, _ = W.spd(640, 10, 1e2, 1e3, 1.0, 5.0, seed_A=14, seed_b=15)
+    s = 50  # 13 blocks, the last of 40 rows
+    for T in (3, 2 * 13 * 10 + 3, 700):
+        x, rep, res = _kpp_pair(K, A, b, s, 1e-4, T=T, grid=grid, cd=True)
+        assert rep.iters == T == res.iters
+        assert rel(x, res.x) <= 1e-10, (T, rel(x, res.x))
+    x, rep, res = _kpp_pair(K, A, b, s, 1e-4, tol=1e-9, grid=grid, cd=True)
+    assert rep.status == K.OK and res.status == oracle.OK
+    assert rep.iters == res.iters
+    assert rep.rel_res_true <= 1e-9
+    assert rel(x, res.x) <= 1e-10
+
+
 def test_cdpp_fp64_nonzero_start(K):
     A, b, _ = W.spd(130, 3, 1e2, 1e3, 1.0, 5.0, seed_A=12, seed_b=13)
     x0 = np.random.default_rng(3).standard_normal(130)
