@@ -507,26 +507,28 @@ drain:
 //
 // Same dataflow and memo as cd3_kernel (owners of S_{t+1} hand r_{t+1} = R_x[S_{t+1}] over through
 // the mailbox; u = W_S^T r with W = G^{-1} A_S memoised), but every FP64 instruction is placed so
-// that the four SMSPs share the work and no phase runs on one warp while the others wait:
-//   * u = W_S^T r by warps 0-3 (one per SMSP, 16 rows each), a 4-way partial sum;
-//   * y = G^{-1} r on the owners' rows of S_t by warps 4-7 at the same time (rows by lanes, the
-//     block dimension split over the four warps; G^{-1} is symmetric, so its stored rows are the
-//     columns needed);
-//   * the R_m / R_x update (warp 0) and the x / m update (warp 1) run on different SMSPs; warp 0
-//     writes r_{t+1} into the mailbox straight from registers;
+// that the four SMSPs share the work and the owners' critical path carries nothing else:
+//   * u = W_S^T r by warps 0-3 (one per SMSP, 16 rows each, two accumulation chains), then warp 0
+//     alone (after a barrier of warps 0-3) updates R_m / R_x and writes r_{t+1} into the mailbox
+//     straight from registers;
+//   * warps 4-7 at the same time: y = G^{-1} r on the owners' rows of S_t (rows by lanes, the block
+//     dimension split over the four warps; G^{-1} is symmetric, so its stored rows are the columns
+//     needed), then warp 4 updates x and m (after a barrier of warps 4-7) and warp 5 prefetches;
 //   * |r|^2 of each step is summed only by the CTAs that publish it (over their rows), and the
 //     window sums E0 / E1 are reduced over the group at the checkpoints;
-//   * block draws come from a table filled 64 steps ahead; two __syncthreads per step.
-// Requirements (checked by the host): FP64 storage with W, k = 1, column chunk <= 32, s <= 64.
+//   * block draws come from a table filled 64 steps ahead; tiles are triple-buffered and r double-
+//     buffered so that one __syncthreads per step orders everything.
+// Requirements (checked by the host): FP64 storage with W, k = 1, column chunk <= 32, 2 <= s <= 64.
 // ---------------------------------------------------------------------------------------------
 constexpr int CD4_RING = 128;    // mailbox slots (steps)
 constexpr int CD4_PERIOD = 64;   // steps between drift-bounding group barriers (<= CD4_RING / 2)
 constexpr int CD4_CW = 32;       // columns per CTA at most
 constexpr int CD4_S = 64;        // block size at most
 constexpr int CD4_JT = 128;      // block-draw table (steps)
+constexpr int CD4_NB = 3;        // tile buffers (prefetch distance 2)
 
 struct Smem4 {
-    int tile[2], ginv[2], total;
+    int tile[CD4_NB], ginv[CD4_NB], total;
 };
 
 __host__ __device__ inline Smem4 smem4_layout(int s, int64_t CW) {
@@ -535,12 +537,20 @@ __host__ __device__ inline Smem4 smem4_layout(int s, int64_t CW) {
     int o = 0;
     const int tile = al((int)(s * CW * 8));
     const int ginv = al((int)min64(CW + 2, s) * s * 8);
-    L.tile[0] = o; o += tile;
-    L.tile[1] = o; o += tile;
-    L.ginv[0] = o; o += ginv;
-    L.ginv[1] = o; o += ginv;
+    for (int i = 0; i < CD4_NB; ++i) {
+        L.tile[i] = o;
+        o += tile;
+    }
+    for (int i = 0; i < CD4_NB; ++i) {
+        L.ginv[i] = o;
+        o += ginv;
+    }
     L.total = o;
     return L;
+}
+
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
 __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ systems, Common cm) {
@@ -566,17 +576,17 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
     const int ginv_stride = L.ginv[1] - L.ginv[0];
 #define TILE4(bf) ((const double *)(tile0 + (bf) * tile_stride))
 #define GINV4(bf) ((const double *)(ginv0 + (bf) * ginv_stride))
-    __shared__ double s_r[CD4_S], s_y[CD4_S];
+    __shared__ double s_r[2][CD4_S];
     __shared__ double s_red[4][CD4_CW], s_yred[4][CD4_CW];
     __shared__ double xc[CD4_CW], mc[CD4_CW], rxc[CD4_CW], rmc[CD4_CW];
     __shared__ int s_jt[CD4_JT];
     __shared__ double s_epart[2][2];   // my partial window sums, by checkpoint-pair parity
-    __shared__ double s_pend;          // |r_{t+1}|^2 over the rows I published, not yet counted
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ double s_pend;          // |r|^2 over the rows I published last, not yet counted
+    __shared__ __align__(8) uint64_t mbar[CD4_NB];
     __shared__ ColState st[1];
     __shared__ double s_part[NW];
-    __shared__ int s_stop, s_need, s_fail, s_pending[2], s_glo[2];
-    __shared__ unsigned s_phase[2];
+    __shared__ int s_stop, s_need, s_fail, s_pending[CD4_NB], s_glo[CD4_NB];
+    __shared__ unsigned s_phase[CD4_NB];
     __shared__ double s_beta;
 
     GroupSync gs{sa.bar, sa.err, 0u, (unsigned)cm.G, cm.timeout_ns};
@@ -589,6 +599,12 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
     int64_t t = t_begin;
     int64_t t_end = cm.t0_state ? t + cm.max_iters : cm.max_iters;
     if (cm.t0_state && !sa.sc[0].active) t_end = t;
+    // running step counters (no 64-bit division in the loop)
+    int ph = (int)(t % (2 * (int64_t)zeta));                 // t mod 2 zeta
+    int pair = (int)((t / (2 * (int64_t)zeta)) & 1);        // parity of the checkpoint pair of t
+    int since = 0;                                           // (t - t_begin) mod 64
+    int per = (int)(t % CD4_PERIOD);                         // t mod CD4_PERIOD
+    int buf = (int)(t % CD4_NB);                             // tile buffer of step t
 
     if (threadIdx.x == 0) {
         ColState cs = {};
@@ -598,12 +614,13 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
         cs.res_true = NAN;
         cs.res_est = NAN;
         st[0] = cs;
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int i = 0; i < CD4_NB; ++i) {
+            mbar_init(&mbar[i], 1);
+            s_pending[i] = 0;
+            s_phase[i] = 0;
+        }
         fence_mbar_init();
         tensormap_acquire(tmap);
-        s_pending[0] = s_pending[1] = 0;
-        s_phase[0] = s_phase[1] = 0;
         s_fail = 0;
         s_epart[0][0] = s_epart[0][1] = s_epart[1][0] = s_epart[1][1] = 0.0;
         s_pend = 0.0;
@@ -680,30 +697,25 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                 s_pend = 0.0;
             }
         };
-        auto window_slot = [&](int64_t tt, int &pair, int &w) {
-            const int64_t ph = tt % (2 * (int64_t)zeta);
-            pair = (int)((tt / (2 * (int64_t)zeta)) & 1);
-            w = ph < zeta ? 0 : 1;
-        };
 
         if (threadIdx.x == 0 && t < t_end) {
-            issue(t, (int)(t & 1));
-            if (t + 1 < t_end) issue(t + 1, (int)((t + 1) & 1));
+            issue(t, (int)(t % CD4_NB));
+            if (t + 1 < t_end) issue(t + 1, (int)((t + 1) % CD4_NB));
         }
         if (warp == 0 && t < t_end) publish_lanes(t, lane < cw ? rxc[lane] : 0.0);
         __syncthreads();
 
         while (t < t_end) {
-            const int bf = (int)(t & 1);
+            const int bf = buf;
+            const int rb = (int)(t & 1);
             const int j = s_jt[t % CD4_JT];
             const int64_t S0 = (int64_t)j * s;
             const int len = (int)min64(s, n - S0);
 
-            // ---- count |r_t|^2 of the rows I published; gather r_t; wait for the tiles ----
+            // ---- count |r_t|^2 of the rows I published (the writer of s_pend is thread 0 too);
+            //      gather r_t; wait for the tiles ----
             if (threadIdx.x == 0) {
-                int pr, w;
-                window_slot(t, pr, w);
-                s_epart[pr][w] += s_pend;
+                s_epart[pair][ph < zeta ? 0 : 1] += s_pend;
                 s_pend = 0.0;
             }
             if (threadIdx.x < len) {
@@ -729,11 +741,11 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                         }
                     }
                 }
-                s_r[threadIdx.x] = v;
+                s_r[rb][threadIdx.x] = v;
             } else if (threadIdx.x < CD4_S) {
-                s_r[threadIdx.x] = 0.0;
+                s_r[rb][threadIdx.x] = 0.0;
             }
-            if (threadIdx.x == 32) {
+            if (threadIdx.x == 64) {
                 if (!mbar_wait_bounded(&mbar[bf], s_phase[bf], cm.timeout_ns)) {
                     s_fail = 1;
                     group_fail(gs, KPP_ERR_TIMEOUT);
@@ -742,83 +754,100 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                     s_pending[bf] = 0;
                 }
             }
-            __syncthreads();  // (A)
+            __syncthreads();  // (A): r_t, the tiles of step t; every warp is done with step t - 1
             if (s_fail) break;
 
             const int64_t olo = max64(c0, S0), ohi = min64(c1, S0 + len);  // my columns inside S_t
+            const double *rv = s_r[rb];
             if (warp < 4) {
-                // u partial: rows [16 warp, 16 warp + 16) of the W tile, lane = column
+                // u partial: rows [16 warp, 16 warp + 16) of the W tile, lane = column, two chains
                 const double *tl = TILE4(bf);
-                double acc = 0.0;
+                double acc0 = 0.0, acc1 = 0.0;
                 if (lane < cw) {
                     const int a0 = warp * 16, a1 = min(len, a0 + 16);
-                    for (int a = a0; a < a1; ++a) acc = fma(tl[a * CWs + lane], s_r[a], acc);
-                }
-                s_red[warp][lane] = acc;
-            } else if (ohi > olo) {
-                // y on my rows of S_t: lane = row (olo - S0 + lane), block index d split over warps 4-7
-                const int q = warp - 4;
-                const int rr = (int)(olo - S0) + lane;  // row of G^{-1} in the block
-                const int glo = s_glo[bf];
-                double acc = 0.0;
-                if (lane < (int)(ohi - olo)) {
-                    const double *grow = GINV4(bf) + (size_t)(rr - glo) * len;
-                    const int d0 = q * len / 4, d1 = (q + 1) * len / 4;
-                    // rotate the start so that lanes (stride len) hit different banks
-                    const int span = d1 - d0;
-                    for (int i = 0; i < span; ++i) {
-                        int d = d0 + ((i + lane) % span);
-                        acc = fma(grow[d], s_r[d], acc);
+                    int a = a0;
+                    for (; a + 1 < a1; a += 2) {
+                        acc0 = fma(tl[a * CWs + lane], rv[a], acc0);
+                        acc1 = fma(tl[(a + 1) * CWs + lane], rv[a + 1], acc1);
                     }
+                    if (a < a1) acc0 = fma(tl[a * CWs + lane], rv[a], acc0);
                 }
-                s_yred[q][lane] = acc;
-            }
-            __syncthreads();  // (B)
-
-            if (warp == 0) {
-                // u, then R_m and R_x on my columns; hand r_{t+1} over at once
-                double rx = 0.0;
-                if (lane < cw) {
-                    const double u = (s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane]);
-                    const double rm = s_beta * (rmc[lane] - u);
-                    rmc[lane] = rm;
-                    rx = rxc[lane] - u + cm.eta * rm;
-                    rxc[lane] = rx;
-                }
-                if (t + 1 < t_end) publish_lanes(t + 1, rx);
-            } else if (warp == 1) {
-                // x and m on my columns: w = y on the columns inside S_t
-                if (lane < cw) {
-                    const int64_t col = c0 + lane;
-                    double wv = 0.0;
-                    if (col >= olo && col < ohi) {
-                        const int l = (int)(col - olo);
-                        wv = (s_yred[0][l] + s_yred[1][l]) + (s_yred[2][l] + s_yred[3][l]);
+                s_red[warp][lane] = acc0 + acc1;
+                named_barrier(1, 128);
+                if (warp == 0) {
+                    // u, then R_m and R_x on my columns; hand r_{t+1} over at once
+                    double rx = 0.0;
+                    if (lane < cw) {
+                        const double u = (s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane]);
+                        const double rm = s_beta * (rmc[lane] - u);
+                        rmc[lane] = rm;
+                        rx = rxc[lane] - u + cm.eta * rm;
+                        rxc[lane] = rx;
                     }
-                    const double mm = s_beta * (mc[lane] - wv);
-                    mc[lane] = mm;
-                    xc[lane] = xc[lane] - wv + cm.eta * mm;
-                }
-            } else if (warp == 2) {
-                if (lane == 0 && t + 2 < t_end) issue(t + 2, bf);  // buffer bf is free after (B)
-            } else if (warp == 3) {
-                // refill the draw table 64 steps ahead
-                if (((t - t_begin) % 64) == 0 && t > t_begin) {
+                    if (t + 1 < t_end) publish_lanes(t + 1, rx);
+                } else if (warp == 3 && since == 0 && t > t_begin) {
+                    // refill the draw table 64 steps ahead (the slots of steps t - 64 .. t - 1)
                     for (int e = lane; e < 64; e += 32) {
                         const int64_t tt = t + 64 + e;
                         s_jt[tt % CD4_JT] = draw_block(cm.seed, tt, sa.sys_id, nb);
                     }
                 }
+            } else {
+                if (warp == 5 && lane == 0 && t + 2 < t_end) {
+                    // the buffer of step t + 2 was last read at step t - 1, before (A)
+                    int b2 = bf + 2;
+                    if (b2 >= CD4_NB) b2 -= CD4_NB;
+                    issue(t + 2, b2);
+                }
+                const int q = warp - 4;
+                if (ohi > olo) {
+                    // y on my rows of S_t: lane = row (olo - S0 + lane), block index split over warps 4-7
+                    const int rr = (int)(olo - S0) + lane;  // row of G^{-1} in the block
+                    const int glo = s_glo[bf];
+                    double acc = 0.0;
+                    if (lane < (int)(ohi - olo)) {
+                        const double *grow = GINV4(bf) + (size_t)(rr - glo) * len;
+                        const int d0 = q * len / 4, d1 = (q + 1) * len / 4;
+                        const int span = d1 - d0;
+                        // rotate the start so that lanes (stride len) hit different banks
+                        for (int i = 0; i < span; ++i) {
+                            int d = d0 + ((i + lane) % span);
+                            acc = fma(grow[d], rv[d], acc);
+                        }
+                    }
+                    s_yred[q][lane] = acc;
+                }
+                named_barrier(2, 128);
+                if (warp == 4) {
+                    // x and m on my columns: w = y on the columns inside S_t
+                    if (lane < cw) {
+                        const int64_t col = c0 + lane;
+                        double wv = 0.0;
+                        if (col >= olo && col < ohi) {
+                            const int l = (int)(col - olo);
+                            wv = (s_yred[0][l] + s_yred[1][l]) + (s_yred[2][l] + s_yred[3][l]);
+                        }
+                        const double mm = s_beta * (mc[lane] - wv);
+                        mc[lane] = mm;
+                        xc[lane] = xc[lane] - wv + cm.eta * mm;
+                    }
+                }
             }
 
-            const int64_t ph = t % (2 * (int64_t)zeta);
             const bool ckpt = (ph == 2 * zeta - 1);
             t += 1;
+            if (++ph == 2 * zeta) {
+                ph = 0;
+                pair ^= 1;
+            }
+            if (++since == 64) since = 0;
+            if (++per == CD4_PERIOD) per = 0;
+            if (++buf == CD4_NB) buf = 0;
             if (ckpt) {
                 // window sums of the finished pair over the group, then the checkpoint of Alg. 3
                 __syncthreads();
-                const int pr = (int)(((t - 1) / (2 * (int64_t)zeta)) & 1);
                 if (threadIdx.x == 0) {
+                    const int pr = pair ^ 1;  // the pair that just ended
                     xpart[(size_t)g * 2 + 0] = s_epart[pr][0];
                     xpart[(size_t)g * 2 + 1] = s_epart[pr][1];
                     s_epart[pr][0] = s_epart[pr][1] = 0.0;
@@ -855,7 +884,7 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                 }
                 __syncthreads();
                 if (s_stop) break;
-            } else if ((t % CD4_PERIOD) == 0) {
+            } else if (per == 0) {
                 // bound the drift between CTAs (mailbox slots are reused every CD4_RING steps)
                 if (!group_barrier(gs)) break;
             }
@@ -865,7 +894,7 @@ drain:
     __syncthreads();
     for (int e = threadIdx.x; e < cw; e += NT) x[c0 + e] = xc[e];
     if (threadIdx.x == 0) {
-        for (int bf = 0; bf < 2; ++bf)
+        for (int bf = 0; bf < CD4_NB; ++bf)
             if (s_pending[bf]) {
                 if (mbar_wait_bounded(&mbar[bf], s_phase[bf], cm.timeout_ns)) s_phase[bf] ^= 1u;
                 else group_fail(gs, KPP_ERR_TIMEOUT);
