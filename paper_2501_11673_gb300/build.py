@@ -65,7 +65,8 @@ def build(verbose: bool = False, force: bool = False, extra: list | None = None)
         list(ex.map(run, jobs))
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-L" + cudalib, "-lcublas", "-Xlinker", "-rpath=" + cudalib])
         os.replace(tmp, LIB)
     return LIB
 

@@ -51,6 +51,8 @@ void FactorSet::release() {
     if (L) cudaFree(L);
     if (Ginv) cudaFree(Ginv);
     if (Ginv32) cudaFree(Ginv32);
+    if (W32) cudaFree(W32);
+    W32 = nullptr;
     if (W) cudaFree(W);
     W = nullptr;
     L = nullptr;
@@ -146,6 +148,19 @@ kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, i
             }
         }
     }
+    // large blocks of FP32/BF16 K++ with the W memo: one exchange per step (kpp_kw.cu)
+    bool v6 = !f64 && !cd && k == 1 && variant >= 3 && (grid <= 0 || grid == kw_grid(A0.cols)) &&
+              kw_fits(dtype, A0.rows, A0.cols, s, k, sm_count()) && nsys * kw_grid(A0.cols) <= sm_count();
+    for (int i = 0; v6 && i < nsys; ++i) {
+        const kpp_matrix &Ai = *sys[i].A;
+        if (!sys[i].F->W32 || ((uintptr_t)Ai.data & 15) || ((Ai.ld * (int64_t)dtype_size(dtype)) & 15)) v6 = false;
+    }
+    if (v6) v6 = kw_can_launch(dtype, s, A0.cols, nsys);
+    if (v6) {
+        v2 = v3 = v4 = false;
+        G = (int)kw_grid(A0.cols);
+        CW = 32;
+    }
     Common &cm = L.cm;
     cm = Common{};
     cm.rows = A0.rows;
@@ -165,7 +180,7 @@ kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, i
     cm.seed = seed;
     cm.timeout_ns = 2000000000ull;
     cm.t0_state = t0_state ? 1 : 0;
-    L.kind = v4 ? 4 : v3 ? 3 : v2 ? 2 : 1;
+    L.kind = v6 ? 6 : v4 ? 4 : v3 ? 3 : v2 ? 2 : 1;
     L.dtype = dtype;
     L.KP = KP;
     L.nsys = nsys;
@@ -219,7 +234,25 @@ kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, i
         a.sys_id = sys[i].sys_id;
         a.t0 = t0;
     }
-    if (L.kind == 4) {
+    if (L.kind == 6) {
+        const size_t sb = sysk_bytes();
+        L.mail_bytes = kw_mail_bytes(s, G);
+        h2.assign(sb * nsys, 0);
+        const uint32_t box = (uint32_t)std::min(s, 256);
+        for (int i = 0; i < nsys; ++i) {
+            alignas(128) unsigned char tma[128], tmw[128];
+            const kpp_matrix &Ai = *sys[i].A;
+            CUDA_OR(scr.alloc(&L.mails[i], L.mail_bytes), KPP_ERR_CUDA);
+            if (!make_tmap_2d(tma, Ai.data, dtype, Ai.cols, Ai.rows, Ai.ld, 32, box) ||
+                !make_tmap_2d(tmw, sys[i].F->W32, KPP_F32, Ai.cols, Ai.rows, Ai.cols, 32, box)) {
+                set_error("cuTensorMapEncodeTiled failed for system %d", i);
+                return KPP_ERR_CUDA;
+            }
+            const SysArgs &a = L.args[i];
+            sysk_fill(h2.data() + sb * i, tma, tmw, (const float *)a.b, (float *)a.x, a.sc, a.bar, a.err, a.rpart,
+                      L.mails[i], a.sys_id, a.t0);
+        }
+    } else if (L.kind == 4) {
         const size_t sb = sys4_bytes();
         h2.assign(sb * nsys, 0);
         for (int i = 0; i < nsys; ++i) {
@@ -300,11 +333,12 @@ kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st, cudaEv
                 }
             }
         }
-        if (L.kind == 3) CUDA_OR(cudaMemsetAsync(L.mails[i], 0, L.mail_bytes, st), KPP_ERR_CUDA);
+        if (L.kind == 3 || L.kind == 6) CUDA_OR(cudaMemsetAsync(L.mails[i], 0, L.mail_bytes, st), KPP_ERR_CUDA);
     }
     if (ev0) CUDA_OR(cudaEventRecord(ev0, st), KPP_ERR_CUDA);
     {
-        cudaError_t le = L.kind == 4   ? launch_stream(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
+        cudaError_t le = L.kind == 6   ? launch_kw(L.dtype, L.d_sys2, L.nsys, L.cm, st)
+                         : L.kind == 4 ? launch_stream(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
                          : L.kind == 3 ? launch_cd3(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
                          : L.kind == 2 ? launch_solve2(L.dtype, L.cd, L.d_sys2, L.nsys, L.cm, L.KP, st)
                                        : launch_solve(L.dtype, L.f64, L.cd, L.d_args, L.nsys, L.cm, L.KP, st);

@@ -464,6 +464,12 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
             set_error("block %d: Cholesky pivot not positive", hb);
         }
     }
+    if (rc == KPP_OK && mode == 0 && A.dtype != KPP_F64 && kw_fits(A.dtype, rows, A.cols, s, 1, sm_count())) {
+        // the large-block K++ kernel reads W_S = G^{-1} A_S instead of applying G^{-1} across the group
+        KPP_TRY(cudaMalloc(&F.W32, (size_t)rows * A.cols * sizeof(float)));
+        rc = build_w32(A, s, F.Ginv32, F.W32, st);
+        if (rc != KPP_OK) goto done;
+    }
     if (rc == KPP_OK && mode == 1 && A.dtype == KPP_F64) {
         KPP_TRY(cudaMalloc(&F.W, (size_t)rows * rows * sizeof(double)));
         dim3 grid((unsigned)nb, (unsigned)((rows + 63) / 64));

@@ -24,6 +24,7 @@ struct FactorSet {
     double *Ginv = nullptr;   // nb x s x s, FP64 (G_j)^{-1}
     float *Ginv32 = nullptr;  // nb x s x s, FP32 copy (FP32/BF16 storage only)
     double *W = nullptr;      // CD++ FP64 only: rows x cols, block j rows = G_j^{-1} A_{S_j} (row-major, ld cols)
+    float *W32 = nullptr;     // K++ with FP32/BF16 storage, large-block kernel only: G_j^{-1} A_{S_j} in FP32
     void release();
 };
 
@@ -44,6 +45,11 @@ int block_gram(const kpp_matrix &A, int s, double lam, double *G, int engine, cu
 kpp_status solve_systems_internal(int nsys, const kpp_matrix *A, const double *const *B, double *const *X, int k,
                                   kpp_partition_t P, const kpp_factors_t *F, const kpp_params *p, kpp_report *reps,
                                   cudaStream_t st, bool cd);
+
+// The FP32 memo W_j = G_j^{-1} A_{S_j} for every block (whole blocks; kpp_wmemo.cu).
+kpp_status build_w32(const kpp_matrix &A, int s, const float *Ginv32, float *W32, cudaStream_t st);
+// Whether the large-block K++ kernel (kpp_kw.cu) takes this shape.
+bool kw_fits(int dtype, int64_t rows, int64_t cols, int s, int k, int sms);
 
 // Number of SMs of the current device (cached).
 int sm_count();

@@ -71,6 +71,14 @@ cudaError_t launch_negate_copy(size_t n, const void *src, void *dst, bool f64, c
 
 // Small-block kernel (kpp_solve2.cu).
 bool solve2_eligible(const kpp_matrix &A, int s, int64_t CW, int KP, bool f64, bool cd, int G);
+// The large-block K++ kernel with the W memo (kpp_kw.cu): FP32 iterations, one right-hand side.
+int64_t kw_grid(int64_t cols);
+size_t kw_mail_bytes(int s, int G);
+size_t sysk_bytes();
+void sysk_fill(void *dst, const void *tmA, const void *tmW, const float *b, float *x, SolveScalars *sc, unsigned *bar,
+               int *err, double *rpart, void *mail, uint32_t sys_id, int64_t t0);
+cudaError_t launch_kw(int dtype, const void *d_sys, int nsys, const Common &cm, cudaStream_t st);
+bool kw_can_launch(int dtype, int s, int64_t cols, int nsys);
 bool make_tmap_2d(void *out, const void *base, int dtype, uint64_t cols, uint64_t rows, uint64_t ld_elems,
                   uint32_t box_cols, uint32_t box_rows, bool swizzle128 = false);
 size_t sys2_bytes();

@@ -411,6 +411,37 @@ def test_streaming_kernel_tracks_general_kernel_in_fp32(K):
         assert rel(out[3][i], out[1][i]) <= 2e-5
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_large_block_kernel_tracks_general_kernel_in_fp32(K, dtype):
+    """The large-block K++ kernel (memoised W = G^-1 A_S, one exchange per step over 8-CTA clusters)
+    against the general kernel on the same FP32 iteration: iterates agree to FP32 rounding after T steps,
+    and both refine to 1e-8 with the same solution."""
+    sy = W.kpp_mixed_lowrank(m=16384, n=512, s=128, n_out=16)
+    A = W.round_to_storage(sy.A, dtype)
+    b = A @ sy.x_star
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    m, n = A.shape
+    P = K.Partition(m, sy.s)
+    Ad = dev(A, tdt)
+    F = K.Factors(Ad, P, sy.lam, 0)
+    out = {}
+    for v in (1, 3):
+        K.set_kernel_variant(v)
+        x = dev(np.zeros(n))
+        K.kpp_solve(Ad, dev(b), x, P, F, K.params(lam=sy.lam, tol=0.0, max_iters=2 * 128 * 2 + 7, refine=0, seed=4),
+                    allow_no_conv=True)
+        out[v] = x.cpu().numpy()
+    K.set_kernel_variant(3)
+    # the memoised W = G^-1 A_S is rounded once where the general kernel rounds G^-1 r every step; with
+    # FP32 arithmetic (eps 6e-8) and block Grams of condition ~1e3 the iterates differ by O(1e-5)
+    assert rel(out[3], out[1]) <= 1e-4
+    x = dev(np.zeros(n))
+    rep = K.kpp_solve(Ad, dev(b), x, P, F, K.params(lam=sy.lam, tol=1e-8, refine=1, inner_tol=1e-3, seed=0))
+    assert rep.status == K.OK and rep.rel_res_true <= 1e-8
+    kappa = sy.spectrum.max() / sy.spectrum.min() * 2.0
+    assert rel(x.cpu().numpy(), sy.x_star) <= kappa * 2e-8
+
+
 @pytest.mark.parametrize("n,s", [(200, 16), (192, 32)])
 def test_batched_cdpp_panels_match_single_rhs_oracle(K, variant, n, s):
     """CD++ with right-hand-side panels (k = 3, two systems): every column against the oracle's
