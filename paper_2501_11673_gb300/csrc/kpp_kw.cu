@@ -82,25 +82,32 @@ __device__ __forceinline__ void kw_st_relaxed(unsigned long long *p, unsigned lo
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// 8 storage values of one tile row (16 bytes) as floats
+// Dot product of one 16-byte piece of a tile row (8 BF16 or 4 FP32 values) with x values in registers.
 template <typename TA> struct KwRow;
 template <> struct KwRow<__nv_bfloat16> {
     static constexpr int PER = 8;  // values per 16-byte load
-    __device__ static void load(const __nv_bfloat16 *p, float (&v)[8]) {
+    __device__ __forceinline__ static float dot(const __nv_bfloat16 *p, const float (&xv)[8]) {
         const uint4 q = *reinterpret_cast<const uint4 *>(p);
-        const unsigned w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            v[2 * i] = __uint_as_float(w[i] << 16);
-            v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
-        }
+        float acc = __uint_as_float(q.x << 16) * xv[0];
+        acc = fmaf(__uint_as_float(q.x & 0xffff0000u), xv[1], acc);
+        acc = fmaf(__uint_as_float(q.y << 16), xv[2], acc);
+        acc = fmaf(__uint_as_float(q.y & 0xffff0000u), xv[3], acc);
+        acc = fmaf(__uint_as_float(q.z << 16), xv[4], acc);
+        acc = fmaf(__uint_as_float(q.z & 0xffff0000u), xv[5], acc);
+        acc = fmaf(__uint_as_float(q.w << 16), xv[6], acc);
+        acc = fmaf(__uint_as_float(q.w & 0xffff0000u), xv[7], acc);
+        return acc;
     }
 };
 template <> struct KwRow<float> {
     static constexpr int PER = 4;
-    __device__ static void load(const float *p, float (&v)[8]) {
+    __device__ __forceinline__ static float dot(const float *p, const float (&xv)[8]) {
         const float4 q = *reinterpret_cast<const float4 *>(p);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        float acc = q.x * xv[0];
+        acc = fmaf(q.y, xv[1], acc);
+        acc = fmaf(q.z, xv[2], acc);
+        acc = fmaf(q.w, xv[3], acc);
+        return acc;
     }
 };
 
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
 #define KW_W(i) ((const float *)(sm + L.w[i]))
 #define KW_A(i) ((const TA *)(sm + L.a[i]))
     __shared__ float s_p[KW_SMAX];      // my partial of r (read by the cluster)
-    __shared__ float s_r[KW_SMAX];      // r of the step
+    __shared__ __align__(16) float s_r[KW_SMAX];  // r of the step (read as float4)
     __shared__ float s_rs[KW_SMAX / KW_CL];  // my slice of r (read by the cluster)
     __shared__ float s_mail[KW_MAILMAX];     // my slice from every cluster (cluster-major)
     __shared__ float s_red[NW][KW_CW];
@@ -245,16 +252,13 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
         auto partial = [&](int i) {
             const TA *tl = KW_A(i);
             const int rs = lane / CG, cgi = lane % CG;
-            float xv[PER];
+            float xv[8];
 #pragma unroll
-            for (int e = 0; e < PER; ++e) xv[e] = xc[cgi * PER + e];
+            for (int e = 0; e < 8; ++e) xv[e] = e < PER ? xc[cgi * PER + e] : 0.0f;
+#pragma unroll 4
             for (int r0 = warp * RPW; r0 < s; r0 += NW * RPW) {
                 const int a = r0 + rs;
-                float v[8];
-                KwRow<TA>::load(tl + (size_t)a * KW_CW + cgi * PER, v);
-                float acc = 0.0f;
-#pragma unroll
-                for (int e = 0; e < PER; ++e) acc = fmaf(v[e], xv[e], acc);
+                float acc = KwRow<TA>::dot(tl + (size_t)a * KW_CW + cgi * PER, xv);
 #pragma unroll
                 for (int o = 1; o < CG; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 if (cgi == 0) s_p[a] = acc;
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
             if (s_fail) break;  // uniform over the cluster (every CTA saw every flag)
 
             // the A buffer of step t is free: prefetch the A tile of step t + 2 into it
-            if (threadIdx.x == 0 && t + 2 < t_end) issueA(t + 2, bi);
+            if (threadIdx.x == NT - 32 && t + 2 < t_end) issueA(t + 2, bi);
 
             // |r|^2 (FP32 in a fixed order, accumulated in FP64)
             {
@@ -370,13 +374,29 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
             {
                 const float *wt = KW_W(bi);
                 float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-                const int rpw = s / NW;
+                const int rpw = s / NW;  // a multiple of 4
                 const int ra = warp * rpw;
-                for (int i = 0; i < rpw; i += 4) {
-                    a0 = fmaf(wt[(ra + i) * KW_CW + lane], s_r[ra + i], a0);
-                    a1 = fmaf(wt[(ra + i + 1) * KW_CW + lane], s_r[ra + i + 1], a1);
-                    a2 = fmaf(wt[(ra + i + 2) * KW_CW + lane], s_r[ra + i + 2], a2);
-                    a3 = fmaf(wt[(ra + i + 3) * KW_CW + lane], s_r[ra + i + 3], a3);
+                for (int i0 = 0; i0 < rpw; i0 += 16) {
+                    // 16 rows: r from shared memory as 4 float4 (broadcast), W column values
+                    float rr[16];
+                    const float4 *r4 = reinterpret_cast<const float4 *>(s_r + ra + i0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 v = r4[u];
+                        rr[4 * u] = v.x; rr[4 * u + 1] = v.y; rr[4 * u + 2] = v.z; rr[4 * u + 3] = v.w;
+                    }
+                    const int n16 = rpw - i0 < 16 ? rpw - i0 : 16;
+                    if (n16 == 16) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4) {
+                            a0 = fmaf(wt[(ra + i0 + i) * KW_CW + lane], rr[i], a0);
+                            a1 = fmaf(wt[(ra + i0 + i + 1) * KW_CW + lane], rr[i + 1], a1);
+                            a2 = fmaf(wt[(ra + i0 + i + 2) * KW_CW + lane], rr[i + 2], a2);
+                            a3 = fmaf(wt[(ra + i0 + i + 3) * KW_CW + lane], rr[i + 3], a3);
+                        }
+                    } else {
+                        for (int i = 0; i < n16; ++i) a0 = fmaf(wt[(ra + i0 + i) * KW_CW + lane], s_r[ra + i0 + i], a0);
+                    }
                 }
                 s_red[warp][lane] = (a0 + a1) + (a2 + a3);
             }
@@ -399,7 +419,7 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
             }
             __syncthreads();
             // the W buffer of step t is free: prefetch the W tile of step t + 2 into it
-            if (threadIdx.x == 0 && t + 2 < t_end) issueW(t + 2, bi);
+            if (threadIdx.x == NT - 32 && t + 2 < t_end) issueW(t + 2, bi);
 
             // ---- 3. my partial of r_{t+1} ----
             if (t + 1 < t_end) {
