@@ -46,7 +46,9 @@ SERVING_METRIC = "solves/s + p99 latency"
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the same
 # kernel build and workload (the summaries under profiles/ give the commands).  Absent: not captured.
-NCU_TRAFFIC_PER_LAUNCH = {}
+NCU_TRAFFIC_PER_LAUNCH = {
+    "cd4_kernel/cdpp4096": 7.113274e9 + 19.861504e6,  # profiles/cd4_kernel_cdpp4096.md
+}
 
 
 def _log(msg):
@@ -669,7 +671,7 @@ def make_workload(args):
     if args.workload in ("cdpp4096", "kpp2000"):
         return SingleFP64(args.workload)
     if args.workload == "mixed262144":
-        return MixedLS(args.storage, args.noisy)
+        return MixedLS(args.storage, args.noisy, m=args.mixed_rows)
     if args.workload == "batched64":
         return Batched()
     if args.workload == "serving":
@@ -738,6 +740,8 @@ def main():
                              "cdpp4096-bf16"])
     ap.add_argument("--storage", default="bf16", choices=["bf16", "f32"], help="mixed262144 storage type")
     ap.add_argument("--noisy", action="store_true", help="mixed262144: b = A x* + 1e-6 N(0,I)")
+    ap.add_argument("--mixed-rows", type=int, default=262144,
+                    help="mixed262144: rows of the system (a smaller one for profiler captures)")
     ap.add_argument("--requests", type=int, default=1024, help="serving: requests per step")
     ap.add_argument("--host-qr", action="store_true",
                     help="Haar factors by a host QR (ncu cannot load torch's device linear algebra)")
