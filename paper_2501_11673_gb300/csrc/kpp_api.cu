@@ -270,17 +270,22 @@ kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, i
         const size_t sb = sys3_bytes();
         L.mail_bytes = cd3_mail_bytes(s, KP, f64);
         h2.assign(sb * nsys, 0);
+        // one right-hand side with a memo (W in FP64, W32 for FP32/BF16 storage): the single-column kernel
+        bool c4 = k == 1 && KP == 1 && cd4_fits(s, CW, (int)tcs);
+        for (int i = 0; c4 && i < nsys; ++i) c4 = f64 ? sys[i].F->W != nullptr : sys[i].F->W32 != nullptr;
         for (int i = 0; i < nsys; ++i) {
             alignas(128) unsigned char tm[128];
-            const void *src = f64 ? (const void *)sys[i].F->W : sys[i].A->data;
-            const int64_t ld = f64 ? sys[i].A->cols : sys[i].A->ld;
+            const void *src = f64 ? (const void *)sys[i].F->W : (c4 ? (const void *)sys[i].F->W32 : sys[i].A->data);
+            const int tdt = f64 ? KPP_F64 : (c4 ? KPP_F32 : dtype);
+            const int64_t ld = (f64 || c4) ? sys[i].A->cols : sys[i].A->ld;
             CUDA_OR(scr.alloc(&L.mails[i], L.mail_bytes), KPP_ERR_CUDA);
-            if (!make_tmap_2d(tm, src, dtype, sys[i].A->cols, sys[i].A->rows, ld, (uint32_t)CW, (uint32_t)s)) {
+            if (!make_tmap_2d(tm, src, tdt, sys[i].A->cols, sys[i].A->rows, ld, (uint32_t)CW, (uint32_t)s)) {
                 set_error("cuTensorMapEncodeTiled failed for system %d", i);
                 return KPP_ERR_CUDA;
             }
             sys3_fill(h2.data() + sb * i, L.args[i], tm, L.mails[i]);
         }
+        if (c4) L.kind = 7;
     } else if (L.kind == 2) {
         const size_t sb = sys2_bytes();
         h2.assign(sb * nsys, 0);
@@ -333,11 +338,13 @@ kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st, cudaEv
                 }
             }
         }
-        if (L.kind == 3 || L.kind == 6) CUDA_OR(cudaMemsetAsync(L.mails[i], 0, L.mail_bytes, st), KPP_ERR_CUDA);
+        if (L.kind == 3 || L.kind == 6 || L.kind == 7)
+            CUDA_OR(cudaMemsetAsync(L.mails[i], 0, L.mail_bytes, st), KPP_ERR_CUDA);
     }
     if (ev0) CUDA_OR(cudaEventRecord(ev0, st), KPP_ERR_CUDA);
     {
-        cudaError_t le = L.kind == 6   ? launch_kw(L.dtype, L.d_sys2, L.nsys, L.cm, st)
+        cudaError_t le = L.kind == 7   ? launch_cd4(L.dtype, L.d_sys2, L.nsys, L.cm, st)
+                         : L.kind == 6 ? launch_kw(L.dtype, L.d_sys2, L.nsys, L.cm, st)
                          : L.kind == 4 ? launch_stream(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
                          : L.kind == 3 ? launch_cd3(L.dtype, L.d_sys2, L.nsys, L.cm, L.KP, st)
                          : L.kind == 2 ? launch_solve2(L.dtype, L.cd, L.d_sys2, L.nsys, L.cm, L.KP, st)

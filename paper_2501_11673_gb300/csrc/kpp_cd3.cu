@@ -531,12 +531,12 @@ struct Smem4 {
     int tile[CD4_NB], ginv[CD4_NB], total;
 };
 
-__host__ __device__ inline Smem4 smem4_layout(int s, int64_t CW) {
+__host__ __device__ inline Smem4 smem4_layout(int s, int64_t CW, int es) {
     auto al = [](int v) { return (v + 127) / 128 * 128; };
     Smem4 L;
     int o = 0;
-    const int tile = al((int)(s * CW * 8));
-    const int ginv = al((int)min64(CW + 2, s) * s * 8);
+    const int tile = al((int)(s * CW * es));
+    const int ginv = al((int)min64(CW + 4, s) * s * es);  // my rows of G^-1 (start rounded down by <= 3)
     for (int i = 0; i < CD4_NB; ++i) {
         L.tile[i] = o;
         o += tile;
@@ -553,7 +553,9 @@ __device__ __forceinline__ void named_barrier(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
+template <typename TA, typename TC>
 __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ systems, Common cm) {
+    constexpr int MW = MailWords<TC>::n;  // mailbox words per value
     const Sys3 &sys = systems[blockIdx.x / cm.G];
     const SysArgs sa = sys.a;
     const void *tmap = &sys.tmapT;
@@ -562,23 +564,23 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = cm.s, nb = cm.nb;
     const int64_t n = cm.rows;
-    const double *__restrict__ b = (const double *)sa.b;
-    double *__restrict__ x = (double *)sa.x;
-    double *__restrict__ Rx = (double *)sa.Rx;
-    const double *__restrict__ Ginv = (const double *)sa.Ginv;
+    const TC *__restrict__ b = (const TC *)sa.b;
+    TC *__restrict__ x = (TC *)sa.x;
+    TC *__restrict__ Rx = (TC *)sa.Rx;
+    const TC *__restrict__ Ginv = (const TC *)sa.Ginv;
     double *__restrict__ xpart = (double *)sa.part;  // G x 2: window-sum partials at checkpoints
 
     extern __shared__ __align__(128) unsigned char sm[];
-    const Smem4 L = smem4_layout(s, cm.CW);
+    const Smem4 L = smem4_layout(s, cm.CW, (int)sizeof(TC));
     unsigned char *const tile0 = sm + L.tile[0];
     const int tile_stride = L.tile[1] - L.tile[0];
     unsigned char *const ginv0 = sm + L.ginv[0];
     const int ginv_stride = L.ginv[1] - L.ginv[0];
-#define TILE4(bf) ((const double *)(tile0 + (bf) * tile_stride))
-#define GINV4(bf) ((const double *)(ginv0 + (bf) * ginv_stride))
-    __shared__ double s_r[2][CD4_S];
-    __shared__ double s_red[4][CD4_CW], s_yred[4][CD4_CW];
-    __shared__ double xc[CD4_CW], mc[CD4_CW], rxc[CD4_CW], rmc[CD4_CW];
+#define TILE4(bf) ((const TC *)(tile0 + (bf) * tile_stride))
+#define GINV4(bf) ((const TC *)(ginv0 + (bf) * ginv_stride))
+    __shared__ TC s_r[2][CD4_S];
+    __shared__ TC s_red[4][CD4_CW], s_yred[4][CD4_CW];
+    __shared__ TC xc[CD4_CW], mc[CD4_CW], rxc[CD4_CW], rmc[CD4_CW];
     __shared__ int s_jt[CD4_JT];
     __shared__ double s_epart[2][2];   // my partial window sums, by checkpoint-pair parity
     __shared__ double s_pend;          // |r|^2 over the rows I published last, not yet counted
@@ -587,7 +589,7 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
     __shared__ double s_part[NW];
     __shared__ int s_stop, s_need, s_fail, s_pending[CD4_NB], s_glo[CD4_NB];
     __shared__ unsigned s_phase[CD4_NB];
-    __shared__ double s_beta;
+    __shared__ TC s_beta;
 
     GroupSync gs{sa.bar, sa.err, 0u, (unsigned)cm.G, cm.timeout_ns};
     const int64_t c0 = min64((int64_t)g * cm.CW, n);
@@ -632,7 +634,8 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
     {
         // |b|^2 over the group (fixed order)
         double acc = 0.0;
-        for (int64_t i = (int64_t)g * NT + threadIdx.x; i < n; i += (int64_t)cm.G * NT) acc += b[i] * b[i];
+        for (int64_t i = (int64_t)g * NT + threadIdx.x; i < n; i += (int64_t)cm.G * NT)
+            acc += (double)b[i] * (double)b[i];
         __syncthreads();
         const double v = block_sum<NT>(acc, s_part);
         if (threadIdx.x == 0) sa.rpart[g] = v;
@@ -646,17 +649,17 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
         if (!group_barrier(gs)) goto drain;
     }
     if (cm.init_residual) {
-        if (!true_residual_phase<double, double, 1>(sa, cm, g, gs, st, s_part, Rx)) goto drain;
+        if (!true_residual_phase<TA, TC, 1>(sa, cm, g, gs, st, s_part, Rx)) goto drain;
     }
     for (int e = threadIdx.x; e < cw; e += NT) {
         xc[e] = __ldcg(x + c0 + e);
-        mc[e] = 0.0;
+        mc[e] = (TC)0;
         rxc[e] = __ldcg(Rx + c0 + e);
-        rmc[e] = 0.0;
+        rmc[e] = (TC)0;
     }
     if (threadIdx.x == 0) {
         const double rho = st[0].rho;
-        s_beta = (1.0 - rho) / (1.0 + rho);
+        s_beta = (TC)((1.0 - rho) / (1.0 + rho));
     }
     __syncthreads();
 
@@ -667,12 +670,20 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
             const int j = s_jt[tt % CD4_JT];
             const int64_t S0 = (int64_t)j * s;
             const int len = (int)min64(s, n - S0);
-            const unsigned abytes = (unsigned)(s * CWs * 8);
+            const unsigned abytes = (unsigned)(s * CWs * sizeof(TC));
             int glo = (int)max64(0, c0 - S0);
             int ghi = (int)min64(len, c1 - S0);
             if (ghi < glo) ghi = glo;
-            if (len & 1) glo &= ~1;  // 16-byte aligned source row offset
-            const unsigned gbytes = (unsigned)(((ghi - glo) * len * 8 + 15) / 16 * 16);
+            {
+                // 16-byte aligned source: glo * len a multiple of ea = 16 / sizeof(TC) elements, so glo
+                // is rounded down to a multiple of ea / gcd(len, ea) (at most 3 rows below my first)
+                constexpr int ea = 16 / (int)sizeof(TC);
+                int gc = ea;
+                while (len % gc) gc >>= 1;
+                const int step = ea / gc;
+                glo = glo / step * step;
+            }
+            const unsigned gbytes = (unsigned)(((ghi - glo) * len * (int)sizeof(TC) + 15) / 16 * 16);
             mbar_arrive_expect_tx(&mbar[bf], abytes + gbytes);
             tma_load_2d((void *)TILE4(bf), tmap, (int)c0, (int)S0, &mbar[bf]);
             if (gbytes) bulk_load((void *)GINV4(bf), Ginv + (size_t)j * s * s + (size_t)glo * len, gbytes, &mbar[bf]);
@@ -680,19 +691,19 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
             s_pending[bf] = 1;
         };
         // warp 0: publish my rows of r_tt (values in lanes) and note their |.|^2
-        auto publish_lanes = [&](int64_t tt, double v_lane) {
+        auto publish_lanes = [&](int64_t tt, TC v_lane) {
             const int j = s_jt[tt % CD4_JT];
             const int64_t S0 = (int64_t)j * s;
             const int len = (int)min64(s, n - S0);
             const int64_t col = c0 + lane;
             const bool mine = lane < cw && col >= S0 && col < S0 + len;
-            unsigned long long *slot = mail + (size_t)(tt % CD4_RING) * s * 2;
-            if (mine) mail_put(slot + (size_t)(col - S0) * 2, v_lane, (unsigned)(tt + 1));
-            double q = mine ? v_lane * v_lane : 0.0;
+            unsigned long long *slot = mail + (size_t)(tt % CD4_RING) * s * MW;
+            if (mine) mail_put(slot + (size_t)(col - S0) * MW, v_lane, (unsigned)(tt + 1));
+            TC q = mine ? v_lane * v_lane : (TC)0;
             if (__any_sync(0xffffffffu, mine)) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-                if (lane == 0) s_pend = q;
+                if (lane == 0) s_pend = (double)q;
             } else if (lane == 0) {
                 s_pend = 0.0;
             }
@@ -702,7 +713,7 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
             issue(t, (int)(t % CD4_NB));
             if (t + 1 < t_end) issue(t + 1, (int)((t + 1) % CD4_NB));
         }
-        if (warp == 0 && t < t_end) publish_lanes(t, lane < cw ? rxc[lane] : 0.0);
+        if (warp == 0 && t < t_end) publish_lanes(t, lane < cw ? rxc[lane] : (TC)0);
         __syncthreads();
 
         while (t < t_end) {
@@ -719,23 +730,23 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                 s_pend = 0.0;
             }
             if (threadIdx.x < len) {
-                const unsigned long long *slot = mail + (size_t)(t % CD4_RING) * s * 2;
+                const unsigned long long *slot = mail + (size_t)(t % CD4_RING) * s * MW;
                 const unsigned tag = (unsigned)(t + 1);
-                double v;
-                if (!mail_get(slot + (size_t)threadIdx.x * 2, tag, v)) {
+                TC v;
+                if (!mail_get(slot + (size_t)threadIdx.x * MW, tag, v)) {
                     const uint64_t tq = globaltimer_ns();
                     unsigned polls = 0;
-                    while (!mail_get(slot + (size_t)threadIdx.x * 2, tag, v)) {
+                    while (!mail_get(slot + (size_t)threadIdx.x * MW, tag, v)) {
                         if ((++polls & 63u) == 0u) {
                             if (globaltimer_ns() - tq > cm.timeout_ns) {
                                 s_fail = 1;
                                 group_fail(gs, KPP_ERR_TIMEOUT);
-                                v = 0.0;
+                                v = (TC)0;
                                 break;
                             }
                             if (*(volatile int *)gs.err != 0) {
                                 s_fail = 1;
-                                v = 0.0;
+                                v = (TC)0;
                                 break;
                             }
                         }
@@ -743,7 +754,7 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                 }
                 s_r[rb][threadIdx.x] = v;
             } else if (threadIdx.x < CD4_S) {
-                s_r[rb][threadIdx.x] = 0.0;
+                s_r[rb][threadIdx.x] = (TC)0;
             }
             if (threadIdx.x == 64) {
                 if (!mbar_wait_bounded(&mbar[bf], s_phase[bf], cm.timeout_ns)) {
@@ -758,30 +769,30 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
             if (s_fail) break;
 
             const int64_t olo = max64(c0, S0), ohi = min64(c1, S0 + len);  // my columns inside S_t
-            const double *rv = s_r[rb];
+            const TC *rv = s_r[rb];
             if (warp < 4) {
                 // u partial: rows [16 warp, 16 warp + 16) of the W tile, lane = column, two chains
-                const double *tl = TILE4(bf);
-                double acc0 = 0.0, acc1 = 0.0;
+                const TC *tl = TILE4(bf);
+                TC acc0 = (TC)0, acc1 = (TC)0;
                 if (lane < cw) {
                     const int a0 = warp * 16, a1 = min(len, a0 + 16);
                     int a = a0;
                     for (; a + 1 < a1; a += 2) {
-                        acc0 = fma(tl[a * CWs + lane], rv[a], acc0);
-                        acc1 = fma(tl[(a + 1) * CWs + lane], rv[a + 1], acc1);
+                        acc0 = tfma<TC>(tl[a * CWs + lane], rv[a], acc0);
+                        acc1 = tfma<TC>(tl[(a + 1) * CWs + lane], rv[a + 1], acc1);
                     }
-                    if (a < a1) acc0 = fma(tl[a * CWs + lane], rv[a], acc0);
+                    if (a < a1) acc0 = tfma<TC>(tl[a * CWs + lane], rv[a], acc0);
                 }
                 s_red[warp][lane] = acc0 + acc1;
                 named_barrier(1, 128);
                 if (warp == 0) {
                     // u, then R_m and R_x on my columns; hand r_{t+1} over at once
-                    double rx = 0.0;
+                    TC rx = (TC)0;
                     if (lane < cw) {
-                        const double u = (s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane]);
-                        const double rm = s_beta * (rmc[lane] - u);
+                        const TC u = (s_red[0][lane] + s_red[1][lane]) + (s_red[2][lane] + s_red[3][lane]);
+                        const TC rm = s_beta * (rmc[lane] - u);
                         rmc[lane] = rm;
-                        rx = rxc[lane] - u + cm.eta * rm;
+                        rx = rxc[lane] - u + (TC)cm.eta * rm;
                         rxc[lane] = rx;
                     }
                     if (t + 1 < t_end) publish_lanes(t + 1, rx);
@@ -804,15 +815,15 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                     // y on my rows of S_t: lane = row (olo - S0 + lane), block index split over warps 4-7
                     const int rr = (int)(olo - S0) + lane;  // row of G^{-1} in the block
                     const int glo = s_glo[bf];
-                    double acc = 0.0;
+                    TC acc = (TC)0;
                     if (lane < (int)(ohi - olo)) {
-                        const double *grow = GINV4(bf) + (size_t)(rr - glo) * len;
+                        const TC *grow = GINV4(bf) + (size_t)(rr - glo) * len;
                         const int d0 = q * len / 4, d1 = (q + 1) * len / 4;
                         const int span = d1 - d0;
                         // rotate the start so that lanes (stride len) hit different banks
                         for (int i = 0; i < span; ++i) {
                             int d = d0 + ((i + lane) % span);
-                            acc = fma(grow[d], rv[d], acc);
+                            acc = tfma<TC>(grow[d], rv[d], acc);
                         }
                     }
                     s_yred[q][lane] = acc;
@@ -822,14 +833,14 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                     // x and m on my columns: w = y on the columns inside S_t
                     if (lane < cw) {
                         const int64_t col = c0 + lane;
-                        double wv = 0.0;
+                        TC wv = (TC)0;
                         if (col >= olo && col < ohi) {
                             const int l = (int)(col - olo);
                             wv = (s_yred[0][l] + s_yred[1][l]) + (s_yred[2][l] + s_yred[3][l]);
                         }
-                        const double mm = s_beta * (mc[lane] - wv);
+                        const TC mm = s_beta * (mc[lane] - wv);
                         mc[lane] = mm;
-                        xc[lane] = xc[lane] - wv + cm.eta * mm;
+                        xc[lane] = xc[lane] - wv + (TC)cm.eta * mm;
                     }
                 }
             }
@@ -869,17 +880,17 @@ __global__ void __launch_bounds__(NT, 1) cd4_kernel(const Sys3 *__restrict__ sys
                 __syncthreads();
                 if (s_need) {
                     // true residual; it also replaces R_x (my rows are re-read below)
-                    if (!true_residual_phase<double, double, 1>(sa, cm, g, gs, st, s_part, Rx)) break;
+                    if (!true_residual_phase<TA, TC, 1>(sa, cm, g, gs, st, s_part, Rx)) break;
                     for (int e = threadIdx.x; e < cw; e += NT) rxc[e] = __ldcg(Rx + c0 + e);
                     __syncthreads();
                     // republish r_t from the new R_x (its |.|^2 replaces the pending one)
-                    if (warp == 0 && t < t_end) publish_lanes(t, lane < cw ? rxc[lane] : 0.0);
+                    if (warp == 0 && t < t_end) publish_lanes(t, lane < cw ? rxc[lane] : (TC)0);
                     if (!group_barrier(gs)) break;
                 }
                 if (threadIdx.x == 0) {
                     if (st[0].active) checkpoint_column(st[0], cm, zeta);
                     const double rho = st[0].rho;
-                    s_beta = (1.0 - rho) / (1.0 + rho);
+                    s_beta = (TC)((1.0 - rho) / (1.0 + rho));
                     s_stop = !st[0].active;
                 }
                 __syncthreads();
@@ -926,22 +937,34 @@ size_t cd3_mail_bytes(int s, int KP, bool f64) {
     return (size_t)ring * s * KP * (f64 ? 2 : 1) * 8;
 }
 
-// s >= 2: the checkpoint partials (G x 2 doubles) live in the G x s partial buffer
-static bool cd4_fits(int s, int64_t CW) { return s >= 2 && s <= CD4_S && CW >= 2 && CW <= CD4_CW && CW % 2 == 0; }
+// s * es >= 16: the checkpoint partials (G x 2 doubles) live in the G x s partial buffer; the tile row of
+// CW values of es bytes must be a multiple of 16 bytes (TMA)
+bool cd4_fits(int s, int64_t CW, int es) {
+    return s * es >= 16 && s <= CD4_S && CW >= 2 && CW <= CD4_CW && (CW * es) % 16 == 0;
+}
 
-static cudaError_t launch4(const void *d_sys, int nsys, const Common &cm, cudaStream_t st) {
-    const size_t smem = (size_t)smem4_layout(cm.s, cm.CW).total;
-    cudaError_t e = cudaFuncSetAttribute(cd4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename TA, typename TC>
+static cudaError_t launch4_t(const void *d_sys, int nsys, const Common &cm, cudaStream_t st) {
+    auto kern = cd4_kernel<TA, TC>;
+    const size_t smem = (size_t)smem4_layout(cm.s, cm.CW, (int)sizeof(TC)).total;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cd4_kernel, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     if (e != cudaSuccess) return e;
     if ((int64_t)per_sm * sm_count() < (int64_t)nsys * cm.G) return cudaErrorCooperativeLaunchTooLarge;
     Common c = cm;
     const Sys3 *p = (const Sys3 *)d_sys;
     void *args[] = {(void *)&p, (void *)&c};
     note_launch();
-    return cudaLaunchCooperativeKernel((const void *)cd4_kernel, dim3((unsigned)(nsys * cm.G)), dim3(NT), args, smem, st);
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)(nsys * cm.G)), dim3(NT), args, smem, st);
+}
+
+// The single-column dataflow kernel: FP64 on W, or FP32 on the FP32 memo W32 for FP32/BF16 storage.
+cudaError_t launch_cd4(int dtype, const void *d_sys, int nsys, const Common &cm, cudaStream_t st) {
+    if (dtype == KPP_F64) return launch4_t<double, double>(d_sys, nsys, cm, st);
+    if (dtype == KPP_F32) return launch4_t<float, float>(d_sys, nsys, cm, st);
+    return launch4_t<__nv_bfloat16, float>(d_sys, nsys, cm, st);
 }
 
 size_t sys3_bytes() { return sizeof(Sys3); }
@@ -981,7 +1004,6 @@ static cudaError_t launch3_kp(const void *d_sys, int nsys, const Common &cm, int
 }
 
 cudaError_t launch_cd3(int dtype, const void *d_sys, int nsys, const Common &cm, int KP, cudaStream_t st) {
-    if (dtype == KPP_F64 && KP == 1 && cm.k == 1 && cd4_fits(cm.s, cm.CW)) return launch4(d_sys, nsys, cm, st);
     if (dtype == KPP_F64) return launch3_kp<double, double, true>(d_sys, nsys, cm, KP, st);
     if (dtype == KPP_F32) return launch3_kp<float, float, false>(d_sys, nsys, cm, KP, st);
     return launch3_kp<__nv_bfloat16, float, false>(d_sys, nsys, cm, KP, st);

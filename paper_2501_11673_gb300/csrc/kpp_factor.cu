@@ -470,6 +470,12 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
         rc = build_w32(A, s, F.Ginv32, F.W32, st);
         if (rc != KPP_OK) goto done;
     }
+    if (rc == KPP_OK && mode == 1 && A.dtype != KPP_F64 && rows % s == 0 && s <= 64) {
+        // CD++ inner FP32 iterations on one right-hand side read W_S = G^{-1} A_S (FP32), as FP64 reads W
+        KPP_TRY(cudaMalloc(&F.W32, (size_t)rows * A.cols * sizeof(float)));
+        rc = build_w32(A, s, F.Ginv32, F.W32, st);
+        if (rc != KPP_OK) goto done;
+    }
     if (rc == KPP_OK && mode == 1 && A.dtype == KPP_F64) {
         KPP_TRY(cudaMalloc(&F.W, (size_t)rows * rows * sizeof(double)));
         dim3 grid((unsigned)nb, (unsigned)((rows + 63) / 64));

@@ -82,7 +82,8 @@ struct SysInput {
 // enqueue_persistent() then issues only memsets, small kernels and the cooperative launch (no
 // allocation, no host synchronisation, no pageable copy), so it can run inside graph capture.
 struct PersistentLaunch {
-    int kind = 0;  // 1 general, 2 small-block, 3 dataflow CD++, 4 streaming, 6 large-block K++ with W
+    int kind = 0;  // 1 general, 2 small-block, 3 dataflow CD++, 4 streaming, 6 large-block K++ with W,
+                   // 7 single-column dataflow CD++ over a memo
     int dtype = 0, KP = 1, nsys = 0, k = 1;
     bool cd = false, f64 = false, init_residual = true;
     int64_t t0 = 0;

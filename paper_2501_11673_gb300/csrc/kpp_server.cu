@@ -127,6 +127,11 @@ size_t factor_bytes(const Matrix &m) {
     const size_t nb = (size_t)((m.A.rows + m.s - 1) / m.s);
     size_t b = nb * (size_t)m.s * m.s * (8 + 8 + 4);  // L, G^{-1} (FP64 or FP32) and the build's workspace
     if (m.mode == 1 && m.A.dtype == KPP_F64) b += (size_t)m.A.rows * m.A.cols * 8;  // W
+    // W32 = G^{-1} A_S in FP32 (CD++ one-column kernel; large-block K++ kernel)
+    if (m.A.dtype != KPP_F64 &&
+        ((m.mode == 1 && m.A.rows % m.s == 0 && m.s <= 64) ||
+         (m.mode == 0 && kpp::kw_fits(m.A.dtype, m.A.rows, m.A.cols, m.s, 1, kpp::sm_count()))))
+        b += (size_t)m.A.rows * m.A.cols * 4;
     return b;
 }
 

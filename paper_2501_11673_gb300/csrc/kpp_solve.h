@@ -79,6 +79,9 @@ void sysk_fill(void *dst, const void *tmA, const void *tmW, const float *b, floa
                int *err, double *rpart, void *mail, uint32_t sys_id, int64_t t0);
 cudaError_t launch_kw(int dtype, const void *d_sys, int nsys, const Common &cm, cudaStream_t st);
 bool kw_can_launch(int dtype, int s, int64_t cols, int nsys);
+// The single-column dataflow CD++ kernel (kpp_cd3.cu): FP64 over the memo W, FP32 over W32.
+bool cd4_fits(int s, int64_t CW, int es);
+cudaError_t launch_cd4(int dtype, const void *d_sys, int nsys, const Common &cm, cudaStream_t st);
 bool make_tmap_2d(void *out, const void *base, int dtype, uint64_t cols, uint64_t rows, uint64_t ld_elems,
                   uint32_t box_cols, uint32_t box_rows, bool swizzle128 = false);
 size_t sys2_bytes();

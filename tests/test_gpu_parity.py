@@ -225,6 +225,34 @@ def test_mixed_precision_refinement_reaches_1e8(K, variant, dtype):
     assert rel(x.cpu().numpy(), xo) <= kappa * 2e-8
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_single_column_cdpp_kernel_fp32_tracks_general_kernel(K, dtype):
+    """CD++ inner FP32 iterations on one column through the single-column kernel (FP32 memo
+    W32 = G^-1 A_S) against the general kernel: the same iteration to FP32 rounding after T steps;
+    then refinement to 1e-8 reaches the solution of the stored system."""
+    A, b, _ = W.spd(512, 8, 1e2, 1e3, 1.0, 10.0, seed_A=30, seed_b=31)
+    Ar = W.round_to_storage(A, dtype)
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    P = K.Partition(512, 64)
+    Ad = dev(Ar, tdt)
+    F = K.Factors(Ad, P, 1e-4, 1)
+    out = {}
+    for v in (1, 3):
+        K.set_kernel_variant(v)
+        x = dev(np.zeros(512))
+        K.cdpp_solve(Ad, dev(b), x, P, F, K.params(lam=1e-4, tol=0.0, max_iters=2 * 8 * 20 + 3, refine=0, seed=5),
+                     allow_no_conv=True)
+        out[v] = x.cpu().numpy()
+    K.set_kernel_variant(3)
+    # W = G^-1 A_S rounded once to FP32 against G^-1 applied to r each step: O(eps32 * kappa) apart
+    assert rel(out[3], out[1]) <= 1e-4
+    x = dev(np.zeros(512))
+    rep = K.cdpp_solve(Ad, dev(b), x, P, F, K.params(lam=1e-4, tol=1e-8, refine=1, inner_tol=1e-3, seed=2))
+    assert rep.status == K.OK and rep.rel_res_true <= 1e-8
+    xo = np.linalg.solve(Ar, b)
+    assert rel(x.cpu().numpy(), xo) <= 1e3 * 2e-8
+
+
 def test_mixed_cdpp_refinement(K, variant):
     A, b, _ = W.spd(512, 8, 1e2, 1e3, 1.0, 10.0, seed_A=20, seed_b=21)
     A32 = W.round_to_storage(A, "f32")
