@@ -438,8 +438,9 @@ class Batched(Workload):
 
     kernel = "stream_kernel"
 
-    def __init__(self, nsys=64, m=2048, n=65536, k=8, s=256):
+    def __init__(self, nsys=64, m=2048, n=65536, k=8, s=256, grid=None):
         self.nsys, self.m, self.n, self.k, self.s = nsys, m, n, k, s
+        self.grid = grid  # CTAs per system; None: the launch autotuner
         self.tol = 1e-8
         self.dtype = "f32"
         self.desc = (f"{nsys} under-determined min-norm K++ systems, each {m}x{n} FP32 i.i.d. N(0,1) with 20 seeded "
@@ -459,7 +460,7 @@ class Batched(Workload):
         self.X = [torch.zeros(self.n, self.k, dtype=torch.float64, device="cuda") for _ in range(self.nsys)]
         self.P = kpp.Partition(self.m, self.s)
         self.prm = kpp.params(lam=self.lam, tol=self.tol, refine=1, inner_tol=1e-3, seed=0, sys_id=rank * 4096,
-                              grid=kpp.GRID_TUNE)
+                              grid=kpp.GRID_TUNE if self.grid is None else self.grid)
         self.cap_stream = torch.cuda.Stream()
 
     def system_seed(self, rank, i):
@@ -673,7 +674,7 @@ def make_workload(args):
     if args.workload == "mixed262144":
         return MixedLS(args.storage, args.noisy, m=args.mixed_rows)
     if args.workload == "batched64":
-        return Batched()
+        return Batched(nsys=args.systems, grid=args.batched_grid)
     if args.workload == "serving":
         return Serving(n_req=args.requests)
     if args.workload in ("cdpp4096-f32", "cdpp4096-bf16"):
@@ -743,6 +744,8 @@ def main():
     ap.add_argument("--mixed-rows", type=int, default=262144,
                     help="mixed262144: rows of the system (a smaller one for profiler captures)")
     ap.add_argument("--requests", type=int, default=1024, help="serving: requests per step")
+    ap.add_argument("--systems", type=int, default=64, help="batched64: systems (fewer for profiler captures)")
+    ap.add_argument("--batched-grid", type=int, default=None, help="batched64: CTAs per system (default: autotuned)")
     ap.add_argument("--host-qr", action="store_true",
                     help="Haar factors by a host QR (ncu cannot load torch's device linear algebra)")
     ap.add_argument("--ref-iters", type=int, default=4096)

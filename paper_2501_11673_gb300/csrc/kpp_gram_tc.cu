@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
     constexpr int STAGES = SPLIT ? 2 : TC_STAGES;
     constexpr int SBYTES = SPLIT ? 2 * TC_STAGE_BYTES : TC_STAGE_BYTES;  // split: hi tiles, then lo tiles
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // keeps the state space
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], split_bar[TC_STAGES], done_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_err;

@@ -28,7 +28,7 @@
 
 namespace kpp {
 
-constexpr int ST_STAGES = 4;
+constexpr int ST_STAGES = 5;
 constexpr int ST_ROWB = 128;  // bytes of one tile row
 
 struct alignas(128) Sys4 {
@@ -76,7 +76,9 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
     float *__restrict__ M = sys.M;
 
     extern __shared__ __align__(1024) unsigned char st_raw[];
-    unsigned char *sm = (unsigned char *)(((uintptr_t)st_raw + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned by an offset from the shared array itself (an integer round trip would lose the
+    // shared state space, and every tile read would become a generic load)
+    unsigned char *sm = st_raw + ((1024u - (smem_u32(st_raw) & 1023u)) & 1023u);
     const int SB = st_stage_bytes(s, KP);
     const int AB = (s * ST_ROWB + 1023) / 1024 * 1024;
     const int VB = (64 * KP * 4 + 127) / 128 * 128;
@@ -184,8 +186,9 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
             s_ppar[stg] = (unsigned)((q / ST_STAGES) & 1);
         };
         // wait for tile q; then refill the stage of tile q-2 (every thread is done with it) with tile
-        // q-2+ST, after the bulk stores older than the most recent group have completed (that covers
-        // the stage's own pass-C store and the last store of any X / M slice the refill reads)
+        // q-2+ST, after the bulk stores older than the most recent group have completed.  That covers the
+        // stage's own pass-C store (tile q-2) and, when the chunk has at least ST tiles, the last store
+        // of any X / M slice the refill reads (tile q-2+ST-nt or older); shorter chunks wait for all.
         auto wait = [&](int64_t q) -> bool {
             const int stg = (int)(q % ST_STAGES);
             if (tid == 0) {
@@ -197,7 +200,8 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
             }
             __syncthreads();
             if (tid == 0 && q >= 2) {
-                asm volatile("cp.async.bulk.wait_group 1;" ::: "memory");
+                if (nt >= ST_STAGES) asm volatile("cp.async.bulk.wait_group 1;" ::: "memory");
+                else asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
                 issue(q - 2 + ST_STAGES);
             }
             return !s_fail;
