@@ -674,7 +674,7 @@ def make_workload(args):
     if args.workload == "mixed262144":
         return MixedLS(args.storage, args.noisy, m=args.mixed_rows)
     if args.workload == "batched64":
-        return Batched(nsys=args.systems, grid=args.batched_grid)
+        return Batched(nsys=getattr(args, "systems", 64), grid=getattr(args, "batched_grid", None))
     if args.workload == "serving":
         return Serving(n_req=args.requests)
     if args.workload in ("cdpp4096-f32", "cdpp4096-bf16"):

@@ -133,19 +133,21 @@ kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, i
         }
         if (A0.cols % TK) v4 = false;
         const int per_sm = v4 ? stream_per_sm(dtype, s, KP) : 0;
-        int G4 = per_sm > 0 ? std::max(1, per_sm * sm_count() / nsys) : 0;
-        if (grid > 0) G4 = grid;
-        if (G4 < 1) v4 = false;
+        // the column tiles are split evenly over the CTAs of a system (chunks differ by at most one tile)
+        // and every chunk keeps stream_min_tiles() tiles: the kernel's prefetch runs that far ahead of
+        // the X / M stores it depends on
+        const int64_t T4 = A0.cols / TK, Gmax = T4 / stream_min_tiles();
+        int64_t G4 = per_sm > 0 ? std::max(1, per_sm * sm_count() / nsys) : 0;
+        if (grid > 0) {
+            G4 = grid;
+            if (G4 > Gmax) v4 = false;
+        } else {
+            G4 = std::min(G4, Gmax);
+        }
+        if (G4 < 1 || G4 * nsys > (int64_t)per_sm * sm_count()) v4 = false;
         if (v4) {
-            int64_t CW4 = (A0.cols + G4 - 1) / G4;
-            CW4 = (CW4 + TK - 1) / TK * TK;
-            const int G4b = (int)((A0.cols + CW4 - 1) / CW4);
-            if (CW4 / TK < 6 || (int64_t)G4b * nsys > (int64_t)per_sm * sm_count()) {
-                v4 = false;
-            } else {
-                G = G4b;
-                CW = CW4;
-            }
+            G = (int)G4;
+            CW = (T4 + G4 - 1) / G4 * TK;  // the widest chunk
         }
     }
     // large blocks of FP32/BF16 K++ with the W memo: one exchange per step (kpp_kw.cu)

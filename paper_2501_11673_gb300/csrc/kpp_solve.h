@@ -102,6 +102,7 @@ void sys4_fill(void *dst, const void *tmap, const float *b, float *X, float *M, 
 int stream_tk(int dtype);
 size_t stream_smem_bytes(int s, int KP);
 int stream_per_sm(int dtype, int s, int KP);
+int stream_min_tiles();  // fewest column tiles of one CTA's chunk
 cudaError_t launch_stream(int dtype, const void *d_sys, int nsys, const Common &cm, int KP, cudaStream_t st);
 
 }  // namespace kpp

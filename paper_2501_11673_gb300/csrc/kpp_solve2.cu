@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
         for (int c = 0; c < cm.k; ++c) any |= sa.sc[c].active;
         if (!any) t_end = t;
     }
+    int ph_c = (int)(t % (2 * (int64_t)zeta));  // t mod 2 zeta, advanced with t (no division per step)
     TC *const Rx0 = (TC *)sa.Rx;  // two published copies of R_x: Rx0 + parity * rows * k
 #define RXP(par) (Rx0 + (size_t)(par) * rows * k)
 
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             }
             // buffer bf is free: prefetch step t+2 into it
             if (threadIdx.x == 0 && t + 2 < t_end) issue(t + 2, bf);
-            const int64_t ph = t % (2 * (int64_t)zeta);
+            const int ph = ph_c;
             const bool ckpt = (ph == 2 * zeta - 1);
             if (CD) {
                 // publish my chunk of R_x for the next step; x too at checkpoints
@@ -475,6 +476,7 @@ __global__ void __launch_bounds__(NT, 1) solve2_kernel(const Sys2 *__restrict__ 
             }
             __syncthreads();
             t += 1;
+            if (++ph_c == 2 * zeta) ph_c = 0;
             if (!CD) {
                 // next block's partial residual from the updated chunk
                 if (t < t_end) {

@@ -6,8 +6,8 @@
 // every right-hand-side column with its own rho, residual estimate and stop test, all columns of a
 // system sharing its block sequence.  For wide blocks (config of 256 rows x 65536 columns) a step is two
 // streaming passes over A_S: the partial residual (P) and the back-projection (C).  The block does not
-// fit on chip, so each CTA owns a column chunk of one system and streams its tiles:
-//   * one TMA tile stream per CTA through a 3-stage ring: A tile (s rows x 128 bytes, 128-byte swizzle:
+// fit on chip, so each CTA owns an even share of the column tiles of one system and streams them:
+//   * one TMA tile stream per CTA through a 5-stage ring: A tile (s rows x 128 bytes, 128-byte swizzle:
 //     thread-per-row 16-byte reads and lane-per-column reads are both conflict-free) plus bulk copies of
 //     the X (and, in pass C, M) panel slices of the same columns;
 //   * the stream never stops between passes or steps: the tiles of the next pass are already in flight
@@ -15,7 +15,8 @@
 //   * Y = G^{-1} R is applied redundantly in every CTA of the system (G^{-1} symmetric: read by
 //     columns, coalesced), so the only exchange is the partial residual.
 // The X / M updates are generic stores that a later bulk copy of the same system reads: a proxy fence
-// orders them.  Every wait is bounded.
+// orders them.  A chunk holds at least ST_MIN_TILES tiles, so a refill never reads a slice whose store
+// is still the most recent one.  Every wait is bounded.
 #include <cuda.h>
 
 #include <cmath>
@@ -29,7 +30,9 @@
 namespace kpp {
 
 constexpr int ST_STAGES = 5;
-constexpr int ST_ROWB = 128;  // bytes of one tile row
+constexpr int ST_MIN_TILES = 8;  // fewest tiles of a chunk (see wait())
+static_assert(ST_MIN_TILES > ST_STAGES && 2 * ST_MIN_TILES >= ST_STAGES, "refill distance");
+constexpr int ST_ROWB = 128;     // bytes of one tile row
 
 struct alignas(128) Sys4 {
     CUtensorMap tmapA;      // A: cols x rows, box {128 B of columns, s rows}, 128-byte swizzle
@@ -95,9 +98,12 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
     __shared__ unsigned s_ppar[ST_STAGES];  // parity of the phase a pending stage completes
 
     GroupSync gs{sys.bar, sys.err, 0u, (unsigned)cm.G, cm.timeout_ns};
-    const int64_t c0 = min64((int64_t)g * cm.CW, cols);
-    const int64_t c1 = min64(c0 + cm.CW, cols);
-    const int nt = (int)((c1 - c0) / TK);  // whole tiles (cols and CW are multiples of TK)
+    // tiles [g T / G, (g + 1) T / G) of the T = cols / TK column tiles (cols is a multiple of TK); the
+    // host keeps every chunk at ST_MIN_TILES tiles or more
+    const int64_t T = cols / TK;
+    const int64_t c0 = (int64_t)g * T / cm.G * TK;
+    const int64_t c1 = (int64_t)(g + 1) * T / cm.G * TK;
+    const int nt = (int)((c1 - c0) / TK);
     const int zeta = nb;
     const int64_t t0 = cm.t0_state ? sys.sc[0].t : sys.t0;
     int64_t t_end = cm.t0_state ? t0 + cm.max_iters : cm.max_iters;
@@ -155,61 +161,75 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
     }
 
     {
-        // tile q of the stream: step t0 + q / (2 nt), pass (q / nt) % 2 (0: P, 1: C), column tile q % nt
-        // cached block draw (thread 0 only): the stream asks for the same step many times in a row
-        int64_t cache_t = -1;
-        int cache_j = 0;
-        auto block_of = [&](int64_t t) -> int {
-            if (t != cache_t) {
-                cache_t = t;
-                cache_j = draw_block(cm.seed, t, sys.sys_id, nb);
-            }
-            return cache_j;
-        };
-        // tile q: A tile by TMA, the X slice (and in pass C the M slice) by bulk copy, one mbarrier.  The
-        // X / M slices were last written by bulk stores of this CTA, waited for before every refill.
-        auto issue = [&](int64_t q) {
-            const int64_t t = t0 + q / (2 * nt);
-            if (t >= t_end) return;
-            const int pass = (int)((q / nt) & 1);
-            const int jt = (int)(q % nt);
-            const int stg = (int)(q % ST_STAGES);
-            const int j = block_of(t);
-            const int64_t col = c0 + (int64_t)jt * TK;
+        // Tile q of the stream: step t0 + q / (2 nt), pass (q / nt) % 2 (0: P, 1: C), column tile q % nt,
+        // ring stage q % ST, mbarrier phase parity (q / ST) % 2.  Both ends walk the stream in order, so
+        // they keep these as cursors instead of dividing (64-bit divisions on thread 0 would sit on
+        // every tile's critical path).
+        // Issue cursor (thread 0): the next tile to load, with its step's block draw.
+        int64_t i_t = t0;
+        int i_pass = 0, i_jt = 0, i_stg = 0, i_j = draw_block(cm.seed, t0, sys.sys_id, nb);
+        unsigned i_par = 0;
+        // load the tile at the cursor: A tile by TMA, the X slice (and in pass C the M slice) by bulk
+        // copy, one mbarrier; then advance.  The X / M slices were last written by bulk stores of this
+        // CTA, waited for before every refill.
+        auto issue_next = [&]() {
+            if (i_t >= t_end) return;
+            const int stg = i_stg;
+            const int64_t col = c0 + (int64_t)i_jt * TK;
             unsigned char *base = sm + stg * SB;
             const unsigned vbytes = (unsigned)(TK * k * 4);
-            mbar_arrive_expect_tx(&full[stg], (unsigned)(s * ST_ROWB) + vbytes * (pass ? 2u : 1u));
-            tma_load_2d(base, tmap, (int)col, j * s, &full[stg]);
+            mbar_arrive_expect_tx(&full[stg], (unsigned)(s * ST_ROWB) + vbytes * (i_pass ? 2u : 1u));
+            tma_load_2d(base, tmap, (int)col, i_j * s, &full[stg]);
             bulk_load(base + AB, X + col * k, vbytes, &full[stg]);
-            if (pass) bulk_load(base + AB + VB, M + col * k, vbytes, &full[stg]);
+            if (i_pass) bulk_load(base + AB + VB, M + col * k, vbytes, &full[stg]);
             s_pend[stg] = 1;
-            s_ppar[stg] = (unsigned)((q / ST_STAGES) & 1);
+            s_ppar[stg] = i_par;
+            if (++i_stg == ST_STAGES) {
+                i_stg = 0;
+                i_par ^= 1u;
+            }
+            if (++i_jt == nt) {
+                i_jt = 0;
+                i_pass ^= 1;
+                if (i_pass == 0 && ++i_t < t_end) i_j = draw_block(cm.seed, i_t, sys.sys_id, nb);
+            }
+        };
+        // Consumer cursor (every thread): the stage and phase parity of the tile being consumed.
+        int c_stg = 0;
+        unsigned c_par = 0;
+        auto next_stage = [&]() {
+            if (++c_stg == ST_STAGES) {
+                c_stg = 0;
+                c_par ^= 1u;
+            }
         };
         // wait for tile q; then refill the stage of tile q-2 (every thread is done with it) with tile
         // q-2+ST, after the bulk stores older than the most recent group have completed.  That covers the
-        // stage's own pass-C store (tile q-2) and, when the chunk has at least ST tiles, the last store
-        // of any X / M slice the refill reads (tile q-2+ST-nt or older); shorter chunks wait for all.
-        auto wait = [&](int64_t q) -> bool {
-            const int stg = (int)(q % ST_STAGES);
+        // stage's own pass-C store (tile q-2) and the last store of any X / M slice the refill reads
+        // (tile q-2+ST-nt or older: chunks have nt >= ST_MIN_TILES > ST tiles, and the first ST tiles,
+        // issued up front, all belong to the first step).  When tile q-1 opens a step (pass P, no
+        // store), the stage's own store is the most recent group: wait for all of them.
+        // opens_step: tile q-1 was the first tile of a step.  The refill is the issue cursor's tile,
+        // which is q-2+ST: ST tiles are issued up front and one per wait from q = 2 on.
+        auto wait = [&](int64_t q, bool opens_step) -> bool {
             if (tid == 0) {
-                if (!mbar_wait_bounded(&full[stg], (unsigned)((q / ST_STAGES) & 1), cm.timeout_ns)) {
+                if (!mbar_wait_bounded(&full[c_stg], c_par, cm.timeout_ns)) {
                     s_fail = 1;
                     group_fail(gs, KPP_ERR_TIMEOUT);
                 }
-                s_pend[stg] = 0;
+                s_pend[c_stg] = 0;
             }
             __syncthreads();
             if (tid == 0 && q >= 2) {
-                if (nt >= ST_STAGES) asm volatile("cp.async.bulk.wait_group 1;" ::: "memory");
-                else asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-                issue(q - 2 + ST_STAGES);
+                if (opens_step) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+                else asm volatile("cp.async.bulk.wait_group 1;" ::: "memory");
+                issue_next();
             }
             return !s_fail;
         };
 
         if (tid == 0)
-            for (int q = 0; q < ST_STAGES; ++q)
-                if (q < 2 * nt) issue(q);
+            for (int i = 0; i < ST_STAGES; ++i) issue_next();  // all in the first step: 2 nt > ST
         int64_t q = 0;
         int64_t t = t0;
         while (t < t_end) {
@@ -226,9 +246,9 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
                 p0[i] = make_float2(0.f, 0.f);
                 p1[i] = make_float2(0.f, 0.f);
             }
-            for (int jt = 0; jt < nt; ++jt, ++q) {
-                if (!wait(q)) break;
-                const unsigned char *base = sm + (q % ST_STAGES) * SB;
+            for (int jt = 0; jt < nt; ++jt, ++q, next_stage()) {
+                if (!wait(q, jt == 1)) break;
+                const unsigned char *base = sm + c_stg * SB;
                 const float *xs = (const float *)(base + AB);
                 if (k == KP && KP % 2 == 0) {
 #pragma unroll
@@ -345,9 +365,9 @@ __global__ void __launch_bounds__(256, 1) stream_kernel(const Sys4 *__restrict__
                 constexpr int RGN = 256 / TK;  // row groups
                 const int cc = tid % TK, rg = tid / TK;
                 const float eta = (float)cm.eta;
-                for (int jt = 0; jt < nt; ++jt, ++q) {
-                    if (!wait(q)) break;
-                    unsigned char *base = sm + (q % ST_STAGES) * SB;
+                for (int jt = 0; jt < nt; ++jt, ++q, next_stage()) {
+                    if (!wait(q, false)) break;
+                    unsigned char *base = sm + c_stg * SB;
                     const float *xs = (const float *)(base + AB);
                     const float *ms = (const float *)(base + AB + VB);
                     float w[KP];
@@ -477,6 +497,8 @@ void sys4_fill(void *dst, const void *tmap, const float *b, float *X, float *M, 
     p->b = b; p->X = X; p->M = M; p->Ginv = Ginv; p->part = part; p->rpart = rpart; p->sc = sc;
     p->bar = bar; p->err = err; p->sys_id = sys_id; p->t0 = t0;
 }
+
+int stream_min_tiles() { return ST_MIN_TILES; }
 
 int stream_tk(int dtype) { return dtype == KPP_BF16 ? st_tk<__nv_bfloat16>() : st_tk<float>(); }
 

@@ -439,6 +439,40 @@ def test_streaming_kernel_tracks_general_kernel_in_fp32(K):
         assert rel(out[3][i], out[1][i]) <= 2e-5
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("k", [3, 8])
+def test_streaming_kernel_uneven_short_chunks_track_general_kernel(K, dtype, k):
+    """The streaming kernel with 43 column tiles over 5 CTAs (chunks of 8 and 9 tiles, the shortest the
+    kernel takes): its prefetch runs close behind the X / M stores of the previous step.  The iterates
+    after T steps agree with the general kernel's to FP32 rounding, for the k = 8 panel path and the
+    generic one."""
+    nsys, m, s = 2, 64, 32
+    n = 43 * (32 if dtype == "f32" else 64)  # 43 tiles of 128 bytes per row
+    As, Bs = _wide_batch(nsys, m, n, s, k, dtype, seed=300)
+    lam = W.row_outlier_lambda(As[0])
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    P = K.Partition(m, s)
+    Ad = [dev(a, tdt) for a in As]
+    Bd = [dev(b) for b in Bs]
+    Fs = [K.Factors(a, P, lam, 0) for a in Ad]
+    out = {}
+    for v in (1, 3):
+        K.set_kernel_variant(v)
+        prm = K.params(lam=lam, tol=0.0, max_iters=37, refine=0, seed=9, grid=5)
+        Xd = [dev(np.zeros((n, k))) for _ in range(nsys)]
+        if v == 3:
+            plan = K.Plan(Ad, Bd, Xd, P, Fs, prm)
+            info = plan.info()
+            plan.close()
+            assert info["kernel"] == 4 and info["grid"] == 5, info
+        K.kpp_solve_batched(Ad, Bd, Xd, P, Fs, prm, allow_no_conv=True)
+        out[v] = [x.cpu().numpy() for x in Xd]
+    K.set_kernel_variant(3)
+    for i in range(nsys):
+        assert np.all(np.isfinite(out[3][i]))
+        assert rel(out[3][i], out[1][i]) <= 2e-5
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "f32"])
 def test_large_block_kernel_tracks_general_kernel_in_fp32(K, dtype):
     """The large-block K++ kernel (memoised W = G^-1 A_S, one exchange per step over 8-CTA clusters)
