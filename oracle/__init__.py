@@ -13,6 +13,10 @@ Convergence" (arXiv 2501.11673).  Functions cite the passage they follow:
   ``K++(Cholesky)`` variant of App. F; Alg. 5's adaptive rho and stopping rule) and the CD++
   iteration (Eq. 5.1, Alg. 3 lines 10-20), both without the randomized Hadamard preprocessing.
 * ``cg``: plain conjugate gradients (context, Sec. 6).
+* ``rht_forward`` / ``rht_inverse`` / ``rht_entry``: the randomized Hadamard preprocessing of CD++
+  (Sec. 5.1, Alg. 3 lines 2-3 and its return D FHT(x)) from the definition Q = H_n D, written out
+  with the explicit Sylvester-Hadamard entries.  ``fht`` / ``symfht``: the paper's recursive FHT and
+  SymFHT (App. on the symmetric fast Hadamard transform), with their operation counts.
 * ``philox4x32_10`` / ``sample_block``: Philox4x32-10 of Salmon et al. (SC'11).
 
 Parity of the adaptive-rho schedule and of the stopping rule is unpinned by the paper (it prints no
@@ -91,6 +95,14 @@ def _load():
             lib.orc_run.restype = ctypes.c_int
             lib.orc_cg.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_double, ctypes.c_int64, dp]
             lib.orc_cg.restype = ctypes.c_int64
+            lib.orc_rht_forward.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int64, dp, dp, dp]
+            lib.orc_rht_inverse.argtypes = [ctypes.c_int64, dp, ctypes.c_int64, dp, dp]
+            lib.orc_rht_entry.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int64, ctypes.c_int64]
+            lib.orc_rht_entry.restype = ctypes.c_double
+            lib.orc_fht.argtypes = [ctypes.c_int64, ctypes.c_int64, dp]
+            lib.orc_fht.restype = ctypes.c_int64
+            lib.orc_symfht.argtypes = [ctypes.c_int64, dp]
+            lib.orc_symfht.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -244,3 +256,62 @@ def cg(A: np.ndarray, b: np.ndarray, tol: float = 1e-8, max_iters: int = 100000,
     rr = ctypes.c_double()
     it = _load().orc_cg(A.shape[0], _dp(A), _dp(_f64(b)), _dp(x), tol, max_iters, ctypes.byref(rr))
     return x, int(it), rr.value
+
+
+# ----------------------------------------------------------------------------------------------
+# Randomized Hadamard preprocessing of CD++ (Sec. 5.1; App. on FHT / SymFHT)
+# ----------------------------------------------------------------------------------------------
+
+def _pow2(n: int) -> None:
+    if n < 1 or n & (n - 1):
+        raise ValueError("n must be a power of 2")
+
+
+def rht_forward(d: np.ndarray, A: np.ndarray, b: np.ndarray | None = None):
+    """(Q A Q^T, Q b) with Q = H_n diag(d) / sqrt(n), H_n Sylvester-Hadamard, d = +-1 signs.  b is a
+    vector or an n x k panel (or None).  Explicit O(n^3) definition."""
+    A = _f64(A)
+    n = A.shape[0]
+    _pow2(n)
+    B = np.zeros((n, 0)) if b is None else _f64(np.asarray(b).reshape(n, -1))
+    k = B.shape[1]
+    Abar = np.empty((n, n))
+    Bbar = np.empty((n, max(k, 1)))
+    _load().orc_rht_forward(n, _dp(_f64(d)), _dp(A), k, _dp(B if k else np.zeros((n, 1))), _dp(Abar), _dp(Bbar))
+    if b is None:
+        return Abar, None
+    return Abar, Bbar[:, :k].reshape(np.shape(b))
+
+
+def rht_inverse(d: np.ndarray, xbar: np.ndarray) -> np.ndarray:
+    """x = Q^T xbar = diag(d) H_n xbar / sqrt(n) (vector or n x k panel)."""
+    Xb = _f64(np.asarray(xbar).reshape(len(d), -1))
+    n, k = Xb.shape
+    _pow2(n)
+    X = np.empty_like(Xb)
+    _load().orc_rht_inverse(n, _dp(_f64(d)), k, _dp(Xb), _dp(X))
+    return X.reshape(np.shape(xbar))
+
+
+def rht_entry(d: np.ndarray, A: np.ndarray, i: int, j: int) -> float:
+    """One entry of Q A Q^T in O(n^2) (for sampled checks at large n)."""
+    A = _f64(A)
+    _pow2(A.shape[0])
+    return float(_load().orc_rht_entry(A.shape[0], _dp(_f64(d)), _dp(A), int(i), int(j)))
+
+
+def fht(V: np.ndarray):
+    """(H_n V, additions used) for a vector or n x k panel, by the halving recursion."""
+    W = _f64(np.asarray(V).reshape(np.shape(V)[0], -1)).copy()
+    n, k = W.shape
+    _pow2(n)
+    ops = _load().orc_fht(n, k, _dp(W))
+    return W.reshape(np.shape(V)), int(ops)
+
+
+def symfht(A: np.ndarray):
+    """(H_n A H_n, additions used) for a symmetric A, by the paper's SymFHT recursion."""
+    W = _f64(A).copy()
+    _pow2(W.shape[0])
+    ops = _load().orc_symfht(W.shape[0], _dp(W))
+    return W, int(ops)

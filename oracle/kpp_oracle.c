@@ -336,3 +336,142 @@ int64_t orc_cg(int64_t n, const double *A, const double *b, double *x, double to
     free(Ap);
     return it;
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Randomized Hadamard preprocessing of CD++ (Sec. 5.1, Algorithm CD++ lines 2-3 and the return
+ * D FHT(x); App. on FHT / SymFHT).
+ *
+ * H_n (n a power of 2) is the Sylvester-Hadamard matrix: H_1 = [1], H_2n = [[H_n, H_n], [H_n, -H_n]].
+ * Unrolling the recursion bit by bit gives its entries: (H_n)_{ij} = (-1)^{popcount(i AND j)}.
+ * Q = H_n D with D = diag(d) / sqrt(n), d_i = +-1, so Q Q^T = H D^2 H = H H / n = I.  The system
+ * A x = b becomes Abar xbar = bbar with Abar = Q A Q^T, bbar = Q b, and x = Q^T xbar = D H xbar.
+ *
+ * orc_rht_forward / orc_rht_inverse / orc_rht_entry are the definition written out: explicit entries
+ * of H and plain left-to-right sums (O(n^3) for the matrix).  orc_symfht is the paper's recursive
+ * SymFHT (H A H of a symmetric A, two half-size recursive calls plus one general transform of the
+ * off-diagonal block), kept to pin its result and its operation count (Thm. on SymFHT:
+ * at most n^2 (2.5 + log2 n) additions / subtractions).
+ * ------------------------------------------------------------------------------------------------ */
+static double had(int64_t i, int64_t j) { return (__builtin_popcountll((unsigned long long)(i & j)) & 1) ? -1.0 : 1.0; }
+
+/* Abar = Q A Q^T (n x n), and bbar = Q b for a panel b of k columns (n x k row-major; k may be 0). */
+void orc_rht_forward(int64_t n, const double *d, const double *A, int64_t k, const double *b, double *Abar,
+                     double *bbar) {
+    double *M = (double *)malloc(sizeof(double) * (size_t)(n * n));
+    double *T = (double *)malloc(sizeof(double) * (size_t)(n * n));
+    for (int64_t p = 0; p < n; ++p)
+        for (int64_t q = 0; q < n; ++q) M[p * n + q] = d[p] * A[p * n + q] * d[q] / (double)n;  /* D A D */
+    for (int64_t p = 0; p < n; ++p)                                                              /* T = M H */
+        for (int64_t j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int64_t q = 0; q < n; ++q) acc += M[p * n + q] * had(q, j);
+            T[p * n + j] = acc;
+        }
+    for (int64_t i = 0; i < n; ++i)                                                              /* H T */
+        for (int64_t j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int64_t p = 0; p < n; ++p) acc += had(i, p) * T[p * n + j];
+            Abar[i * n + j] = acc;
+        }
+    const double rs = 1.0 / sqrt((double)n);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t c = 0; c < k; ++c) {
+            double acc = 0.0;
+            for (int64_t p = 0; p < n; ++p) acc += had(i, p) * (d[p] * rs * b[p * k + c]);
+            bbar[i * k + c] = acc;
+        }
+    free(M);
+    free(T);
+}
+
+/* x = Q^T xbar = D H xbar for a panel of k columns. */
+void orc_rht_inverse(int64_t n, const double *d, int64_t k, const double *xbar, double *x) {
+    const double rs = 1.0 / sqrt((double)n);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t c = 0; c < k; ++c) {
+            double acc = 0.0;
+            for (int64_t p = 0; p < n; ++p) acc += had(i, p) * xbar[p * k + c];
+            x[i * k + c] = d[i] * rs * acc;
+        }
+}
+
+/* One entry (Q A Q^T)_{ij} = sum_p H_ip d_p / sqrt(n) sum_q A_pq d_q / sqrt(n) H_qj, O(n^2). */
+double orc_rht_entry(int64_t n, const double *d, const double *A, int64_t i, int64_t j) {
+    double acc = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+        double row = 0.0;
+        for (int64_t q = 0; q < n; ++q) row += A[p * n + q] * d[q] * had(q, j);
+        acc += had(i, p) * d[p] * row;
+    }
+    return acc / (double)n;
+}
+
+/* FHT of a length-n vector with stride `st`, in place, by the recursion H_n v = [H(v1 + v2); H(v1 - v2)]
+ * (v1, v2 the halves); n log2 n additions / subtractions, added to *ops. */
+static void fht_vec(int64_t n, double *v, int64_t st, double *tmp, int64_t *ops) {
+    if (n == 1) return;
+    const int64_t h = n / 2;
+    for (int64_t i = 0; i < h; ++i) {
+        const double a = v[i * st], c = v[(i + h) * st];
+        tmp[i] = a + c;
+        tmp[i + h] = a - c;
+    }
+    *ops += n;
+    for (int64_t i = 0; i < n; ++i) v[i * st] = tmp[i];
+    fht_vec(h, v, st, tmp, ops);
+    fht_vec(h, v + h * st, st, tmp, ops);
+}
+
+/* H_n v for k columns of an n x k row-major panel, in place; returns the operation count. */
+int64_t orc_fht(int64_t n, int64_t k, double *V) {
+    int64_t ops = 0;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int64_t c = 0; c < k; ++c) fht_vec(n, V + c, k, tmp, &ops);
+    free(tmp);
+    return ops;
+}
+
+/* SymFHT of the symmetric n x n block at A (leading dimension ld), in place: the block becomes H A H.
+ * With A = [[A11, A12], [A12^T, A22]] and B11 = H A11 H, B22 = H A22 H (recursive), B12 = H A12 H:
+ *   C11 = B11 + B12^T, C12 = B11 - B12, C21 = B12 + B22, C22 = B12^T - B22,
+ *   H A H = [[C11 + C21, C12 + C22], [(C12 + C22)^T, C12 - C22]]. */
+static void symfht_rec(int64_t n, double *A, int64_t ld, double *tmp, int64_t *ops) {
+    if (n == 1) return;
+    const int64_t h = n / 2;
+    double *A11 = A, *A12 = A + h, *A21 = A + h * ld, *A22 = A + h * ld + h;
+    symfht_rec(h, A11, ld, tmp, ops);
+    symfht_rec(h, A22, ld, tmp, ops);
+    for (int64_t i = 0; i < h; ++i) fht_vec(h, A12 + i * ld, 1, tmp, ops);  /* rows:    A12 H   */
+    for (int64_t j = 0; j < h; ++j) fht_vec(h, A12 + j, ld, tmp, ops);      /* columns: H A12 H */
+    double *C = (double *)malloc(sizeof(double) * (size_t)(4 * h * h));
+    double *C11 = C, *C12 = C + h * h, *C21 = C + 2 * h * h, *C22 = C + 3 * h * h;
+    for (int64_t i = 0; i < h; ++i)
+        for (int64_t j = 0; j < h; ++j) {
+            const double b11 = A11[i * ld + j], b22 = A22[i * ld + j];
+            const double b12 = A12[i * ld + j], b12t = A12[j * ld + i];
+            C11[i * h + j] = b11 + b12t;
+            C12[i * h + j] = b11 - b12;
+            C21[i * h + j] = b12 + b22;
+            C22[i * h + j] = b12t - b22;
+        }
+    *ops += 4 * h * h;
+    for (int64_t i = 0; i < h; ++i)
+        for (int64_t j = 0; j < h; ++j) {
+            A11[i * ld + j] = C11[i * h + j] + C21[i * h + j];
+            A12[i * ld + j] = C12[i * h + j] + C22[i * h + j];
+            A22[i * ld + j] = C12[i * h + j] - C22[i * h + j];
+        }
+    for (int64_t i = 0; i < h; ++i)
+        for (int64_t j = 0; j < h; ++j) A21[i * ld + j] = A12[j * ld + i];
+    *ops += 3 * h * h;
+    free(C);
+}
+
+/* H A H of a symmetric n x n row-major A, in place; returns the additions / subtractions used. */
+int64_t orc_symfht(int64_t n, double *A) {
+    int64_t ops = 0;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    symfht_rec(n, A, n, tmp, &ops);
+    free(tmp);
+    return ops;
+}

@@ -81,6 +81,11 @@ def spd(n: int, n_out: int, out_lo: float, out_hi: float, bulk_lo: float, bulk_h
     return A, b, sig
 
 
+def rademacher_signs(n: int, seed: int) -> np.ndarray:
+    """n independent +-1 signs (FP64), the diagonal of the randomized Hadamard transform's D."""
+    return np.where(np.random.default_rng(seed).integers(0, 2, n) == 1, 1.0, -1.0)
+
+
 def gaussian_rows(m: int, n: int, n_big: int, scale: float, seed_A: int, seed_b: int,
                   k_rhs: int = 1) -> tuple:
     """Under-determined A (m < n) with i.i.d. N(0,1) entries; n_big seeded rows scaled by `scale`."""

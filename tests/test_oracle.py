@@ -10,6 +10,9 @@ Paper: arXiv 2501.11673.  What pins what:
   * CD++ step            -> K++ on Phi with Phi Phi^T = A (Eq. 5.1 / the implicit form in the proof of Thm 5.1)
   * whole solves         -> x*, numpy.linalg.solve / lstsq / the min-norm solution; range invariance (Thm 2.1)
   * CG                   -> numpy.linalg.solve
+  * Hadamard preprocessing (Sec. 5.1) -> scipy.linalg.hadamard (Sylvester construction); the spectrum and
+                            the solution are invariant (Q orthogonal); the SymFHT operation count of its
+                            theorem, n^2 (2.5 + log2 n), and the recursion's exact count
 The adaptive-rho schedule and the stop rule have no printed values in the paper ("parity unpinned"):
 only their structural properties are checked here.
 """
@@ -277,3 +280,73 @@ def test_storage_rounding_is_exact_widening():
     assert np.all(np.abs(Ab - A) <= 2.0 ** -8 * np.abs(A))
     bits = W.bf16_bits(A).astype(np.uint32) << 16
     np.testing.assert_array_equal(bits.view(np.float32).astype(np.float64), Ab)
+
+
+# ---------------------------------------------------------------------------------------------
+# Randomized Hadamard preprocessing of CD++ (Sec. 5.1, Alg. 3 lines 2-3; App. on FHT / SymFHT)
+# ---------------------------------------------------------------------------------------------
+
+def _sym(n, seed):
+    A = np.random.default_rng(seed).standard_normal((n, n))
+    return A + A.T
+
+
+def _signs(n, seed):
+    return W.rademacher_signs(n, seed)
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 16, 64])
+def test_rht_matches_scipy_hadamard(n):
+    """Q A Q^T, Q b and Q^T x against scipy's Sylvester-Hadamard matrix, Q = H diag(d) / sqrt(n)."""
+    import scipy.linalg
+    A, d = _sym(n, n), _signs(n, 100 + n)
+    B = np.random.default_rng(200 + n).standard_normal((n, 3))
+    Q = scipy.linalg.hadamard(n).astype(float) * d[None, :] / math.sqrt(n)
+    Abar, Bbar = oracle.rht_forward(d, A, B)
+    assert np.abs(Abar - Q @ A @ Q.T).max() <= 1e-13 * n
+    assert np.abs(Bbar - Q @ B).max() <= 1e-13 * n
+    assert np.abs(oracle.rht_inverse(d, Bbar) - B).max() <= 1e-13 * n
+    for i, j in [(0, 0), (n - 1, 0), (n // 2, n - 1)]:
+        assert abs(oracle.rht_entry(d, A, i, j) - Abar[i, j]) <= 1e-13 * n
+
+
+def test_rht_keeps_spectrum_and_solution():
+    """Q is orthogonal: Q A Q^T has the eigenvalues of A, and Q^T (Q A Q^T)^{-1} Q b = A^{-1} b."""
+    n = 32
+    A, b, _ = W.spd(n, 4, 1e1, 1e3, 1.0, 2.0, seed_A=3, seed_b=6)
+    d = W.rademacher_signs(n, 5)
+    Abar, bbar = oracle.rht_forward(d, A, b)
+    np.testing.assert_allclose(np.linalg.eigvalsh(Abar), np.linalg.eigvalsh(A), rtol=1e-12)
+    assert np.abs(Abar - Abar.T).max() <= 1e-12 * np.abs(A).max()
+    x = oracle.rht_inverse(d, np.linalg.solve(Abar, bbar))
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-10)
+
+
+def test_rht_rejects_sizes_that_are_not_powers_of_two():
+    with pytest.raises(ValueError):
+        oracle.rht_forward(np.ones(6), np.eye(6))
+
+
+@pytest.mark.parametrize("n", [1, 2, 8, 32, 128])
+def test_fht_follows_the_sylvester_definition_with_n_log_n_operations(n):
+    """H_2n = [[H_n, H_n], [H_n, -H_n]]: H v = [H(v1 + v2); H(v1 - v2)] for the halves v1, v2 (the
+    appendix's listing writes the second half as H(v2 - v1); the definition decides), n log2 n ops."""
+    import scipy.linalg
+    V = np.random.default_rng(n).standard_normal((n, 2))
+    got, ops = oracle.fht(V)
+    assert np.abs(got - scipy.linalg.hadamard(n) @ V).max() <= 1e-13 * n
+    assert ops == 2 * n * int(round(math.log2(n)))
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 64, 128])
+def test_symfht_returns_hah_within_its_operation_bound(n):
+    """SymFHT(A) = H A H for symmetric A, using n^2 log2 n + 1.5 n^2 - 1.5 n additions (the recursion
+    T(n) = 2 T(n/2) + 2 (n/2)^2 log2(n/2) + 7 (n/2)^2, T(1) = 0), within the theorem's n^2 (2.5 + log2 n)."""
+    import scipy.linalg
+    A = _sym(n, 7 + n)
+    H = scipy.linalg.hadamard(n).astype(float)
+    got, ops = oracle.symfht(A)
+    assert np.abs(got - H @ A @ H).max() <= 1e-12 * n
+    L = int(round(math.log2(n)))
+    assert ops == n * n * L + (3 * n * n - 3 * n) // 2
+    assert ops <= n * n * (2.5 + L)
