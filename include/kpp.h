@@ -225,6 +225,25 @@ kpp_status cdpp_solve_noalloc(const kpp_matrix *A, const double *b, double *x, k
 kpp_status kpp_block_gram(const kpp_matrix *A, int32_t s, double lambda, int32_t engine, double *G_out,
                           int32_t *engine_used, void *stream);
 
+/* Randomized Hadamard preprocessing of a symmetric system for CD++ (Sec. 5.1: Alg. 3's transform of
+ * A and b before the loop and its return D FHT(x); the FHT / SymFHT appendix):
+ *   Abar = Q A Q^T,  bbar = Q b,   Q = H_n D,  D = diag(d) / sqrt(n),
+ * H_n the Sylvester-Hadamard matrix (H_1 = [1], H_2n = [[H_n, H_n], [H_n, -H_n]]).  Q is orthogonal, so
+ * Abar is symmetric (PSD if A is) with A's spectrum, and x = Q^T xbar solves A x = b when xbar solves
+ * Abar xbar = bbar; |Abar xbar - bbar| = |A x - b|.
+ * n: a power of 2, 1 <= n <= 16384.  d: device, n FP64 signs +1 / -1 (the caller draws them).
+ * A: device FP64 n x n, row-major (A->ld >= n), symmetric.  Abar: device, n x n, leading dimension n;
+ * it may be A->data itself when A->ld = n.  b, bbar: device n x k panels (row-major, leading dimension
+ * k; k = 0 transforms the matrix only and b, bbar may be NULL); bbar may equal b.
+ * Two streaming passes over the matrix plus an n x n FP64 scratch allocated and freed on `stream`.
+ * Errors: KPP_ERR_ARG (size, dtype, null pointer), KPP_ERR_OOM, KPP_ERR_CUDA.  Stream-ordered. */
+kpp_status kpp_rht_forward(int64_t n, const double *d, const kpp_matrix *A, double *Abar, const double *b,
+                           double *bbar, int32_t k, void *stream);
+
+/* x = Q^T xbar = diag(d) H_n xbar / sqrt(n) for an n x k device panel (row-major, leading dimension k;
+ * k >= 1); x may equal xbar.  Errors: KPP_ERR_ARG, KPP_ERR_CUDA.  Stream-ordered. */
+kpp_status kpp_rht_inverse(int64_t n, const double *d, const double *xbar, double *x, int32_t k, void *stream);
+
 /* Select the solve kernel for later calls in this process.  All variants compute the same iteration.
  *   3 (default): CD++ uses the dataflow kernel (no per-step barrier: the owners of the next block
  *     hand r over through a tagged mailbox; FP64 streams the memoised W_j = G_j^{-1} A_{S_j}); K++ uses

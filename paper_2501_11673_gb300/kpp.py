@@ -35,7 +35,7 @@ EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_par
            "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_reset_stats", "kpp_server_destroy",
            "cdpp_solve_batched", "kpp_plan_create", "kpp_plan_launch", "kpp_plan_report", "kpp_plan_info",
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
-           "kpp_tune_cache_load", "kpp_launch_count", "kpp_build_info"]
+           "kpp_tune_cache_load", "kpp_launch_count", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
 
@@ -133,6 +133,10 @@ def load(path: str | None = None):
             getattr(lib, name).restype = ctypes.c_int
         lib.kpp_block_gram.argtypes = [ctypes.POINTER(Matrix), i32, dbl, i32, vp, ctypes.POINTER(i32), vp]
         lib.kpp_block_gram.restype = ctypes.c_int
+        lib.kpp_rht_forward.argtypes = [i64, vp, ctypes.POINTER(Matrix), vp, vp, vp, i32, vp]
+        lib.kpp_rht_forward.restype = ctypes.c_int
+        lib.kpp_rht_inverse.argtypes = [i64, vp, vp, vp, i32, vp]
+        lib.kpp_rht_inverse.restype = ctypes.c_int
         for name in ("kpp_set_kernel_variant", "cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
                      "kpp_solve_host", "kpp_rel_residual", "kpp_solve_batched"):
             getattr(lib, name).restype = ctypes.c_int
@@ -428,6 +432,36 @@ def block_gram(A, s: int, lam: float, engine: int = 0, stream=None):
     _check(load().kpp_block_gram(ctypes.byref(m), int(s), float(lam), int(engine), ctypes.c_void_p(G.data_ptr()),
                                  ctypes.byref(used), _stream_ptr(stream)))
     return G, used.value
+
+
+def rht_forward(d, A, b=None, stream=None):
+    """(Q A Q^T, Q b) with Q = H_n diag(d) / sqrt(n) (kpp_rht_forward): d FP64 signs, A FP64 n x n, b a
+    vector or n x k panel (FP64) or None.  Returns new device tensors."""
+    import torch
+    n = A.shape[0]
+    Abar = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    m = matrix(A)
+    if b is None:
+        bb, bbar, k = None, None, 0
+    else:
+        bb = b.reshape(n, -1).contiguous()
+        bbar = torch.empty_like(bb)
+        k = bb.shape[1]
+    vp = ctypes.c_void_p
+    _check(load().kpp_rht_forward(n, vp(d.data_ptr()), ctypes.byref(m), vp(Abar.data_ptr()),
+                                  vp(bb.data_ptr() if bb is not None else 0), vp(bbar.data_ptr() if bbar is not None else 0),
+                                  k, _stream_ptr(stream)))
+    return Abar, (None if b is None else bbar.reshape(b.shape))
+
+
+def rht_inverse(d, xbar, stream=None):
+    """x = Q^T xbar = diag(d) H_n xbar / sqrt(n) (kpp_rht_inverse) for a vector or n x k panel."""
+    n = xbar.shape[0]
+    xb = xbar.reshape(n, -1).contiguous()
+    x = xb.new_empty(xb.shape)
+    _check(load().kpp_rht_inverse(n, ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(xb.data_ptr()),
+                                  ctypes.c_void_p(x.data_ptr()), xb.shape[1], _stream_ptr(stream)))
+    return x.reshape(xbar.shape)
 
 
 class Server:
