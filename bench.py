@@ -334,6 +334,79 @@ class MixedSPD(SingleFP64):
         return None
 
 
+class RhtSPD(SingleFP64):
+    """The cdpp4096 system with CD++'s randomized Hadamard preprocessing inside the step (Alg. 3):
+    Abar = Q A Q^T and bbar = Q b on the GPU, factors and CD++ on (Abar, bbar), x = Q^T xbar."""
+
+    def __init__(self):
+        super().__init__("cdpp4096")
+        self.name = "cdpp4096-rht"
+        self.desc += ("; randomized Hadamard preprocessing Q = H_n diag(d) / sqrt(n) (d Rademacher, seed 7) "
+                      "applied on the GPU inside every step, and x = Q^T xbar after it")
+
+    def setup(self, kpp, torch, rank):
+        super().setup(kpp, torch, rank)
+        n = self.sy.A.shape[1]
+        self.d = torch.as_tensor(W.rademacher_signs(n, 7), device="cuda")
+        self.xbar = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+    def _solve(self, A, b):
+        kpp, torch = self.kpp, self.torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Abar, bbar = kpp.rht_forward(self.d, A, b)
+        e1.record()
+        self.xbar.zero_()
+        F = kpp.Factors(Abar, self.P, self.sy.lam, 1)
+        rep = kpp.cdpp_solve(Abar, bbar, self.xbar, self.P, F, self.prm)
+        x = kpp.rht_inverse(self.d, self.xbar)
+        del F, Abar
+        return rep, x, e0, e1
+
+    def step(self):
+        rep, self.x, e0, e1 = self._solve(self.Ad, self.bd)
+        # the original system's FP64 residual (equal to the transformed one up to rounding: Q is orthogonal)
+        res = self.kpp.rel_residual(self.Ad, self.bd, self.x)
+        return {"units": rep.iters, "ok": rep.status == self.kpp.OK and res <= 1.0001 * self.sy.tol,
+                "kernel_ms": rep.kernel_ms, "kernel_launches": rep.launches, "iters": rep.iters,
+                "outer": rep.outer, "rel_res": res, "rht_ms": e0.elapsed_time(e1)}
+
+    def extra(self, steps):
+        n = self.sy.A.shape[1]
+        rht_ms = statistics.mean(st["rht_ms"] for st in steps)
+        # two streaming passes over the n x n FP64 matrix (read + write each) and the vector
+        byts = 4 * 8 * n * n + 2 * 8 * n
+        return {"rht_forward_ms": rht_ms, "rht_forward_gbs": byts / (rht_ms / 1e3) / 1e9,
+                "rht_forward_bytes": byts}
+
+    def cpu_baseline(self, budget_s):
+        out = super().cpu_baseline(budget_s)
+        out["sample"] += "; on the untransformed matrix (same sizes, same work per iteration)"
+        return out
+
+    def e2e(self):
+        """Pinned host A and b in, transform + factors + CD++ + inverse transform, x out."""
+        torch = self.torch
+        A_h = torch.as_tensor(self.sy.A).pin_memory()
+        b_h = torch.as_tensor(self.sy.b).pin_memory()
+        x_h = torch.empty_like(b_h).pin_memory()
+        ets = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A = A_h.to("cuda", non_blocking=True)
+            b = b_h.to("cuda", non_blocking=True)
+            rep, x, _, _ = self._solve(A, b)
+            x_h.copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+            ets.append(time.perf_counter() - t0)
+            assert rep.status == self.kpp.OK
+            del A, b
+        return {"value": rep.iters / ets[-1], "unit": self.unit,
+                "h2d_bytes_per_step": A_h.numel() * 8 + b_h.numel() * 8, "d2h_bytes_per_step": x_h.numel() * 8,
+                "time_to_tol_ms": 1e3 * ets[-1], "note": "pinned host A, b in and x out around the whole step"}
+
+
 class MixedLS(Workload):
     """K++ on a 262144 x 4096 LS stored BF16 / FP32, FP32 iterations + FP64 refinement."""
 
@@ -677,6 +750,8 @@ def make_workload(args):
         return Batched(nsys=getattr(args, "systems", 64), grid=getattr(args, "batched_grid", None))
     if args.workload == "serving":
         return Serving(n_req=args.requests)
+    if args.workload == "cdpp4096-rht":
+        return RhtSPD()
     if args.workload in ("cdpp4096-f32", "cdpp4096-bf16"):
         return MixedSPD(args.workload.split("-")[1])
     raise SystemExit(f"unknown workload {args.workload}")
@@ -738,7 +813,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cdpp4096",
                     choices=["cdpp4096", "kpp2000", "mixed262144", "batched64", "serving", "cdpp4096-f32",
-                             "cdpp4096-bf16"])
+                             "cdpp4096-bf16", "cdpp4096-rht"])
     ap.add_argument("--storage", default="bf16", choices=["bf16", "f32"], help="mixed262144 storage type")
     ap.add_argument("--noisy", action="store_true", help="mixed262144: b = A x* + 1e-6 N(0,I)")
     ap.add_argument("--mixed-rows", type=int, default=262144,

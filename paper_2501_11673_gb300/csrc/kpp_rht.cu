@@ -6,14 +6,16 @@
 // with H_n the Sylvester-Hadamard matrix (H_2n = [[H_n, H_n], [H_n, -H_n]]; entry (i, j) is
 // (-1)^popcount(i AND j)), so Q is orthogonal and CD++ on (Abar, bbar) solves the original system.
 //
-// The paper's SymFHT saves arithmetic by transforming one off-diagonal block for both.  On this GPU
-// the transform is bound by HBM, not arithmetic (12 butterfly levels per element at n = 4096 against
-// one read and one write of it), so the matrix takes two streaming passes instead:
+// The matrix takes two streaming passes:
 //   1. rows:    R = (D A D) H   -- every row scaled by d_i d_j / n and transformed in shared memory;
 //   2. columns: Abar = H R      -- CTAs gather four columns of R (32 contiguous bytes per row: whole
 //      sectors), transform them in shared memory and write them out as four rows of Abar (Abar is
 //      symmetric: its row c is H applied to column c of R).
-// Each pass reads and writes the n x n matrix once.  Within a CTA the length-n transform runs as radix-16
+// Each pass reads and writes the n x n matrix once, and adds log2 n FP64 butterflies per element.  On
+// this GPU the FP64 additions, not HBM, bound the passes: 2 n^2 log2 n in all, at about 1.7 FP64 lanes
+// per clock per SM.  The paper's SymFHT needs n^2 log2 n + 1.5 n^2 (it transforms one off-diagonal block
+// for both at each level of its recursion); it is not used here, since the transform is a few percent
+// of a CD++ solve.  Within a CTA the length-n transform runs as radix-16
 // passes over 4 bits of the index each (the Sylvester factors commute), in registers, over a shared
 // vector padded by one double per 16 so that strided and unit-stride groups are both conflict-free.
 // Vectors and panels (b, x) use the column pass without the transpose.
