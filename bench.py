@@ -205,8 +205,9 @@ def _hbm_roof(kernel, byts_per_launch, launch_ms, peaks, traffic_key, per_iter, 
 class SingleFP64(Workload):
     """One FP64 system, factor + solve per step (CD++ n=4096, or K++ 2000x200)."""
 
-    def __init__(self, name):
+    def __init__(self, name, grid_tune=False):
         self.name = name
+        self.grid_tune = grid_tune
         self.cd = name.startswith("cdpp4096")
         if self.cd:
             self.sy = W.cdpp_fp64_spd()
@@ -228,7 +229,10 @@ class SingleFP64(Workload):
         self.bd = torch.as_tensor(sy.b, device="cuda")
         self.x = torch.zeros(n, dtype=torch.float64, device="cuda")
         self.P = kpp.Partition(m, sy.s)
-        self.prm = kpp.params(lam=sy.lam, tol=sy.tol, seed=self.seed, sys_id=rank)
+        self.prm = kpp.params(lam=sy.lam, tol=sy.tol, seed=self.seed, sys_id=rank,
+                              grid=kpp.GRID_TUNE if self.grid_tune else 0)
+        if self.grid_tune:
+            self.desc += "; CTAs per system chosen by the launch autotuner (during warm-up)"
         self.solve = kpp.cdpp_solve if self.cd else kpp.kpp_solve
 
     def step(self):
@@ -743,7 +747,7 @@ class Serving(Workload):
 
 def make_workload(args):
     if args.workload in ("cdpp4096", "kpp2000"):
-        return SingleFP64(args.workload)
+        return SingleFP64(args.workload, grid_tune=getattr(args, "grid_tune", False))
     if args.workload == "mixed262144":
         return MixedLS(args.storage, args.noisy, m=args.mixed_rows)
     if args.workload == "batched64":
@@ -819,6 +823,8 @@ def main():
     ap.add_argument("--mixed-rows", type=int, default=262144,
                     help="mixed262144: rows of the system (a smaller one for profiler captures)")
     ap.add_argument("--requests", type=int, default=1024, help="serving: requests per step")
+    ap.add_argument("--grid-tune", action="store_true",
+                    help="cdpp4096 / kpp2000: let the launch autotuner pick the CTAs per system")
     ap.add_argument("--systems", type=int, default=64, help="batched64: systems (fewer for profiler captures)")
     ap.add_argument("--batched-grid", type=int, default=None, help="batched64: CTAs per system (default: autotuned)")
     ap.add_argument("--host-qr", action="store_true",
