@@ -13,6 +13,9 @@ Convergence" (arXiv 2501.11673).  Functions cite the passage they follow:
   ``K++(Cholesky)`` variant of App. F; Alg. 5's adaptive rho and stopping rule) and the CD++
   iteration (Eq. 5.1, Alg. 3 lines 10-20), both without the randomized Hadamard preprocessing.
 * ``cg``: plain conjugate gradients (context, Sec. 6).
+* ``run_memo`` (with ``memo_prob``, ``memo_subset``, ``memo_draw``, ``step_subset``): K++ / CD++ with the
+  online block memoisation over random s-subsets (Sec. 4 "Block memoization", Sec. 5.2, the sampling
+  lines of Alg. 3 and Alg. 5), the readings for its random draws stated in kpp_oracle.c.
 * ``rht_forward`` / ``rht_inverse`` / ``rht_entry``: the randomized Hadamard preprocessing of CD++
   (Sec. 5.1, Alg. 3 lines 2-3 and its return D FHT(x)) from the definition Q = H_n D, written out
   with the explicit Sylvester-Hadamard entries.  ``fht`` / ``symfht``: the paper's recursive FHT and
@@ -103,6 +106,21 @@ def _load():
             lib.orc_fht.restype = ctypes.c_int64
             lib.orc_symfht.argtypes = [ctypes.c_int64, dp]
             lib.orc_symfht.restype = ctypes.c_int64
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            lib.orc_memo_prob.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int64]
+            lib.orc_memo_prob.restype = ctypes.c_double
+            lib.orc_memo_subset.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int64,
+                                            ctypes.c_int, i64p]
+            lib.orc_memo_draw.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int,
+                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int64]
+            lib.orc_memo_draw.restype = ctypes.c_int64
+            lib.orc_step_subset.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, i64p, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+            lib.orc_step_subset.restype = ctypes.c_int
+            lib.orc_run_memo.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, ctypes.POINTER(_Params),
+                                         ctypes.POINTER(_State), dp, dp, ctypes.POINTER(_Report), i64p, i64p,
+                                         ctypes.c_int64]
+            lib.orc_run_memo.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -315,3 +333,63 @@ def symfht(A: np.ndarray):
     _pow2(W.shape[0])
     ops = _load().orc_symfht(W.shape[0], _dp(W))
     return W, int(ops)
+
+
+# ----------------------------------------------------------------------------------------------
+# Online block memoisation with random subsets (Sec. 4, Sec. 5.2; Alg. 3 / Alg. 5 sampling lines)
+# ----------------------------------------------------------------------------------------------
+
+def memo_prob(cd: bool, rows: int, n: int, s: int, t: int) -> float:
+    """Probability that step t draws a new block (CD++: min(1, (n/s) ln n / t); K++: the minimum with
+    (m/s) ln m / t and (n/s) ln m / t; 1 at t = 0)."""
+    return float(_load().orc_memo_prob(int(cd), rows, n, s, t))
+
+
+def memo_subset(seed: int, t: int, sys: int, N: int, s: int) -> np.ndarray:
+    """The uniform s-subset of range(N) drawn at step t (Floyd's sampling), sorted."""
+    S = np.empty(s, dtype=np.int64)
+    _load().orc_memo_subset(seed, t, sys, N, s, S.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return S
+
+
+def memo_draw(seed: int, t: int, sys: int, cd: bool, rows: int, n: int, s: int, nb: int) -> int:
+    """-1 when step t draws a new subset, else the index in [0, nb) of the memoised block it reuses."""
+    return int(_load().orc_memo_draw(seed, t, sys, int(cd), rows, n, s, nb))
+
+
+def step_subset(A: np.ndarray, b: np.ndarray, S, *, cd: bool, lam: float, beta: float = 1.0, eta: float = 0.0,
+                x0=None, mom0=None):
+    """One step on the rows S (factor computed here): (x, mom, |r|^2)."""
+    A, b = _f64(A), _f64(b)
+    rows, n = A.shape
+    Sv = np.ascontiguousarray(S, dtype=np.int64)
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    mom = np.zeros(n) if mom0 is None else _f64(mom0).copy()
+    rn2 = ctypes.c_double()
+    rc = _load().orc_step_subset(rows, n, _dp(A), _dp(b), Sv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(Sv),
+                                 int(cd), lam, beta, eta, _dp(x), _dp(mom), ctypes.byref(rn2))
+    if rc:
+        raise ValueError("subset block not SPD")
+    return x, mom, rn2.value
+
+
+def run_memo(A: np.ndarray, b: np.ndarray, s: int, *, cd: bool = False, lam: float = 0.0, tol: float = 1e-8,
+             max_iters: int = 100000, seed: int = 0, sys: int = 0, adaptive: bool = True, eta: float | None = None,
+             confirm: bool = True, block_cap: int = 0):
+    """K++ / CD++ with the online memo from x0 = 0.  Returns (Result, number of memoised blocks,
+    memo index of each of the first block_cap steps)."""
+    lib = _load()
+    A, b = _f64(A), _f64(b)
+    rows, n = A.shape
+    x, mom = np.zeros(n), np.zeros(n)
+    cst = _State(0, 0, 0.0, 0.0, 0.0, 0.0)
+    p = _Params(s=s, cd=int(cd), lam=lam, tol=tol, max_iters=max_iters, seed=seed, sys=sys,
+                adaptive=int(adaptive), eta=default_eta(rows, n, s) if eta is None else eta, confirm=int(confirm))
+    rep = _Report()
+    nb = ctypes.c_int64()
+    blocks = np.full(max(block_cap, 1), -2, dtype=np.int64)
+    lib.orc_run_memo(rows, n, _dp(A), _dp(b), ctypes.byref(p), ctypes.byref(cst), _dp(x), _dp(mom), ctypes.byref(rep),
+                     ctypes.byref(nb), blocks.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), block_cap)
+    st = State(cst.t, cst.ci, cst.E0, cst.E1, cst.rhat, cst.rho)
+    res = Result(x, mom, st, rep.iters, rep.rel_res_true, rep.rel_res_est, rep.status, np.zeros((0, 5)))
+    return res, int(nb.value), blocks[:block_cap]

@@ -475,3 +475,200 @@ int64_t orc_symfht(int64_t n, double *A) {
     free(tmp);
     return ops;
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Online block memoisation with random subsets (Sec. 4, "Block memoization"; Sec. 5.2, the
+ * simplified scheme of CD++ in Alg. 3's sampling lines; the sampling line of Alg. 5 for K++).
+ *
+ * The collection B of memoised blocks starts empty.  At step t a Bernoulli draw with probability
+ *   CD++: p_t = min(1, (n / s) ln(n) / t)          K++: p_t = min(1, (m / s) ln(m) / t, (n / s) ln(m) / t)
+ * (p_0 = 1) decides between a new uniformly random s-subset S of the rows (its factor is computed and
+ * S joins B) and a uniform pick from B (its factor is reused).  The factor is chol(A_S A_S^T + lam I)
+ * for K++ and chol(A_SS + lam I) for CD++; the step itself is the one of orc_run on the rows of S.
+ *
+ * Readings (the paper is silent): log is the natural log; the draws come from Philox4x32-10 with the
+ * key {seed_lo, seed_hi}: counter {t_lo, t_hi, sys, 0} gives the Bernoulli word (out[1], new iff
+ * out[1] < p_t 2^32) and the pick (out[2]: j = out[2] |B| >> 32); counter {t_lo, t_hi, sys, 1 + i/4}
+ * gives word out[i mod 4] for the i-th draw of Floyd's sampling of S (R. W. Floyd's algorithm for a
+ * uniform s-subset of [0, N): for j = N - s .. N - 1 take r uniform in [0, j] (r = word (j + 1) >> 32),
+ * and add j if r is already taken, else r); S is then sorted ascending.  zeta = ceil(rows / s) as for
+ * the fixed partition.  The memo lives for one call of orc_run_memo.
+ * ------------------------------------------------------------------------------------------------ */
+double orc_memo_prob(int cd, int64_t rows, int64_t n, int s, int64_t t) {
+    if (t <= 0) return 1.0;
+    double p;
+    if (cd) {
+        p = (double)n / (double)s * log((double)n) / (double)t;
+    } else {
+        const double lm = log((double)rows);
+        const double a = (double)rows / (double)s * lm / (double)t, c = (double)n / (double)s * lm / (double)t;
+        p = a < c ? a : c;
+    }
+    return p < 1.0 ? p : 1.0;
+}
+
+static void memo_words(uint64_t seed, int64_t t, uint32_t sys, uint32_t lane, uint32_t out[4]) {
+    uint32_t ctr[4] = {(uint32_t)(uint64_t)t, (uint32_t)((uint64_t)t >> 32), sys, lane};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* Uniform s-subset of [0, N) drawn at step t (Floyd), sorted ascending into S[0..s). */
+void orc_memo_subset(uint64_t seed, int64_t t, uint32_t sys, int64_t N, int s, int64_t *S) {
+    uint32_t wv[4];
+    int cnt = 0;
+    for (int i = 0; i < s; ++i) {
+        if (i % 4 == 0) memo_words(seed, t, sys, 1u + (uint32_t)(i / 4), wv);
+        const int64_t j = N - s + i;
+        const int64_t r = (int64_t)(((uint64_t)wv[i % 4] * (uint64_t)(j + 1)) >> 32);
+        int taken = 0;
+        for (int q = 0; q < cnt; ++q) taken |= (S[q] == r);
+        S[cnt++] = taken ? j : r;
+    }
+    for (int a = 1; a < s; ++a) { /* insertion sort */
+        const int64_t v = S[a];
+        int q = a - 1;
+        while (q >= 0 && S[q] > v) {
+            S[q + 1] = S[q];
+            --q;
+        }
+        S[q + 1] = v;
+    }
+}
+
+/* The draw of step t with nb blocks memoised so far: -1 = sample a new subset, else the memo index. */
+int64_t orc_memo_draw(uint64_t seed, int64_t t, uint32_t sys, int cd, int64_t rows, int64_t n, int s, int64_t nb) {
+    if (nb <= 0) return -1;
+    uint32_t o[4];
+    memo_words(seed, t, sys, 0u, o);
+    const double p = orc_memo_prob(cd, rows, n, s, t);
+    if ((double)o[1] < p * 4294967296.0) return -1;
+    return (int64_t)(((uint64_t)o[2] * (uint64_t)nb) >> 32);
+}
+
+/* Factor of the subset S (lower Cholesky, s x s): K++ A_S A_S^T + lam I, CD++ A_SS + lam I. */
+static int subset_factor(int64_t n, const double *A, const int64_t *S, int s, int cd, double lam, double *L) {
+    for (int a = 0; a < s; ++a)
+        for (int c = 0; c < s; ++c) {
+            double g = cd ? A[(size_t)S[a] * n + S[c]] : dot(n, A + (size_t)S[a] * n, A + (size_t)S[c] * n);
+            L[(size_t)a * s + c] = g + (a == c ? lam : 0.0);
+        }
+    return orc_cholesky(s, L);
+}
+
+/* One step on the rows S with their factor L (as step() for a contiguous block).  Returns |r|^2. */
+static double step_rows(int64_t n, const double *A, const double *b, const int64_t *S, int s, int cd,
+                        const double *L, double beta, double eta, double *x, double *mom, double *r, double *w) {
+    double rn2 = 0.0;
+    for (int a = 0; a < s; ++a) {
+        r[a] = dot(n, A + (size_t)S[a] * n, x) - b[S[a]];
+        rn2 += r[a] * r[a];
+    }
+    orc_chol_solve(s, L, r);
+    for (int64_t k = 0; k < n; ++k) w[k] = 0.0;
+    if (cd) {
+        for (int a = 0; a < s; ++a) w[S[a]] = r[a];
+    } else {
+        for (int a = 0; a < s; ++a) {
+            const double *row = A + (size_t)S[a] * n;
+            for (int64_t k = 0; k < n; ++k) w[k] += row[k] * r[a];
+        }
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        mom[k] = beta * (mom[k] - w[k]);
+        x[k] = x[k] - w[k] + eta * mom[k];
+    }
+    return rn2;
+}
+
+/* One step on a given subset (factor computed here): for the pins.  Returns ORC_OK or ORC_NOT_SPD. */
+int orc_step_subset(int64_t rows, int64_t n, const double *A, const double *b, const int64_t *S, int s, int cd,
+                    double lam, double beta, double eta, double *x, double *mom, double *rn2_out) {
+    (void)rows;
+    double *L = (double *)malloc(sizeof(double) * (size_t)s * s);
+    double *r = (double *)malloc(sizeof(double) * (size_t)s);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    int rc = subset_factor(n, A, S, s, cd, lam, L) ? ORC_NOT_SPD : ORC_OK;
+    if (rc == ORC_OK) *rn2_out = step_rows(n, A, b, S, s, cd, L, beta, eta, x, mom, r, w);
+    free(L);
+    free(r);
+    free(w);
+    return rc;
+}
+
+/* The solve with online memoisation: as orc_run, with the block of step t from the memo scheme.
+ * *nblocks_out receives |B| at return; blocks_out (optional, capacity cap) the memo index of each
+ * step (-1 never appears: a new block is recorded with its new index). */
+int orc_run_memo(int64_t rows, int64_t n, const double *A, const double *b, const orc_params *p, orc_state *st,
+                 double *x, double *mom, orc_report *rep, int64_t *nblocks_out, int64_t *blocks_out, int64_t cap) {
+    if (p->s <= 0 || p->s > rows || rows <= 0 || n <= 0 || (p->cd && rows != n)) return ORC_BAD_ARG;
+    const int s = p->s;
+    const int64_t zeta = nblocks(rows, s);
+    const double bn2 = dot(rows, b, b);
+    int64_t nb = 0, mcap = 64;
+    int64_t *Sset = (int64_t *)malloc(sizeof(int64_t) * (size_t)(mcap * s));
+    double *Lset = (double *)malloc(sizeof(double) * (size_t)(mcap * s * s));
+    double *r = (double *)malloc(sizeof(double) * (size_t)s);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    const int64_t it0 = st->t;
+    int status = ORC_NO_CONVERGENCE;
+    rep->rel_res_est = NAN;
+    while (st->t < p->max_iters) {
+        const int64_t t = st->t;
+        int64_t j = orc_memo_draw(p->seed, t, p->sys, p->cd, rows, n, s, nb);
+        if (j < 0) {
+            if (nb == mcap) {
+                mcap *= 2;
+                Sset = (int64_t *)realloc(Sset, sizeof(int64_t) * (size_t)(mcap * s));
+                Lset = (double *)realloc(Lset, sizeof(double) * (size_t)(mcap * s * s));
+            }
+            j = nb;
+            orc_memo_subset(p->seed, t, p->sys, rows, s, Sset + (size_t)j * s);
+            if (subset_factor(n, A, Sset + (size_t)j * s, s, p->cd, p->lam, Lset + (size_t)j * s * s)) {
+                status = ORC_NOT_SPD;
+                break;
+            }
+            ++nb;
+        }
+        if (blocks_out && t - it0 < cap) blocks_out[t - it0] = j;
+        const double beta = (1.0 - st->rho) / (1.0 + st->rho);
+        const double rn2 = step_rows(n, A, b, Sset + (size_t)j * s, s, p->cd, Lset + (size_t)j * s * s, beta,
+                                     p->eta, x, mom, r, w);
+        st->t = t + 1;
+        if ((t % (2 * zeta)) < zeta) st->E0 += rn2; else st->E1 += rn2;
+        if ((t % (2 * zeta)) == 2 * zeta - 1) {
+            st->ci += 1;
+            rep->rel_res_est = bn2 > 0.0 ? sqrt(st->E1 / bn2) : sqrt(st->E1);
+            if (p->tol > 0.0 && st->E1 <= p->tol * p->tol * bn2 &&
+                (!p->confirm || orc_rel_residual(rows, n, A, b, x) <= p->tol)) {
+                status = ORC_OK;
+                break;
+            }
+            if (p->adaptive) { /* Eq. 5.2 - 5.3, as in orc_run */
+                const double q = st->E0 > 0.0 ? st->E1 / st->E0 : 0.0;
+                if (st->ci == 1) {
+                    st->rhat = q;
+                } else {
+                    const double li = log((double)st->ci), li1 = log((double)st->ci + 1.0);
+                    const double wgt = exp(li * li - li1 * li1);
+                    st->rhat = wgt * st->rhat + (1.0 - wgt) * q;
+                }
+                double rho = 1.0 - pow(st->rhat, 1.0 / (double)zeta);
+                if (!(rho > 0.0)) rho = 0.0;
+                if (rho > 1.0 - 1e-12) rho = 1.0 - 1e-12;
+                st->rho = rho;
+            }
+            st->E0 = 0.0;
+            st->E1 = 0.0;
+        }
+    }
+    rep->iters = st->t - it0;
+    rep->rel_res_true = orc_rel_residual(rows, n, A, b, x);
+    rep->status = status;
+    *nblocks_out = nb;
+    free(Sset);
+    free(Lset);
+    free(r);
+    free(w);
+    return status;
+}

@@ -10,6 +10,9 @@ Paper: arXiv 2501.11673.  What pins what:
   * CD++ step            -> K++ on Phi with Phi Phi^T = A (Eq. 5.1 / the implicit form in the proof of Thm 5.1)
   * whole solves         -> x*, numpy.linalg.solve / lstsq / the min-norm solution; range invariance (Thm 2.1)
   * CG                   -> numpy.linalg.solve
+  * online memo (Sec. 4, 5.2) -> uniform s-subsets (inclusion and pair frequencies), the Bernoulli schedule's
+                            expected block count, the argmin / block-residual invariants on arbitrary
+                            subsets, convergence to the direct solution
   * Hadamard preprocessing (Sec. 5.1) -> scipy.linalg.hadamard (Sylvester construction); the spectrum and
                             the solution are invariant (Q orthogonal); the SymFHT operation count of its
                             theorem, n^2 (2.5 + log2 n), and the recursion's exact count
@@ -350,3 +353,95 @@ def test_symfht_returns_hah_within_its_operation_bound(n):
     L = int(round(math.log2(n)))
     assert ops == n * n * L + (3 * n * n - 3 * n) // 2
     assert ops <= n * n * (2.5 + L)
+
+
+# ---------------------------------------------------------------------------------------------
+# Online block memoisation with random subsets (Sec. 4 "Block memoization", Sec. 5.2)
+# ---------------------------------------------------------------------------------------------
+
+def test_memo_subsets_are_uniform_distinct_and_sorted():
+    """Floyd's sampling gives uniform s-subsets: every element is in a subset with probability s/N and
+    every pair with probability s(s-1)/(N(N-1))."""
+    N, s, T = 20, 5, 20000
+    inc = np.zeros(N)
+    pair01 = pair_end = 0
+    for t in range(T):
+        S = oracle.memo_subset(7, t, 3, N, s)
+        assert len(set(S.tolist())) == s and np.all(np.diff(S) > 0) and S[0] >= 0 and S[-1] < N
+        inc[S] += 1
+        ss = set(S.tolist())
+        pair01 += (0 in ss and 1 in ss)
+        pair_end += (N - 2 in ss and N - 1 in ss)
+    assert np.abs(inc / T - s / N).max() <= 0.02           # sd 0.003
+    p2 = s * (s - 1) / (N * (N - 1))
+    assert abs(pair01 / T - p2) <= 0.01 and abs(pair_end / T - p2) <= 0.01  # sd 0.0016
+
+
+def test_memo_bernoulli_schedule_and_expected_block_count():
+    """p_t = 1 while t <= (n/s) ln n, then (n/s) ln(n) / t (CD++), the K++ form takes the smaller of the
+    m and n terms; the number of memoised blocks after T steps is sum_t p_t (the paper's B (1 + ln(T/B)))
+    within four standard deviations."""
+    n, s = 256, 16
+    B = n / s * math.log(n)
+    assert oracle.memo_prob(True, n, n, s, 0) == 1.0
+    assert oracle.memo_prob(True, n, n, s, int(B)) == 1.0
+    assert abs(oracle.memo_prob(True, n, n, s, 1000) - B / 1000) <= 1e-15
+    m2 = 1000
+    assert abs(oracle.memo_prob(False, m2, 60, 20, 5000) - min(m2, 60) / 20 * math.log(m2) / 5000) <= 1e-15
+    T = 4000
+    A, b, _ = W.spd(n, 4, 1e1, 1e2, 1.0, 2.0, seed_A=1, seed_b=2)
+    res, nb, blocks = oracle.run_memo(A, b, s, cd=True, lam=1e-4, tol=0.0, max_iters=T, seed=11, block_cap=T)
+    ps = np.array([oracle.memo_prob(True, n, n, s, t) for t in range(T)])
+    mean, sd = ps.sum(), math.sqrt((ps * (1 - ps)).sum())
+    assert abs(nb - mean) <= 4 * sd + 1, (nb, mean, sd)
+    assert abs(mean - B * (1 + math.log(T / B))) <= 0.05 * mean
+    # the first ceil(B) steps all add a block, in order; later steps reuse a memoised one
+    k = int(math.ceil(B))
+    assert np.array_equal(blocks[:k], np.arange(k))
+    assert blocks.max() == nb - 1 and blocks.min() == 0
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_memo_subset_step_is_regularised_argmin(seed):
+    """K++ step on an arbitrary row subset (eta = 0, beta = 1): x+ minimises |z - x|^2 + |A_S z - b_S|^2 / lam,
+    solved through the n x n normal equations."""
+    rng = np.random.default_rng(seed)
+    m, n, lam = 40, 12, 0.3
+    A, b, x0 = rng.standard_normal((m, n)), rng.standard_normal(m), rng.standard_normal(n)
+    S = np.sort(rng.choice(m, 7, replace=False))
+    x, _, rn2 = oracle.step_subset(A, b, S, cd=False, lam=lam, x0=x0)
+    AS = A[S]
+    z = np.linalg.solve(np.eye(n) + AS.T @ AS / lam, x0 + AS.T @ b[S] / lam)
+    np.testing.assert_allclose(x, z, rtol=1e-12, atol=1e-12)
+    assert abs(rn2 - np.sum((AS @ x0 - b[S]) ** 2)) <= 1e-12 * rn2
+
+
+def test_memo_subset_cd_step_zeroes_the_block_residual():
+    """CD++ step on an arbitrary coordinate subset with lam = 0, eta = 0: (A x+ - b)_S = 0."""
+    n = 30
+    A, b, _ = W.spd(n, 3, 1e1, 1e2, 1.0, 2.0, seed_A=4, seed_b=5)
+    x0 = np.random.default_rng(6).standard_normal(n)
+    S = np.array([0, 3, 4, 17, 29])
+    x, _, _ = oracle.step_subset(A, b, S, cd=True, lam=0.0, x0=x0)
+    assert np.abs((A @ x - b)[S]).max() <= 1e-12 * np.abs(b).max()
+    others = np.setdiff1d(np.arange(n), S)
+    np.testing.assert_array_equal(x[others], x0[others])
+
+
+def test_memo_solves_converge_to_the_direct_solution():
+    """CD++ (SPD) and K++ (consistent least squares) with the online memo reach 1e-8 and the solution."""
+    n, s = 128, 16
+    A, b, sig = W.spd(n, 4, 1e1, 1e3, 1.0, 2.0, seed_A=8, seed_b=9)
+    res, nb, _ = oracle.run_memo(A, b, s, cd=True, lam=1e-4, tol=1e-8, max_iters=200000, seed=3)
+    assert res.status == oracle.OK and res.rel_res_true <= 1e-8
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) <= sig.max() / sig.min() * 1e-8
+    rng = np.random.default_rng(10)
+    m2, n2 = 400, 40
+    A2 = rng.standard_normal((m2, n2)) * np.concatenate([np.full(5, 20.0), np.ones(n2 - 5)])[None, :]
+    xstar = rng.standard_normal(n2)
+    b2 = A2 @ xstar
+    res2, nb2, _ = oracle.run_memo(A2, b2, 20, cd=False, lam=1e-3, tol=1e-8, max_iters=200000, seed=4)
+    assert res2.status == oracle.OK and res2.rel_res_true <= 1e-8
+    assert np.linalg.norm(res2.x - xstar) / np.linalg.norm(xstar) <= 1e-6
+    assert 0 < nb2 < res2.iters
