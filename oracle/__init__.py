@@ -16,6 +16,8 @@ Convergence" (arXiv 2501.11673).  Functions cite the passage they follow:
 * ``run_memo`` (with ``memo_prob``, ``memo_subset``, ``memo_draw``, ``step_subset``): K++ / CD++ with the
   online block memoisation over random s-subsets (Sec. 4 "Block memoization", Sec. 5.2, the sampling
   lines of Alg. 3 and Alg. 5), the readings for its random draws stated in kpp_oracle.c.
+* ``proj_precond`` / ``proj_lsqr``: the inexact projection by sketch-preconditioned LSQR (Sec. 4.1 and the
+  supplement's Proj algorithm) with the SRHT sketch; the signs and the column subset are inputs.
 * ``rht_forward`` / ``rht_inverse`` / ``rht_entry``: the randomized Hadamard preprocessing of CD++
   (Sec. 5.1, Alg. 3 lines 2-3 and its return D FHT(x)) from the definition Q = H_n D, written out
   with the explicit Sylvester-Hadamard entries.  ``fht`` / ``symfht``: the paper's recursive FHT and
@@ -121,6 +123,11 @@ def _load():
                                          ctypes.POINTER(_State), dp, dp, ctypes.POINTER(_Report), i64p, i64p,
                                          ctypes.c_int64]
             lib.orc_run_memo.restype = ctypes.c_int
+            lib.orc_proj_precond.argtypes = [ctypes.c_int64, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                             i64p, dp, dp]
+            lib.orc_proj_precond.restype = ctypes.c_int
+            lib.orc_proj_lsqr.argtypes = [ctypes.c_int64, dp, ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_int, dp]
+            lib.orc_proj_lsqr.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -393,3 +400,30 @@ def run_memo(A: np.ndarray, b: np.ndarray, s: int, *, cd: bool = False, lam: flo
     st = State(cst.t, cst.ci, cst.E0, cst.E1, cst.rhat, cst.rho)
     res = Result(x, mom, st, rep.iters, rep.rel_res_true, rep.rel_res_est, rep.status, np.zeros((0, 5)))
     return res, int(nb.value), blocks[:block_cap]
+
+
+# ----------------------------------------------------------------------------------------------
+# Inexact projection: sketch-preconditioned LSQR (Sec. 4.1; the supplement's Proj algorithm)
+# ----------------------------------------------------------------------------------------------
+
+def proj_precond(AS: np.ndarray, lam: float, T, d) -> np.ndarray:
+    """Lower L with L L^T = Ahat Ahat^T + lam I, Ahat = (A_S D H)[:, T] / sqrt(tau) (SRHT sketch; A_S padded
+    with zero columns to the next power of 2; d: that many signs)."""
+    AS = _f64(AS)
+    s, n = AS.shape
+    Tv = np.ascontiguousarray(T, dtype=np.int64)
+    L = np.empty((s, s))
+    rc = _load().orc_proj_precond(n, _dp(AS), s, lam, len(Tv), Tv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  _dp(_f64(d)), _dp(L))
+    if rc:
+        raise ValueError("sketched Gram not SPD")
+    return L
+
+
+def proj_lsqr(AS: np.ndarray, r: np.ndarray, lam: float, L: np.ndarray, t_max: int):
+    """(w, iterations): LSQR on L^{-1} [A_S, sqrt(lam) I] [w; v] = L^{-1} r from zero, the first n entries."""
+    AS = _f64(AS)
+    s, n = AS.shape
+    w = np.empty(n)
+    it = _load().orc_proj_lsqr(n, _dp(AS), s, _dp(_f64(r)), lam, _dp(_f64(L)), int(t_max), _dp(w))
+    return w, int(it)

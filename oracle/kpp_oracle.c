@@ -672,3 +672,137 @@ int orc_run_memo(int64_t rows, int64_t n, const double *A, const double *b, cons
     free(w);
     return status;
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Inexact projection by sketch-preconditioned LSQR (Sec. 4.1, "Computing the projection step", and
+ * the Proj algorithm of the supplement): w = argmin |A_S w - r|^2 + lam |w|^2 is the first n entries
+ * of the minimum-length solution of
+ *     M [w; v] = L^{-1} r,   M = L^{-1} [A_S, sqrt(lam) I],   L L^T = Ahat Ahat^T + lam I,
+ * with the sketch Ahat = A_S Pi^T of the subsampled randomized Hadamard transform
+ *     Pi = sqrt(n'/tau) I_T H_{n'} D / sqrt(n')   (n' = the power of 2 >= n, A_S padded with zero
+ * columns; D = diag(d), d_i = +-1; T a tau-subset of [0, n')),  i.e. Ahat = (A_S D H)[:, T] / sqrt(tau).
+ * The signs d and the subset T are inputs.  L is lower triangular (the paper's R = L^T).  LSQR is Paige
+ * and Saunders' bidiagonalisation method (ACM TOMS 8, 1982) from x = 0, t_max iterations.
+ * ------------------------------------------------------------------------------------------------ */
+static void lsolve_lower(int s, const double *L, double *y) { /* y <- L^{-1} y */
+    for (int i = 0; i < s; ++i) {
+        double v = y[i];
+        for (int k = 0; k < i; ++k) v -= L[(size_t)i * s + k] * y[k];
+        y[i] = v / L[(size_t)i * s + i];
+    }
+}
+static void lsolve_upper_t(int s, const double *L, double *y) { /* y <- L^{-T} y */
+    for (int i = s - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < s; ++k) v -= L[(size_t)k * s + i] * y[k];
+        y[i] = v / L[(size_t)i * s + i];
+    }
+}
+
+/* The preconditioner L (s x s lower) from the SRHT sketch; returns 0 or ORC_NOT_SPD. */
+int orc_proj_precond(int64_t n, const double *AS, int s, double lam, int64_t tau, const int64_t *T,
+                     const double *d, double *L) {
+    int64_t np2 = 1;
+    while (np2 < n) np2 *= 2;
+    double *row = (double *)malloc(sizeof(double) * (size_t)np2);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)np2);
+    double *Ah = (double *)malloc(sizeof(double) * (size_t)(s * tau));
+    int64_t ops = 0;
+    for (int a = 0; a < s; ++a) {
+        for (int64_t k = 0; k < np2; ++k) row[k] = k < n ? AS[(size_t)a * n + k] * d[k] : 0.0;
+        fht_vec(np2, row, 1, tmp, &ops);
+        for (int64_t q = 0; q < tau; ++q) Ah[(size_t)a * tau + q] = row[T[q]] / sqrt((double)tau);
+    }
+    for (int a = 0; a < s; ++a)
+        for (int c = 0; c < s; ++c)
+            L[(size_t)a * s + c] = dot(tau, Ah + (size_t)a * tau, Ah + (size_t)c * tau) + (a == c ? lam : 0.0);
+    const int rc = orc_cholesky(s, L) ? ORC_NOT_SPD : ORC_OK;
+    free(row);
+    free(tmp);
+    free(Ah);
+    return rc;
+}
+
+/* w (n) from t_max LSQR iterations on the preconditioned system; returns the iterations taken. */
+int orc_proj_lsqr(int64_t n, const double *AS, int s, const double *r, double lam, const double *L, int t_max,
+                  double *w) {
+    const int64_t N = n + s; /* unknowns [w; v] */
+    const double sl = sqrt(lam);
+    double *u = (double *)malloc(sizeof(double) * (size_t)s);
+    double *z = (double *)malloc(sizeof(double) * (size_t)s);
+    double *v = (double *)malloc(sizeof(double) * (size_t)N);
+    double *wd = (double *)malloc(sizeof(double) * (size_t)N);
+    double *x = (double *)calloc((size_t)N, sizeof(double));
+    /* u = M v_in  (s):  L^{-1} (A_S v[0:n] + sqrt(lam) v[n:]) */
+#define ORC_MV(out, in)                                                                   \
+    do {                                                                                  \
+        for (int a_ = 0; a_ < s; ++a_)                                                    \
+            (out)[a_] = dot(n, AS + (size_t)a_ * n, (in)) + sl * (in)[n + a_];           \
+        lsolve_lower(s, L, (out));                                                        \
+    } while (0)
+    /* v_out = M^T u_in (N):  z = L^{-T} u;  [A_S^T z; sqrt(lam) z] */
+#define ORC_MTV(out, in)                                                                  \
+    do {                                                                                  \
+        for (int a_ = 0; a_ < s; ++a_) z[a_] = (in)[a_];                                  \
+        lsolve_upper_t(s, L, z);                                                          \
+        for (int64_t k_ = 0; k_ < n; ++k_) {                                              \
+            double acc_ = 0.0;                                                            \
+            for (int a_ = 0; a_ < s; ++a_) acc_ += AS[(size_t)a_ * n + k_] * z[a_];       \
+            (out)[k_] = acc_;                                                             \
+        }                                                                                 \
+        for (int a_ = 0; a_ < s; ++a_) (out)[n + a_] = sl * z[a_];                        \
+    } while (0)
+    for (int a = 0; a < s; ++a) u[a] = r[a];
+    lsolve_lower(s, L, u); /* c = L^{-1} r */
+    double beta = sqrt(dot(s, u, u));
+    int it = 0;
+    if (beta > 0.0) {
+        for (int a = 0; a < s; ++a) u[a] /= beta;
+        ORC_MTV(v, u);
+        double alpha = sqrt(dot(N, v, v));
+        if (alpha > 0.0) {
+            for (int64_t k = 0; k < N; ++k) v[k] /= alpha;
+            for (int64_t k = 0; k < N; ++k) wd[k] = v[k];
+            double phibar = beta, rhobar = alpha;
+            double *Mv = (double *)malloc(sizeof(double) * (size_t)s);
+            double *Mtu = (double *)malloc(sizeof(double) * (size_t)N);
+            for (it = 0; it < t_max; ++it) {
+                ORC_MV(Mv, v);
+                for (int a = 0; a < s; ++a) u[a] = Mv[a] - alpha * u[a];
+                beta = sqrt(dot(s, u, u));
+                if (beta > 0.0)
+                    for (int a = 0; a < s; ++a) u[a] /= beta;
+                ORC_MTV(Mtu, u);
+                for (int64_t k = 0; k < N; ++k) Mtu[k] -= beta * v[k];
+                alpha = sqrt(dot(N, Mtu, Mtu));
+                if (alpha > 0.0)
+                    for (int64_t k = 0; k < N; ++k) v[k] = Mtu[k] / alpha;
+                const double rho = sqrt(rhobar * rhobar + beta * beta);
+                const double c = rhobar / rho, sn = beta / rho;
+                const double theta = sn * alpha;
+                rhobar = -c * alpha;
+                const double phi = c * phibar;
+                phibar = sn * phibar;
+                for (int64_t k = 0; k < N; ++k) {
+                    x[k] += (phi / rho) * wd[k];
+                    wd[k] = v[k] - (theta / rho) * wd[k];
+                }
+                if (beta == 0.0 || alpha == 0.0) {
+                    ++it;
+                    break;
+                }
+            }
+            free(Mv);
+            free(Mtu);
+        }
+    }
+#undef ORC_MV
+#undef ORC_MTV
+    for (int64_t k = 0; k < n; ++k) w[k] = x[k];
+    free(u);
+    free(z);
+    free(v);
+    free(wd);
+    free(x);
+    return it;
+}

@@ -13,6 +13,8 @@ Paper: arXiv 2501.11673.  What pins what:
   * online memo (Sec. 4, 5.2) -> uniform s-subsets (inclusion and pair frequencies), the Bernoulli schedule's
                             expected block count, the argmin / block-residual invariants on arbitrary
                             subsets, convergence to the direct solution
+  * LSQR projection (Sec. 4.1) -> the regularised argmin (normal equations); one iteration when the sketch is
+                            the whole (orthogonal) transform; the preconditioned condition number against tau
   * Hadamard preprocessing (Sec. 5.1) -> scipy.linalg.hadamard (Sylvester construction); the spectrum and
                             the solution are invariant (Q orthogonal); the SymFHT operation count of its
                             theorem, n^2 (2.5 + log2 n), and the recursion's exact count
@@ -445,3 +447,62 @@ def test_memo_solves_converge_to_the_direct_solution():
     assert res2.status == oracle.OK and res2.rel_res_true <= 1e-8
     assert np.linalg.norm(res2.x - xstar) / np.linalg.norm(xstar) <= 1e-6
     assert 0 < nb2 < res2.iters
+
+
+# ---------------------------------------------------------------------------------------------
+# Inexact projection by sketch-preconditioned LSQR (Sec. 4.1; the supplement's Proj algorithm)
+# ---------------------------------------------------------------------------------------------
+
+def _proj_case(s, n, lam, seed):
+    rng = np.random.default_rng(seed)
+    AS = rng.standard_normal((s, n)) * np.linspace(10.0, 0.1, s)[:, None]
+    r = rng.standard_normal(s)
+    w_star = np.linalg.solve(np.eye(n) * lam + AS.T @ AS, AS.T @ r)  # argmin |A_S w - r|^2 + lam |w|^2
+    return AS, r, w_star
+
+
+def test_proj_lsqr_with_the_whole_transform_is_exact_in_one_iteration():
+    """tau = n (a power of 2), T = everything: Ahat Ahat^T = A_S A_S^T, the preconditioned operator has
+    orthonormal rows, and one LSQR iteration returns the projection."""
+    s, n, lam = 16, 128, 0.7
+    AS, r, w_star = _proj_case(s, n, lam, 1)
+    L = oracle.proj_precond(AS, lam, np.arange(n), W.rademacher_signs(n, 2))
+    np.testing.assert_allclose(L @ L.T, AS @ AS.T + lam * np.eye(s), rtol=1e-12, atol=1e-10)
+    w, it = oracle.proj_lsqr(AS, r, lam, L, 1)
+    assert it == 1
+    assert np.linalg.norm(w - w_star) <= 1e-12 * np.linalg.norm(w_star)
+
+
+def test_proj_lsqr_converges_monotonically_to_the_regularised_projection():
+    """tau = 2 s (the supplement's choice), n not a power of 2 (zero padding): the error to the argmin
+    falls monotonically and reaches rounding level."""
+    s, n, lam = 32, 300, 0.05
+    AS, r, w_star = _proj_case(s, n, lam, 3)
+    d = W.rademacher_signs(512, 4)
+    T = np.sort(np.random.default_rng(5).choice(512, 2 * s, replace=False))
+    L = oracle.proj_precond(AS, lam, T, d)
+    errs = [np.linalg.norm(oracle.proj_lsqr(AS, r, lam, L, t)[0] - w_star) / np.linalg.norm(w_star)
+            for t in range(1, 13)]
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(errs, errs[1:]))
+    w, _ = oracle.proj_lsqr(AS, r, lam, L, 3 * s)
+    assert np.linalg.norm(w - w_star) <= 1e-10 * np.linalg.norm(w_star)
+
+
+def test_proj_preconditioned_condition_number_shrinks_with_the_sketch():
+    """kappa(L^{-1} [A_S, sqrt(lam) I]) is 1 for the whole transform and, averaged over draws, smaller for
+    a sketch of 8 s columns than for one of s columns; at 2 s it is a small constant."""
+    s, n, lam = 24, 256, 0.01
+    AS, _, _ = _proj_case(s, n, lam, 6)
+    Mfull = np.hstack([AS, math.sqrt(lam) * np.eye(s)])
+
+    def kappa(T, seed):
+        L = oracle.proj_precond(AS, lam, T, W.rademacher_signs(n, seed))
+        sv = np.linalg.svd(np.linalg.solve(L, Mfull), compute_uv=False)
+        return sv[0] / sv[-1]
+
+    assert abs(kappa(np.arange(n), 7) - 1.0) <= 1e-9
+    rng = np.random.default_rng(8)
+    ks = {tau: np.mean([kappa(np.sort(rng.choice(n, tau, replace=False)), 10 + i) for i in range(5)])
+          for tau in (s, 2 * s, 8 * s)}
+    assert ks[8 * s] < ks[s]
+    assert ks[2 * s] <= 10.0
