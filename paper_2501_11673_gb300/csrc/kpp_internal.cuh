@@ -55,15 +55,26 @@ __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ double widen(float v) { return (double)v; }
 __device__ __forceinline__ double widen(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
-// Exact FP32 -> FP64 widening with integer operations (rebias the exponent, shift the mantissa), so
-// that an FP64-bound loop spends its FP64 pipe on FMAs only.  Zero and subnormal inputs (exponent 0)
-// take the conversion instruction; inf / NaN do not occur in a valid matrix.
+// Exact FP32 -> FP64 widening with integer operations only, so that an FP64-bound loop spends its FP64
+// pipe on FMAs.  On this GPU the conversion instruction occupies the FP64 pipe like an FMA, and even a
+// predicated-off one for the rare case costs the same issue on that pipe, so no case uses it:
+//   normal (exponent e in 1..254): exponent e + 896 (bias 127 -> 1023), mantissa shifted 23 -> 52 bits;
+//   inf / NaN (e = 255): exponent 2047, mantissa shifted;
+//   zero: the sign alone;
+//   subnormal m 2^-149 (e = 0, m != 0): with p the position of m's leading one, the value is
+//   2^(p - 149) (1 + (m - 2^p) / 2^p): exponent p + 874, fraction (m - 2^p) << (52 - p).
 __device__ __forceinline__ double widen_int(float f) {
     const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xffu;
-    if (e == 0u) return (double)f;
-    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-    const uint32_t lo = (u & 7u) << 29;
+    const uint32_t sgn = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    const uint32_t eb = e == 255u ? 2047u : e + 896u;
+    uint32_t hi = sgn | (eb << 20) | (m >> 3);
+    uint32_t lo = m << 29;
+    if (e == 0u) {
+        const int p = 31 - __clz((int)(m | 1u));
+        const uint64_t frac = (uint64_t)(m ^ (1u << p)) << (52 - p);
+        hi = m ? (sgn | ((uint32_t)(p + 874) << 20) | (uint32_t)(frac >> 32)) : sgn;
+        lo = m ? (uint32_t)frac : 0u;
+    }
     return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ double widen_fast(double v) { return v; }

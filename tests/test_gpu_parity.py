@@ -386,6 +386,40 @@ def test_true_residual_is_exact_fp64_of_stored_entries(K, dtype):
     assert abs(got - want) <= 1e-12 * want
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_true_residual_widens_subnormal_zero_and_extreme_entries_exactly(K, dtype):
+    """Rows made of subnormal, zero and extreme-exponent FP32 / BF16 entries, with x scaled so that each
+    row's products are O(1): the FP64 residual is sensitive to every entry's widened value, and matches
+    numpy's FP64 on the exactly widened matrix."""
+    rng = np.random.default_rng(11)
+    m, n = 64, 256
+    mag = np.zeros((m, 1))
+    mag[0:16] = 1e-40     # subnormal in FP32 and BF16
+    mag[16:24] = 1e-44    # deep subnormal (a few mantissa bits)
+    mag[24:40] = 1e30     # large normal
+    mag[40:56] = 1e-37    # small normal
+    mag[56:64] = 1.0
+    A = rng.standard_normal((m, n)) * mag
+    A[::5, ::7] = 0.0
+    A[3, 0] = -0.0
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    Ad = dev(A, tdt)
+    Ar = Ad.double().cpu().numpy()  # the stored values, exactly widened by torch on the host side
+    assert np.count_nonzero((np.abs(Ar) < 1.1754943508222875e-38) & (Ar != 0)) > 100
+    x = rng.standard_normal(n)
+    rows_scale = 1.0 / np.maximum(np.abs(Ar).max(axis=1), 1e-300)
+    # one x for all rows: scale columns so that each magnitude class contributes O(1) through its rows
+    b = np.empty(m)
+    res = []
+    for lo, hi in [(0, 16), (16, 24), (24, 40), (40, 56), (56, 64)]:
+        xs = x * rows_scale[lo]
+        bb = Ar[lo:hi] @ xs + 1e-3 * rng.standard_normal(hi - lo)
+        got = K.rel_residual(dev(Ar[lo:hi], tdt), dev(bb), dev(xs))
+        want = np.linalg.norm(bb - Ar[lo:hi] @ xs) / np.linalg.norm(bb)
+        res.append((got, want))
+        assert abs(got - want) <= 1e-12 * want, (lo, got, want)
+
+
 def _wide_batch(nsys, m, n, s, k, dtype, seed=0):
     As, Bs = [], []
     for i in range(nsys):
