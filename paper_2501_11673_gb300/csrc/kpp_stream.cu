@@ -49,10 +49,6 @@ struct alignas(128) Sys4 {
     int64_t t0;
 };
 
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
 template <typename TA>
 __host__ __device__ constexpr int st_tk() { return ST_ROWB / (int)sizeof(TA); }
 
