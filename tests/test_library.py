@@ -80,3 +80,21 @@ def test_plan_handles_and_tune_cache_on_the_host(lib, tmp_path):
     assert kpp.tune_cache_size() == 0
     with pytest.raises(kpp.KppError):
         kpp.tune_cache_load(tmp_path / "missing.txt")
+
+
+def test_hadamard_entry_points_refuse_bad_arguments_on_the_host(lib):
+    """kpp_rht_forward / kpp_rht_inverse check sizes, dtype and pointers before any device work."""
+    m = kpp.Matrix(ctypes.c_void_p(16), kpp.KPP_F64, 0, 8, 8, 8)
+    vp = ctypes.c_void_p
+    for n in (0, 6, 12, 1 << 15):  # not a power of 2, or above 16384
+        assert lib.kpp_rht_forward(n, vp(16), ctypes.byref(m), vp(16), None, None, 0, None) == kpp.ERR_ARG
+        assert "power of 2" in kpp.last_error()
+    m6 = kpp.Matrix(ctypes.c_void_p(16), kpp.KPP_F64, 0, 4, 8, 8)  # rows != n
+    assert lib.kpp_rht_forward(8, vp(16), ctypes.byref(m6), vp(16), None, None, 0, None) == kpp.ERR_ARG
+    m32 = kpp.Matrix(ctypes.c_void_p(16), kpp.KPP_F32, 0, 8, 8, 8)  # not FP64
+    assert lib.kpp_rht_forward(8, vp(16), ctypes.byref(m32), vp(16), None, None, 0, None) == kpp.ERR_ARG
+    assert lib.kpp_rht_forward(8, None, ctypes.byref(m), vp(16), None, None, 0, None) == kpp.ERR_ARG
+    assert lib.kpp_rht_forward(8, vp(16), ctypes.byref(m), vp(16), None, None, 2, None) == kpp.ERR_ARG  # k > 0, no b
+    assert lib.kpp_rht_inverse(8, vp(16), vp(16), vp(16), 0, None) == kpp.ERR_ARG                   # k < 1
+    assert lib.kpp_rht_inverse(6, vp(16), vp(16), vp(16), 1, None) == kpp.ERR_ARG
+    assert lib.kpp_rht_inverse(8, vp(16), None, vp(16), 1, None) == kpp.ERR_ARG
