@@ -244,6 +244,25 @@ kpp_status kpp_rht_forward(int64_t n, const double *d, const kpp_matrix *A, doub
  * k >= 1); x may equal xbar.  Errors: KPP_ERR_ARG, KPP_ERR_CUDA.  Stream-ordered. */
 kpp_status kpp_rht_inverse(int64_t n, const double *d, const double *xbar, double *x, int32_t k, void *stream);
 
+/* The block sequence of the online block memoisation (Sec. 4, "Block memoization"; Sec. 5.2; the
+ * sampling lines of Alg. 3 and Alg. 5) for steps t0 .. t0 + count - 1 of Philox stream sys_id, with nb0
+ * blocks memoised before t0.  Step t samples a new uniformly random s-subset of the rows with
+ * probability p_0 = 1, p_t = min(1, (n/s) ln(n) / t) (mode 1, CD++) or min(1, (m/s) ln(m) / t,
+ * (n/s) ln(m) / t) (mode 0, K++), and otherwise reuses a memoised block picked uniformly.  The draws:
+ * Philox4x32-10, key {seed_lo, seed_hi}; counter {t_lo, t_hi, sys_id, 0}: out[1] < p_t 2^32 means new,
+ * out[2] |B| >> 32 is the pick; counter {t_lo, t_hi, sys_id, 1 + i/4}: word i mod 4 of Floyd's sampling
+ * of the subset, which is returned sorted.  The sequence does not depend on the data, so a window can
+ * be drawn before its steps run.
+ * blocks (host, count entries): the memo index each step uses; a new block takes the next index
+ * (nb0, nb0 + 1, ...).  subsets (host, subsets_cap x s): the new blocks' row indices, in order.
+ * *nb_out: the number of memoised blocks after the window.  rows, cols: the shape of A (CD++: square).
+ * Host only: no device memory and no stream.  Errors: KPP_ERR_ARG for an invalid argument, or when
+ * the window draws more than subsets_cap new blocks (subsets_cap >= count always suffices; *nb_out
+ * then holds the count reached). */
+kpp_status kpp_memo_sequence(uint64_t seed, uint32_t sys_id, int32_t mode, int64_t rows, int64_t cols, int32_t s,
+                             int64_t t0, int64_t count, int64_t nb0, int64_t *blocks, int64_t *subsets,
+                             int64_t subsets_cap, int64_t *nb_out);
+
 /* Select the solve kernel for later calls in this process.  All variants compute the same iteration.
  *   3 (default): CD++ uses the dataflow kernel (no per-step barrier: the owners of the next block
  *     hand r over through a tagged mailbox; FP64 streams the memoised W_j = G_j^{-1} A_{S_j}); K++ uses

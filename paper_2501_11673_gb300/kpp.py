@@ -35,7 +35,8 @@ EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_par
            "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_reset_stats", "kpp_server_destroy",
            "cdpp_solve_batched", "kpp_plan_create", "kpp_plan_launch", "kpp_plan_report", "kpp_plan_info",
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
-           "kpp_tune_cache_load", "kpp_launch_count", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse"]
+           "kpp_tune_cache_load", "kpp_launch_count", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
+           "kpp_memo_sequence"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
 
@@ -137,6 +138,10 @@ def load(path: str | None = None):
         lib.kpp_rht_forward.restype = ctypes.c_int
         lib.kpp_rht_inverse.argtypes = [i64, vp, vp, vp, i32, vp]
         lib.kpp_rht_inverse.restype = ctypes.c_int
+        i64p = ctypes.POINTER(i64)
+        lib.kpp_memo_sequence.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i32, i64, i64, i32, i64, i64, i64, i64p,
+                                          i64p, i64, i64p]
+        lib.kpp_memo_sequence.restype = ctypes.c_int
         for name in ("kpp_set_kernel_variant", "cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
                      "kpp_solve_host", "kpp_rel_residual", "kpp_solve_batched"):
             getattr(lib, name).restype = ctypes.c_int
@@ -432,6 +437,19 @@ def block_gram(A, s: int, lam: float, engine: int = 0, stream=None):
     _check(load().kpp_block_gram(ctypes.byref(m), int(s), float(lam), int(engine), ctypes.c_void_p(G.data_ptr()),
                                  ctypes.byref(used), _stream_ptr(stream)))
     return G, used.value
+
+
+def memo_sequence(seed: int, sys_id: int, cd: bool, rows: int, cols: int, s: int, t0: int, count: int, nb0: int = 0):
+    """The online memo's block sequence for steps t0 .. t0+count-1 (kpp_memo_sequence): (memo index per
+    step, the new blocks' row subsets (new x s), number of memoised blocks after the window)."""
+    import numpy as np
+    blocks = np.empty(max(count, 1), dtype=np.int64)
+    subsets = np.empty((max(count, 1), s), dtype=np.int64)
+    nb = ctypes.c_int64()
+    p = ctypes.POINTER(ctypes.c_int64)
+    _check(load().kpp_memo_sequence(seed, sys_id, int(cd), rows, cols, s, t0, count, nb0,
+                                    blocks.ctypes.data_as(p), subsets.ctypes.data_as(p), count, ctypes.byref(nb)))
+    return blocks[:count], subsets[: nb.value - nb0], nb.value
 
 
 def rht_forward(d, A, b=None, stream=None):

@@ -6,6 +6,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2501_11673_gb300 import build as kbuild
@@ -98,3 +99,45 @@ def test_hadamard_entry_points_refuse_bad_arguments_on_the_host(lib):
     assert lib.kpp_rht_inverse(8, vp(16), vp(16), vp(16), 0, None) == kpp.ERR_ARG                   # k < 1
     assert lib.kpp_rht_inverse(6, vp(16), vp(16), vp(16), 1, None) == kpp.ERR_ARG
     assert lib.kpp_rht_inverse(8, vp(16), None, vp(16), 1, None) == kpp.ERR_ARG
+
+
+def _oracle_memo_sequence(seed, sys_id, cd, rows, cols, s, t0, count, nb0):
+    import oracle
+    nb, blocks, subsets = nb0, [], []
+    for t in range(t0, t0 + count):
+        j = oracle.memo_draw(seed, t, sys_id, cd, rows, cols, s, nb)
+        if j < 0:
+            subsets.append(oracle.memo_subset(seed, t, sys_id, rows, s))
+            j, nb = nb, nb + 1
+        blocks.append(j)
+    return blocks, subsets, nb
+
+
+@pytest.mark.parametrize("cd,rows,cols,s,seed,sys_id", [(True, 256, 256, 16, 11, 0), (True, 4096, 4096, 64, 1, 3),
+                                                        (False, 2000, 200, 20, 0, 5), (False, 500, 900, 7, 2**63 + 9, 1)])
+def test_memo_sequence_matches_the_oracle_draws(lib, cd, rows, cols, s, seed, sys_id):
+    """The library's host draw of the memo block sequence (kpp_memo_sequence) equals the oracle's, step by
+    step and subset by subset (integer results: bitwise), and a window split in two gives the same
+    sequence as one window."""
+    T = 3000
+    blocks, subsets, nb = kpp.memo_sequence(seed, sys_id, cd, rows, cols, s, 0, T)
+    ob, osub, onb = _oracle_memo_sequence(seed, sys_id, cd, rows, cols, s, 0, T, 0)
+    assert nb == onb and blocks.tolist() == ob
+    assert len(subsets) == len(osub) and all((a == b).all() for a, b in zip(subsets, osub))
+    b1, s1, nb1 = kpp.memo_sequence(seed, sys_id, cd, rows, cols, s, 0, 1234)
+    b2, s2, nb2 = kpp.memo_sequence(seed, sys_id, cd, rows, cols, s, 1234, T - 1234, nb1)
+    assert nb2 == nb and (np.concatenate([b1, b2]) == blocks).all()
+    assert (np.concatenate([s1, s2]) == subsets).all()
+
+
+def test_memo_sequence_refuses_bad_arguments(lib):
+    nb = ctypes.c_int64()
+    p = ctypes.POINTER(ctypes.c_int64)
+    buf = np.zeros(64, dtype=np.int64)
+    args = lambda mode, rows, cols, s, count, cap: (1, 0, mode, rows, cols, s, 0, count, 0, buf.ctypes.data_as(p),
+                                                    buf.ctypes.data_as(p), cap, ctypes.byref(nb))
+    assert lib.kpp_memo_sequence(*args(2, 10, 10, 2, 4, 4)) == kpp.ERR_ARG   # mode
+    assert lib.kpp_memo_sequence(*args(1, 10, 12, 2, 4, 4)) == kpp.ERR_ARG   # CD++ needs a square matrix
+    assert lib.kpp_memo_sequence(*args(0, 10, 12, 11, 4, 4)) == kpp.ERR_ARG  # s > rows
+    assert lib.kpp_memo_sequence(*args(0, 10, 12, 2, 4, 1)) == kpp.ERR_ARG   # steps 0, 1 both draw new blocks
+    assert nb.value == 1 and "subsets_cap" in kpp.last_error()
