@@ -9,7 +9,7 @@
  *      CD++ (Eq. 5.1), applied through a per-block factor memoised once (Sec. 4, Sec. 5.2);
  *   4. w = A_S^T y (CD++: w = I_S^T y), m <- (1-rho)/(1+rho) (m - w), x <- x - w + eta m (Eq. 1.4);
  *   5. residual estimate, adaptive rho and the stopping rule every 2 zeta steps (Eq. 5.2, Eq. 5.3,
- *      Alg. 3 lines 14-20, Alg. 5 lines 13-19), confirmed by the true FP64 residual |Ax - b|/|b|.
+ *      the checkpoints of Alg. 3 and Alg. 5), confirmed by the true FP64 residual |Ax - b|/|b|.
  *
  * Conventions shared by every entry point:
  *   - Matrices are row-major with a leading dimension `ld` (elements).  A `kpp_matrix` names memory
@@ -68,7 +68,7 @@ typedef struct kpp_factors_s *kpp_factors_t;
 /* Solver parameters.  Fill with kpp_params_default() and override fields as needed. */
 typedef struct {
     double lambda;         /* Tikhonov regulariser (Eq. 1.3); must equal the factors' lambda */
-    double tol;            /* eps: stop when |Ax-b|/|b| <= eps (Alg. 3 line 16) */
+    double tol;            /* eps: stop when |Ax-b|/|b| <= eps (Alg. 3's stop test) */
     int64_t max_iters;     /* cap on block iterations (per inner solve when refining) */
     uint64_t seed;         /* Philox key */
     uint32_t sys_id;       /* Philox stream id (system / request index) */
@@ -109,7 +109,7 @@ const char *kpp_status_string(kpp_status st);
 const char *kpp_last_error(void);
 
 /* Fixed contiguous partition of `rows` rows into blocks of `s` rows: the block collection B of
- * Alg. 1 line 4, held fixed so that every block's factor is memoised up front (Sec. 4).  The last
+ * Alg. 1, held fixed so that every block's factor is memoised up front (Sec. 4).  The last
  * block holds rows mod s rows when s does not divide rows.  Errors: KPP_ERR_ARG if rows < 1, s < 1
  * or s > 1024.  Host-only; no device memory is used.  Free with kpp_partition_destroy. */
 kpp_status kpp_partition(int64_t rows, int32_t s, kpp_partition_t *out);
@@ -117,7 +117,7 @@ void kpp_partition_destroy(kpp_partition_t p);
 /* Number of blocks nb = ceil(rows / s) of a partition (0 for a null handle). */
 int64_t kpp_partition_blocks(kpp_partition_t p);
 
-/* Memoised per-block factors (Sec. 4; Sec. 5.2; Alg. 1 line 7; Alg. 3 line 8).
+/* Memoised per-block factors (Sec. 4; Sec. 5.2; Alg. 1; Alg. 3).
  *   mode 0 (K++):  G_j = A_{S_j} A_{S_j}^T + lambda I  (the block Gram; for F32/BF16 storage it is
  *                  built on the tensor cores with FP32 accumulation, then widened to FP64);
  *   mode 1 (CD++): G_j = A_{S_j S_j} + lambda I  (the principal block; A must be square and symmetric).
@@ -168,7 +168,7 @@ kpp_status kpp_solve_host(const kpp_matrix *A_host, const double *b_host, double
                           int32_t mode, const kpp_params *p, kpp_report *rep, void *stream);
 
 /* |A x - b|_2 / |b|_2 with FP64 accumulation (stored entries widened exactly) -- the stopping
- * rule's confirmation (Alg. 3 line 16).  A, b, x: device.  Result to *out_host.  Synchronises. */
+ * rule's confirmation (Alg. 3).  A, b, x: device.  Result to *out_host.  Synchronises. */
 kpp_status kpp_rel_residual(const kpp_matrix *A, const double *b, const double *x, double *out_host,
                             void *stream);
 
@@ -245,7 +245,7 @@ kpp_status kpp_rht_forward(int64_t n, const double *d, const kpp_matrix *A, doub
 kpp_status kpp_rht_inverse(int64_t n, const double *d, const double *xbar, double *x, int32_t k, void *stream);
 
 /* The block sequence of the online block memoisation (Sec. 4, "Block memoization"; Sec. 5.2; the
- * sampling lines of Alg. 3 and Alg. 5) for steps t0 .. t0 + count - 1 of Philox stream sys_id, with nb0
+ * sampling steps of Alg. 3 and Alg. 5) for steps t0 .. t0 + count - 1 of Philox stream sys_id, with nb0
  * blocks memoised before t0.  Step t samples a new uniformly random s-subset of the rows with
  * probability p_0 = 1, p_t = min(1, (n/s) ln(n) / t) (mode 1, CD++) or min(1, (m/s) ln(m) / t,
  * (n/s) ln(m) / t) (mode 0, K++), and otherwise reuses a memoised block picked uniformly.  The draws:

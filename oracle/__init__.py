@@ -9,24 +9,25 @@ Paper: Derezinski, Needell, Rebrova, Yang, "Randomized Kaczmarz Methods with Bey
 Convergence" (arXiv 2501.11673).  Functions cite the passage they follow:
 
 * ``kpp_factor`` / ``cdpp_factor``: memoised Cholesky factor per block (Sec. 4, Sec. 5.2).
-* ``run``: the K++ iteration (Alg. 1 lines 6-11 with exact Cholesky projection, i.e. the
+* ``run``: the K++ iteration (Alg. 1's loop with exact Cholesky projection, i.e. the
   ``K++(Cholesky)`` variant of App. F; Alg. 5's adaptive rho and stopping rule) and the CD++
-  iteration (Eq. 5.1, Alg. 3 lines 10-20), both without the randomized Hadamard preprocessing.
+  iteration (Eq. 5.1, Alg. 3's loop), both without the randomized Hadamard preprocessing.
 * ``cg``: plain conjugate gradients (context, Sec. 6).
 * ``run_memo`` (with ``memo_prob``, ``memo_subset``, ``memo_draw``, ``step_subset``): K++ / CD++ with the
   online block memoisation over random s-subsets (Sec. 4 "Block memoization", Sec. 5.2, the sampling
-  lines of Alg. 3 and Alg. 5), the readings for its random draws stated in kpp_oracle.c.
+  steps of Alg. 3 and Alg. 5), the readings for its random draws stated in kpp_oracle.c.
 * ``proj_precond`` / ``proj_lsqr``: the inexact projection by sketch-preconditioned LSQR (Sec. 4.1 and the
   supplement's Proj algorithm) with the SRHT sketch; the signs and the column subset are inputs.
 * ``rht_forward`` / ``rht_inverse`` / ``rht_entry``: the randomized Hadamard preprocessing of CD++
-  (Sec. 5.1, Alg. 3 lines 2-3 and its return D FHT(x)) from the definition Q = H_n D, written out
+  (Sec. 5.1, the preprocessing of Alg. 3 and its return D FHT(x)) from the definition Q = H_n D, written out
   with the explicit Sylvester-Hadamard entries.  ``fht`` / ``symfht``: the paper's recursive FHT and
   SymFHT (App. on the symmetric fast Hadamard transform), with their operation counts.
 * ``philox4x32_10`` / ``sample_block``: Philox4x32-10 of Salmon et al. (SC'11).
 
-Parity of the adaptive-rho schedule and of the stopping rule is unpinned by the paper (it prints no
-worked values); they are pinned only by lockstep agreement with the CUDA path under the stated
-readings.
+The adaptive-rho schedule and the stopping rule have no worked values in the paper.  They are pinned
+instead by closed forms: on diagonal systems with the momentum off, every windowed residual sum, every
+ratio, the weighted mean of Eq. 5.3, each rho and the stop iteration follow from the per-entry decay
+factors alone (tests/test_oracle.py).
 """
 from __future__ import annotations
 
@@ -250,8 +251,8 @@ def run(A: np.ndarray, b: np.ndarray, L: np.ndarray, s: int, *, cd: bool = False
         state: State | None = None, trace_cap: int = 4096) -> Result:
     """Run K++ (cd=False) or CD++ (cd=True) iterations from a state until the stop rule or max_iters.
 
-    K++ step: Eq. 1.3 with the memoised factor L (Alg. 1 lines 6-10); CD++ step: Eq. 5.1.
-    Adaptive rho, residual estimate and stop: Eq. 5.2, Eq. 5.3, Alg. 3 lines 14-20 / Alg. 5 lines 13-19.
+    K++ step: Eq. 1.3 with the memoised factor L (Alg. 1); CD++ step: Eq. 5.1.
+    Adaptive rho, residual estimate and stop: Eq. 5.2, Eq. 5.3, the checkpoints of Alg. 3 / Alg. 5.
     """
     lib = _load()
     A = _f64(A)
@@ -343,7 +344,7 @@ def symfht(A: np.ndarray):
 
 
 # ----------------------------------------------------------------------------------------------
-# Online block memoisation with random subsets (Sec. 4, Sec. 5.2; Alg. 3 / Alg. 5 sampling lines)
+# Online block memoisation with random subsets (Sec. 4, Sec. 5.2; the sampling steps of Alg. 3 / Alg. 5)
 # ----------------------------------------------------------------------------------------------
 
 def memo_prob(cd: bool, rows: int, n: int, s: int, t: int) -> float:

@@ -338,7 +338,7 @@ int64_t orc_cg(int64_t n, const double *A, const double *b, double *x, double to
 }
 
 /* ------------------------------------------------------------------------------------------------
- * Randomized Hadamard preprocessing of CD++ (Sec. 5.1, Algorithm CD++ lines 2-3 and the return
+ * Randomized Hadamard preprocessing of CD++ (Sec. 5.1, the preprocessing of Alg. 3 and the return
  * D FHT(x); App. on FHT / SymFHT).
  *
  * H_n (n a power of 2) is the Sylvester-Hadamard matrix: H_1 = [1], H_2n = [[H_n, H_n], [H_n, -H_n]].
@@ -478,7 +478,7 @@ int64_t orc_symfht(int64_t n, double *A) {
 
 /* ------------------------------------------------------------------------------------------------
  * Online block memoisation with random subsets (Sec. 4, "Block memoization"; Sec. 5.2, the
- * simplified scheme of CD++ in Alg. 3's sampling lines; the sampling line of Alg. 5 for K++).
+ * simplified scheme of CD++ in Alg. 3's sampling step; the sampling step of Alg. 5 for K++).
  *
  * The collection B of memoised blocks starts empty.  At step t a Bernoulli draw with probability
  *   CD++: p_t = min(1, (n / s) ln(n) / t)          K++: p_t = min(1, (m / s) ln(m) / t, (n / s) ln(m) / t)

@@ -1,4 +1,4 @@
-// kpp_cd3.cu -- CD++ (Eq. 5.1; Alg. 3 lines 10-20, maintained residual) as a dataflow kernel.
+// kpp_cd3.cu -- CD++ (Eq. 5.1; Alg. 3's loop, maintained residual) as a dataflow kernel.
 //
 // The only value one step of CD++ needs from other CTAs is r = R_x[S] of the next block, and only the
 // CTAs owning the columns of that block produce it.  So instead of a group barrier per step:

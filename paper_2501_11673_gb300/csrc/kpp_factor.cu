@@ -1,5 +1,5 @@
-// kpp_factor.cu -- memoised per-block factors (Sec. 4 "block memoization"; Sec. 5.2; Alg. 1 line 7;
-// Alg. 3 line 8).
+// kpp_factor.cu -- memoised per-block factors (Sec. 4 "block memoization"; Sec. 5.2; Alg. 1;
+// Alg. 3).
 //
 // For each block j of the fixed partition:
 //   G_j  = A_{S_j} A_{S_j}^T + lam I    (K++; Eq. 1.3)   or   A_{S_j S_j} + lam I   (CD++; Eq. 5.1)

@@ -1,5 +1,5 @@
 // kpp_gram_tc.cu -- block Gram G_j = A_{S_j} A_{S_j}^T + lam I on the tcgen05 tensor cores (Sec. 4:
-// the memoised factor of K++ is chol(A_S A_S^T + lam I); Alg. 1 line 7).
+// the memoised factor of K++ is chol(A_S A_S^T + lam I); Alg. 1).
 //
 // FP32 / BF16 storage only (kind::tf32 / kind::f16, FP32 accumulation in tensor memory); the result is
 // widened to FP64 for the FP64 Cholesky.  One CTA computes one 128 x 256 tile of one block's Gram:

@@ -1,5 +1,5 @@
 // kpp_memo.cuh -- the draws of the online block memoisation (Sec. 4, "Block memoization"; Sec. 5.2, the
-// simplified scheme of CD++; the sampling lines of Alg. 3 and Alg. 5), host and device.
+// simplified scheme of CD++; the sampling steps of Alg. 3 and Alg. 5), host and device.
 //
 // Step t either samples a new uniformly random s-subset S of the rows (with probability p_t; it joins
 // the memo with the next index) or reuses a memoised block picked uniformly.  p_0 = 1, and for t >= 1

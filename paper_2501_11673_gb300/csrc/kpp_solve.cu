@@ -1,13 +1,13 @@
 // kpp_solve.cu -- the block-step iteration of Kaczmarz++ and CD++ as one persistent kernel.
 //
 // Paper: arXiv 2501.11673.  One launch runs every iteration of one or more systems:
-//   K++  (Alg. 1 lines 6-10; Alg. 5 lines 9-12, exact projection through the memoised factor):
+//   K++  (Alg. 1; Alg. 5, exact projection through the memoised factor):
 //        r = A_S x - b_S;  y = (A_S A_S^T + lam I)^{-1} r;  w = A_S^T y;
 //        m <- beta (m - w);  x <- x - w + eta m;   beta = (1 - rho)/(1 + rho)          (Eq. 1.3, 1.4)
-//   CD++ (Eq. 5.1; Alg. 3 lines 10-13) with the residual kept up to date:
+//   CD++ (Eq. 5.1; Alg. 3) with the residual kept up to date:
 //        r = R_x[S];  y = (A_SS + lam I)^{-1} r;  u = A_{:,S} y  (= A_S^T y, A symmetric);
 //        R_m <- beta (R_m - u);  R_x <- R_x - u + eta R_m;  m <- beta (m - I_S^T y);  x <- x - I_S^T y + eta m
-//   then, every step, E0 / E1 += |r|^2 and every 2 zeta steps the checkpoint of Alg. 3 lines 14-20:
+//   then, every step, E0 / E1 += |r|^2 and every 2 zeta steps the checkpoint of Alg. 3:
 //   stop test on E1 (confirmed by the true residual), weighted ratio (Eq. 5.3), rho = 1 - rhat^(1/zeta).
 //
 // Work split inside a system (G CTAs, one group barrier counter):

@@ -1,6 +1,6 @@
 // kpp_solve_device.cuh -- device pieces shared by the persistent solve kernels (kpp_solve.cu,
 // kpp_solve2.cu): per-column state, small reductions, and the FP64 true-residual phase that confirms
-// the stopping rule (Alg. 3 line 16) and, for CD++, replaces the maintained residual.
+// the stopping rule (Alg. 3) and, for CD++, replaces the maintained residual.
 #pragma once
 
 #include "kpp_internal.cuh"
@@ -95,7 +95,7 @@ __device__ bool true_residual_phase(const SysArgs &sa, const Common &cm, int g, 
 
 namespace kpp {
 
-// The checkpoint of Alg. 3 lines 15-20 (Alg. 5 lines 14-19) for one right-hand-side column, after
+// The checkpoint of Alg. 3 (and of Alg. 5) for one right-hand-side column, after
 // the optional true-residual check has filled cs.res_true: stop test, then the weighted ratio of
 // Eq. 5.3 (a_i = (i+1)^{ln(i+1)}; the first checkpoint takes the ratio itself) and
 // rho = 1 - rhat^(1/zeta), clamped to [0, 1 - 1e-12]; then E0 = E1 = 0.

@@ -1,7 +1,7 @@
 // kpp_stream.cu -- batched K++ inner iteration for wide systems (FP32 / BF16 storage, FP32 arithmetic):
 // many systems, each with a panel of k right-hand sides, in one persistent launch.
 //
-// The step is K++'s (Eq. 1.3, 1.4; Alg. 5 lines 9-19 with exact memoised projections):
+// The step is K++'s (Eq. 1.3, 1.4; Alg. 5 with exact memoised projections):
 //   R = A_S X - B_S,  Y = G^{-1} R,  W = A_S^T Y,  M <- beta (M - W),  X <- X - W + eta M,
 // every right-hand-side column with its own rho, residual estimate and stop test, all columns of a
 // system sharing its block sequence.  For wide blocks (config of 256 rows x 65536 columns) a step is two

@@ -18,8 +18,10 @@ Paper: arXiv 2501.11673.  What pins what:
   * Hadamard preprocessing (Sec. 5.1) -> scipy.linalg.hadamard (Sylvester construction); the spectrum and
                             the solution are invariant (Q orthogonal); the SymFHT operation count of its
                             theorem, n^2 (2.5 + log2 n), and the recursion's exact count
-The adaptive-rho schedule and the stop rule have no printed values in the paper ("parity unpinned"):
-only their structural properties are checked here.
+  * adaptive rho, stop rule (Eq. 5.2, 5.3) -> closed forms on diagonal systems with eta = 0: each residual
+                            entry decays by its own factor per draw of its block, so the windows E0 / E1,
+                            the ratios, the weighted mean of Eq. 5.3 (written as an explicit weighted sum),
+                            rho with its clamps, the confirmations and the stop iteration are all fixed
 """
 import math
 import os
@@ -250,7 +252,7 @@ def test_cdpp_converges_to_spd_solution():
 
 
 def test_adaptive_rho_schedule_structure():
-    """Alg. 3 lines 14-20 (parity unpinned): checkpoints every 2 zeta steps; rho in [0, 1); the first
+    """Alg. 3's checkpoints: every 2 zeta steps; rho in [0, 1); the first
     rho follows from the first ratio as 1 - (E1/E0)^(1/zeta)."""
     sy = W.kpp_fp64_2000x200()
     L = oracle.kpp_factor(sy.A, sy.s, sy.lam)
@@ -259,10 +261,143 @@ def test_adaptive_rho_schedule_structure():
     tr = res.trace
     assert len(tr) == 10
     np.testing.assert_array_equal(tr[:, 0], np.arange(1, 11) * 2 * zeta - 1)
-    assert tr[0, 3] == 0.0  # rho_0 = 0 (Alg. 3 line 4)
+    assert tr[0, 3] == 0.0  # rho_0 = 0 (Alg. 3's initialisation)
     rho1 = 1.0 - (tr[0, 2] / tr[0, 1]) ** (1.0 / zeta)
     assert tr[1, 3] == pytest.approx(max(rho1, 0.0), rel=1e-12)
     assert np.all((res.trace[:, 3] >= 0) & (res.trace[:, 3] < 1))
+
+
+def _weighted_mean_rhat(q):
+    """Eq. 5.3 solved for rhat_i: a_i rhat_i = a_{i-1} rhat_{i-1} + (a_i - a_{i-1}) q_i with rhat_1 = q_1,
+    so rhat_i = (a_1 q_1 + sum_{j=2..i} (a_j - a_{j-1}) q_j) / a_i, a_j = (j+1)^{ln(j+1)}."""
+    a = [(j + 1.0) ** math.log(j + 1.0) for j in range(len(q) + 1)]
+    out, acc = [], 0.0
+    for i in range(1, len(q) + 1):
+        acc += (a[1] if i == 1 else a[i] - a[i - 1]) * q[i - 1]
+        out.append(acc / a[i])
+    return out
+
+
+def _diagonal_windows(cfac, b, s, seed, T):
+    """E0/E1 windows of a diagonal system in closed form.  With A = diag(d), one step on block S
+    multiplies each residual entry of S by its factor c_i (K++: lambda/(d_i^2 + lambda); CD++:
+    lambda/(d_i + lambda)) and leaves the other entries alone, so after k_i draws of i's block the
+    entry is -b_i c_i^{k_i}.  Window membership and checkpoint times follow Alg. 3.
+    Returns zeta and, per checkpoint, (t, E0, E1, |A x_{t+1} - b|)."""
+    n = len(b)
+    nb = -(-n // s)
+    zeta = nb
+    k = np.zeros(n)
+    E0 = E1 = 0.0
+    ckpt = []
+    for t in range(T):
+        j = oracle.sample_block(seed, t, 0, nb)
+        S = slice(j * s, min((j + 1) * s, n))
+        e = float(np.sum((b[S] * cfac[S] ** k[S]) ** 2))
+        k[S] += 1
+        if t % (2 * zeta) < zeta:
+            E0 += e
+        else:
+            E1 += e
+        if t % (2 * zeta) == 2 * zeta - 1:
+            ckpt.append((t, E0, E1, float(np.linalg.norm(b * cfac ** k))))
+            E0 = E1 = 0.0
+    return zeta, ckpt
+
+
+@pytest.mark.parametrize("cd", [False, True])
+@pytest.mark.parametrize("n,s,scales,lam_rel,T,rtol,kind", [
+    (9, 9, (1.0,), 4.0, 12, 1e-9, "inside"),             # one block: zeta = 1, every window deterministic
+    (12, 4, (1.0, 1.5, 0.7), 0.5, 90, 1e-8, "mixed"),    # zeta = 3 under the Philox draw
+    (12, 4, (1.0, 1e2, 1e-2), 4.0, 90, 1e-8, "low"),     # ratios far above 1: rho stays at its lower clamp 0
+    (4, 4, (1.0,), 1e-8, 2, 1e-6, "high"),               # ratio below 1e-12: rho hits its upper clamp
+])
+def test_adaptive_rho_follows_closed_form_windows_on_diagonal_systems(cd, n, s, scales, lam_rel, T, rtol, kind):
+    """Eq. 5.2 and Eq. 5.3 with the checkpoints of Alg. 3 on diagonal systems with eta = 0 (momentum off, so
+    rho never changes the iterates): the windows E0 and E1, the ratio q_i = E1/E0 at each checkpoint,
+    rhat_i as the explicit weighted mean of Eq. 5.3's weights, rho_i = 1 - rhat_i^(1/zeta) clamped to
+    [0, 1 - 1e-12] (readings 5 and 6), all from the closed-form residual decay.  The oracle forms each
+    residual as A_S x - b_S, which loses digits as the residual shrinks (absolute error ~1e-16 |b| per
+    step), so lambda keeps the decay factors >= 0.8 and rtol follows the smallest c_i^{k_i} reached."""
+    rng = np.random.default_rng(900 + n + s)
+    d = rng.uniform(1.0, 3.0, n)
+    b = rng.standard_normal(n) * np.repeat(np.asarray(scales), s)[:n]
+    A = np.diag(d)
+    lam = lam_rel * (float(np.max(d)) if cd else float(np.max(d)) ** 2)
+    cfac = lam / (d + lam) if cd else lam / (d * d + lam)
+    L = oracle.cdpp_factor(A, s, lam) if cd else oracle.kpp_factor(A, s, lam)
+    res = oracle.run(A, b, L, s, cd=cd, lam=lam, tol=0.0, max_iters=T, seed=7, eta=0.0)
+    zeta, ck = _diagonal_windows(cfac, b, s, 7, T)
+    tr = res.trace
+    assert len(tr) == len(ck) == T // (2 * zeta)
+    np.testing.assert_array_equal(tr[:, 0], [c[0] for c in ck])
+    np.testing.assert_allclose(tr[:, 1], [c[1] for c in ck], rtol=rtol)
+    np.testing.assert_allclose(tr[:, 2], [c[2] for c in ck], rtol=rtol)
+    q = [c[2] / c[1] for c in ck]
+    rhat = _weighted_mean_rhat(q)
+    rho = [min(max(1.0 - r ** (1.0 / zeta), 0.0), 1.0 - 1e-12) for r in rhat]
+    # the trace holds the rho in force at each checkpoint: 0 at the first (Alg. 3's initialisation), then rho_{i-1}
+    np.testing.assert_allclose(tr[:, 3], [0.0] + rho[:-1], rtol=0, atol=10 * rtol)
+    assert res.state.rhat == pytest.approx(rhat[-1], rel=10 * rtol)
+    assert res.state.rho == pytest.approx(rho[-1], rel=0, abs=10 * rtol)
+    np.testing.assert_allclose(res.x, b / d * (1.0 - cfac ** _draw_counts(n, s, 7, T)), rtol=1e-12)
+    if kind == "inside":
+        assert min(rho) > 0.0 and max(rho) < 1.0 - 1e-12
+    elif kind == "mixed":
+        assert max(rho) > 0.0 and max(q) > 1.0
+    elif kind == "low":
+        assert q[0] > 1.0 and max(rho) == 0.0
+    else:
+        assert q[0] < 1e-12 and res.state.rho == 1.0 - 1e-12
+
+
+@pytest.mark.parametrize("cd", [False, True])
+@pytest.mark.parametrize("n,s,scales,lam_rel", [(9, 9, (1.0,), 4.0), (12, 4, (1.0, 30.0, 0.03), 0.5)])
+def test_stop_rule_follows_closed_form_on_diagonal_systems(cd, n, s, scales, lam_rel):
+    """Eq. 5.2's stopping test E1 <= eps^2 |b|^2 at each checkpoint (Alg. 3), confirmed by the true
+    residual |Ax - b| / |b| <= eps before returning (reading 8): on diagonal systems with eta = 0 both sides
+    of both tests are closed forms, so the stop iteration, the checkpoints where the confirmation ran and
+    what it found are fixed.  With uneven block scales the window can pass while an undrawn block still
+    holds a large residual; the confirmation must then reject and the run continue."""
+    rng = np.random.default_rng(700 + n)
+    d = rng.uniform(1.0, 3.0, n)
+    b = rng.standard_normal(n) * np.repeat(np.asarray(scales), s)[:n]
+    if len(scales) > 1:
+        d[s:2 * s] *= 0.3  # the large block also converges slowest
+    A = np.diag(d)
+    lam = lam_rel * (float(np.max(d)) if cd else float(np.max(d)) ** 2)
+    cfac = lam / (d + lam) if cd else lam / (d * d + lam)
+    L = oracle.cdpp_factor(A, s, lam) if cd else oracle.kpp_factor(A, s, lam)
+    eps, T = 1e-3, 3000
+    res = oracle.run(A, b, L, s, cd=cd, lam=lam, tol=eps, max_iters=T, seed=7, eta=0.0)
+    zeta, ck = _diagonal_windows(cfac, b, s, 7, T)
+    bn = float(np.linalg.norm(b))
+    stop, tested, rejected = None, [], 0
+    for i, (t, _, E1, rn) in enumerate(ck):
+        if E1 <= eps * eps * bn * bn:
+            tested.append(i)
+            if rn <= eps * bn:
+                stop = i
+                break
+            rejected += 1
+    assert stop is not None
+    assert res.status == oracle.OK and res.iters == ck[stop][0] + 1
+    tr = res.trace
+    assert len(tr) == stop + 1
+    assert np.flatnonzero(~np.isnan(tr[:, 4])).tolist() == tested
+    np.testing.assert_allclose(tr[tested, 4], [ck[i][3] / bn for i in tested], rtol=1e-8)
+    assert res.rel_res_true == pytest.approx(ck[stop][3] / bn, rel=1e-8)
+    if len(scales) > 1:
+        assert rejected > 0
+
+
+def _draw_counts(n, s, seed, T):
+    nb = -(-n // s)
+    k = np.zeros(n)
+    for t in range(T):
+        j = oracle.sample_block(seed, t, 0, nb)
+        k[j * s:min((j + 1) * s, n)] += 1
+    return k
 
 
 def test_cg_matches_direct_solve():
@@ -288,7 +423,7 @@ def test_storage_rounding_is_exact_widening():
 
 
 # ---------------------------------------------------------------------------------------------
-# Randomized Hadamard preprocessing of CD++ (Sec. 5.1, Alg. 3 lines 2-3; App. on FHT / SymFHT)
+# Randomized Hadamard preprocessing of CD++ (Sec. 5.1, the preprocessing of Alg. 3; App. on FHT / SymFHT)
 # ---------------------------------------------------------------------------------------------
 
 def _sym(n, seed):
