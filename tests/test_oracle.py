@@ -2,6 +2,7 @@
 
 Paper: arXiv 2501.11673.  What pins what:
   * Philox4x32-10       -> published known-answer vectors (tests/golden/philox4x32_10_kat.txt)
+  * block draw           -> its counter layout {t_lo, t_hi, system, 0} on the pinned generator; uniformity
   * Cholesky / solve     -> LAPACK through numpy
   * K++ step, lam > 0    -> the argmin definition of Eq. 1.3, solved through the n x n normal equations
   * K++ step, lam = 0    -> the projection invariant A_S x = b_S (Sec. 1.1) and, for s = 1, the classical
@@ -12,9 +13,11 @@ Paper: arXiv 2501.11673.  What pins what:
   * CG                   -> numpy.linalg.solve
   * online memo (Sec. 4, 5.2) -> uniform s-subsets (inclusion and pair frequencies), the Bernoulli schedule's
                             expected block count, the argmin / block-residual invariants on arbitrary
-                            subsets, convergence to the direct solution
+                            subsets, convergence to the direct solution, closed-form windows and rho on
+                            diagonal systems
   * LSQR projection (Sec. 4.1) -> the regularised argmin (normal equations); one iteration when the sketch is
-                            the whole (orthogonal) transform; the preconditioned condition number against tau
+                            the whole (orthogonal) transform; the preconditioned condition number against tau;
+                            the sketched Gram against scipy's Hadamard matrix
   * Hadamard preprocessing (Sec. 5.1) -> scipy.linalg.hadamard (Sylvester construction); the spectrum and
                             the solution are invariant (Q orthogonal); the SymFHT operation count of its
                             theorem, n^2 (2.5 + log2 n), and the recursion's exact count
@@ -49,6 +52,16 @@ def _kat_rows():
 @pytest.mark.parametrize("ctr,key,expected", _kat_rows())
 def test_philox_known_answers(ctr, key, expected):
     assert oracle.philox4x32_10(ctr, key) == expected
+
+
+@pytest.mark.parametrize("seed,t,sys_id,nb", [(0, 0, 0, 100), (1234, 77, 3, 7), (2**40 + 5, 2**33 + 9, 11, 64),
+                                             (2**64 - 1, 2**32 - 1, 2**32 - 1, 1), (9, 5, 0, 2**31 - 1)])
+def test_block_draw_follows_the_counter_layout(seed, t, sys_id, nb):
+    """The block of step t is j = (out0 * nb) >> 32 with out = Philox4x32-10(counter {t_lo, t_hi, system, 0},
+    key {seed_lo, seed_hi}) (the sampling reading), built here from the known-answer-pinned generator."""
+    m32 = 0xFFFFFFFF
+    out = oracle.philox4x32_10([t & m32, t >> 32, sys_id, 0], [seed & m32, seed >> 32])
+    assert oracle.sample_block(seed, t, sys_id, nb) == (out[0] * nb) >> 32
 
 
 def test_block_sampling_uniform_and_in_range():
@@ -309,6 +322,7 @@ def _diagonal_windows(cfac, b, s, seed, T):
 @pytest.mark.parametrize("n,s,scales,lam_rel,T,rtol,kind", [
     (9, 9, (1.0,), 4.0, 12, 1e-9, "inside"),             # one block: zeta = 1, every window deterministic
     (12, 4, (1.0, 1.5, 0.7), 0.5, 90, 1e-8, "mixed"),    # zeta = 3 under the Philox draw
+    (11, 4, (1.0, 1.5, 0.7), 0.5, 90, 1e-8, "mixed"),    # ragged last block: zeta = ceil(11/4) = 3
     (12, 4, (1.0, 1e2, 1e-2), 4.0, 90, 1e-8, "low"),     # ratios far above 1: rho stays at its lower clamp 0
     (4, 4, (1.0,), 1e-8, 2, 1e-6, "high"),               # ratio below 1e-12: rho hits its upper clamp
 ])
@@ -450,6 +464,20 @@ def test_rht_matches_scipy_hadamard(n):
         assert abs(oracle.rht_entry(d, A, i, j) - Abar[i, j]) <= 1e-13 * n
 
 
+@pytest.mark.parametrize("n", [2, 8, 32])
+def test_rht_definition_holds_for_a_general_matrix(n):
+    """Q A Q^T and its single entries for a non-symmetric A (the definition does not use symmetry)."""
+    import scipy.linalg
+    A = np.random.default_rng(300 + n).standard_normal((n, n))
+    d = _signs(n, 400 + n)
+    Q = scipy.linalg.hadamard(n).astype(float) * d[None, :] / math.sqrt(n)
+    ref = Q @ A @ Q.T
+    Abar, _ = oracle.rht_forward(d, A, None)
+    assert np.abs(Abar - ref).max() <= 1e-13 * n
+    for i, j in [(0, n - 1), (n - 1, 0), (1, n // 2)]:
+        assert abs(oracle.rht_entry(d, A, i, j) - ref[i, j]) <= 1e-13 * n
+
+
 def test_rht_keeps_spectrum_and_solution():
     """Q is orthogonal: Q A Q^T has the eigenvalues of A, and Q^T (Q A Q^T)^{-1} Q b = A^{-1} b."""
     n = 32
@@ -565,6 +593,48 @@ def test_memo_subset_cd_step_zeroes_the_block_residual():
     np.testing.assert_array_equal(x[others], x0[others])
 
 
+@pytest.mark.parametrize("n", [11, 12])
+@pytest.mark.parametrize("cd", [False, True])
+def test_memo_windows_follow_closed_form_on_diagonal_systems(cd, n):
+    """The online memo's run keeps the windows, ratios and rho of Eq. 5.2 - 5.3 with zeta = ceil(rows / s)
+    (here 11 or 12 rows in subsets of 4, zeta = 3): on a diagonal system with eta = 0 each row's residual entry
+    decays by its own factor whenever a subset holding it is drawn, so rhat, rho and x after T steps are
+    closed forms of the recorded block sequence and subsets."""
+    s, T, seed = 4, 96, 5
+    rng = np.random.default_rng(31)
+    d = rng.uniform(1.0, 3.0, n)
+    b = rng.standard_normal(n) * np.where(np.arange(n) < 5, 1.0, 1.8)
+    lam = 4.0 * (float(np.max(d)) if cd else float(np.max(d)) ** 2)
+    cfac = lam / (d + lam) if cd else lam / (d * d + lam)
+    res, nb, blocks = oracle.run_memo(np.diag(d), b, s, cd=cd, lam=lam, tol=0.0, max_iters=T, seed=seed, eta=0.0,
+                                      block_cap=T)
+    assert res.iters == T and nb == blocks.max() + 1
+    first = {}
+    for t, j in enumerate(blocks.tolist()):
+        first.setdefault(j, t)
+    subsets = {j: oracle.memo_subset(seed, t, 0, n, s) for j, t in first.items()}
+    zeta = -(-n // s)
+    k = np.zeros(n)
+    E0 = E1 = 0.0
+    q = []
+    for t, j in enumerate(blocks.tolist()):
+        S = subsets[j]
+        e = float(np.sum((b[S] * cfac[S] ** k[S]) ** 2))
+        k[S] += 1
+        if t % (2 * zeta) < zeta:
+            E0 += e
+        else:
+            E1 += e
+        if t % (2 * zeta) == 2 * zeta - 1:
+            q.append(E1 / E0)
+            E0 = E1 = 0.0
+    rhat = _weighted_mean_rhat(q)[-1]
+    assert res.state.ci == len(q) == T // (2 * zeta)
+    assert res.state.rhat == pytest.approx(rhat, rel=1e-9)
+    assert res.state.rho == pytest.approx(min(max(1.0 - rhat ** (1.0 / zeta), 0.0), 1.0 - 1e-12), abs=1e-9)
+    np.testing.assert_allclose(res.x, b / d * (1.0 - cfac ** k), rtol=1e-12)
+
+
 def test_memo_solves_converge_to_the_direct_solution():
     """CD++ (SPD) and K++ (consistent least squares) with the online memo reach 1e-8 and the solution."""
     n, s = 128, 16
@@ -594,6 +664,22 @@ def _proj_case(s, n, lam, seed):
     r = rng.standard_normal(s)
     w_star = np.linalg.solve(np.eye(n) * lam + AS.T @ AS, AS.T @ r)  # argmin |A_S w - r|^2 + lam |w|^2
     return AS, r, w_star
+
+
+@pytest.mark.parametrize("s,n,tau", [(8, 100, 16), (12, 64, 40)])
+def test_proj_precond_is_the_sketched_gram(s, n, tau):
+    """L L^T - lam I = Ahat Ahat^T with Ahat = (A_S D H_n')[:, T] / sqrt(tau) (Sec. 4.1's SRHT sketch), built
+    here from scipy's Hadamard matrix on A_S padded with zero columns to n' = the next power of 2."""
+    import scipy.linalg
+    lam = 0.3
+    AS, _, _ = _proj_case(s, n, lam, 20 + s)
+    n2 = 1 << (n - 1).bit_length()
+    d = W.rademacher_signs(n2, 21)
+    T = np.sort(np.random.default_rng(22).choice(n2, tau, replace=False))
+    L = oracle.proj_precond(AS, lam, T, d)
+    pad = np.hstack([AS, np.zeros((s, n2 - n))])
+    Ah = (pad * d[None, :] @ scipy.linalg.hadamard(n2).astype(float))[:, T] / math.sqrt(tau)
+    np.testing.assert_allclose(L @ L.T - lam * np.eye(s), Ah @ Ah.T, rtol=1e-12, atol=1e-10)
 
 
 def test_proj_lsqr_with_the_whole_transform_is_exact_in_one_iteration():
