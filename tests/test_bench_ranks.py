@@ -59,3 +59,22 @@ def test_replicas_draw_their_own_inputs():
     seeds = {r: [wl.system_seed(r, i) for i in range(wl.nsys)] for r in range(4)}
     flat = [s for v in seeds.values() for s in v]
     assert len(flat) == len(set(flat))
+
+
+def test_clock_summary_reads_throttle_reasons():
+    """The clocks object of the bench line: median SM clock under load, the maximum clock, and the
+    throttle reasons seen Active in any sample (nvidia-smi csv,noheader,nounits rows)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    clk = bench.ClockSampler(0)
+    na = "Not Active"
+    clk.lines = [f"0, 2070, 2070, 812.3, 0x0000000000000000, {na}, {na}, {na}, {na}",
+                 f"0, 1980, 2070, 1390.0, 0x0000000000000004, {na}, {na}, {na}, Active",
+                 f"0, 2055, 2070, 1100.0, 0x0000000000000000, {na}, {na}, {na}, {na}",
+                 "garbage line", "0, [N/A], 2070, 0, 0, a, b, c, d"]
+    s = clk.summary()
+    assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    clk.lines.append(f"0, 1200, 2070, 1400.0, 0x0000000000000008, Active, {na}, Active, {na}")
+    assert clk.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                                               "samples": 0}
