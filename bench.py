@@ -163,6 +163,57 @@ def _factors_numpy_gram(A, s, lam):
     return L
 
 
+def cg_torch(A, b, tol, max_iters):
+    """Plain conjugate gradients (Hestenes and Stiefel, 1952) from x0 = 0 with torch ops, FP64: the
+    Krylov reference point beside CD++ on the SPD workload.  Same update order as the oracle's CG, and
+    the stop test |r| <= tol |b| on the recursively updated residual, checked on the host every
+    iteration.  Returns (x, iterations, |b - A x| / |b| recomputed in FP64)."""
+    import torch
+    x = torch.zeros_like(b)
+    r = b.clone()
+    p = r.clone()
+    bn = float(torch.linalg.vector_norm(b))
+    rr = torch.dot(r, r)
+    it = 0
+    while it < max_iters and math.sqrt(float(rr)) > tol * bn:
+        Ap = torch.mv(A, p)
+        alpha = rr / torch.dot(p, Ap)
+        x.add_(alpha * p)
+        r.sub_(alpha * Ap)
+        rr2 = torch.dot(r, r)
+        p.mul_(rr2 / rr).add_(r)
+        rr = rr2
+        it += 1
+    res = float(torch.linalg.vector_norm(b - torch.mv(A, x))) / bn if bn > 0 else float(torch.linalg.vector_norm(x))
+    return x, it, res
+
+
+def cg_reference(A, b, tol, reps=3, max_iters=20000):
+    """Time-to-tolerance of cg_torch on A, b (device tensors: CUDA events on the current stream around
+    each run, after one warm-up run; host tensors: wall clock).  Median over `reps` runs."""
+    import torch
+    cg_torch(A, b, tol, max_iters)
+    ms = []
+    for _ in range(reps):
+        if A.is_cuda:
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, it, res = cg_torch(A, b, tol, max_iters)
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        else:
+            t0 = time.perf_counter()
+            _, it, res = cg_torch(A, b, tol, max_iters)
+            ms.append(1e3 * (time.perf_counter() - t0))
+    n = A.shape[0]
+    return {"what": "plain FP64 conjugate gradients from x0 = 0 on the same system and device (torch / cuBLAS "
+                    "matrix-vector products; stop test on the host every iteration)",
+            "iters": it, "time_to_tol_ms": statistics.median(ms), "rel_res_true": res,
+            "flops_paper_model": (2 * n * n + 11 * n) * it, "flops_model": "(2 n^2 + 11 n) per CG iteration"}
+
+
 # ---------------------------------------------------------------------------------------------
 # Workloads
 # ---------------------------------------------------------------------------------------------
@@ -273,6 +324,23 @@ class SingleFP64(Workload):
                                "(MEASURED_PEAKS.json sm_max_mhz)",
                 "hbm_view": {"achieved": achb, "peak": hbm, "unit": "GB/s", "frac": achb / hbm,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
+
+    def extra(self, steps):
+        """CD++ only: plain FP64 CG on the same system as a reference point, and both methods' flop counts
+        (CG: the paper's 2n^2 + 11n per iteration; CD++: per-iteration flops of this step times the
+        iterations, plus the factor phase nb (s^3/3 + 2 s^2 n), Cholesky and the memo W = G^-1 A_S)."""
+        if not self.cd:
+            return {}
+        n, s = self.sy.A.shape[1], self.sy.s
+        nb = -(-n // s)
+        iters = statistics.mean(st["iters"] for st in steps)
+        out = {"cdpp_flops": {"iterations": self.per_iter()[0] * iters,
+                              "factor_phase": nb * (s ** 3 / 3 + 2 * s * s * n)}}
+        try:
+            out["cg_reference"] = cg_reference(self.Ad, self.bd, self.sy.tol)
+        except Exception as exc:  # a failed reference point must not lose the bench line
+            out["cg_reference"] = {"error": f"{type(exc).__name__}: {exc}"}
+        return out
 
     def e2e(self):
         kpp = self.kpp
