@@ -48,7 +48,7 @@ typedef enum {
     KPP_ERR_NO_CONVERGENCE = 6, /* max_iters (or max_outer) reached; x holds the last iterate */
     KPP_ERR_TIMEOUT = 7,        /* a bounded device-side wait expired; x holds the last iterate */
     KPP_ERR_BUDGET = 8,         /* a serving request does not fit the memory budget */
-    KPP_ERR_UNSUPPORTED = 9     /* a combination this build does not implement */
+    KPP_ERR_UNSUPPORTED = 9     /* a combination the library does not implement */
 } kpp_status;
 
 /* A dense row-major matrix in caller-owned memory. */
