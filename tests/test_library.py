@@ -141,3 +141,64 @@ def test_memo_sequence_refuses_bad_arguments(lib):
     assert lib.kpp_memo_sequence(*args(0, 10, 12, 11, 4, 4)) == kpp.ERR_ARG  # s > rows
     assert lib.kpp_memo_sequence(*args(0, 10, 12, 2, 4, 1)) == kpp.ERR_ARG   # steps 0, 1 both draw new blocks
     assert nb.value == 1 and "subsets_cap" in kpp.last_error()
+
+
+def test_solver_entry_points_refuse_bad_arguments_on_the_host(lib):
+    """The factor, solve, batched, plan, server, sampling, Gram and residual entry points check their
+    arguments before any device work: each call below has exactly one bad argument (the device pointers
+    are never dereferenced) and returns KPP_ERR_ARG with a message."""
+    vp = ctypes.c_void_p
+    dev = vp(256)  # a stand-in device address; validation rejects every call before using it
+    P = kpp.Partition(64, 8)
+    out = vp()
+    prm = kpp.params(lam=1e-3)
+    rep = kpp.Report()
+
+    def mat(rows=64, cols=64, dtype=kpp.KPP_F64, ld=None, data=dev):
+        return kpp.Matrix(data, dtype, 0, rows, cols, cols if ld is None else ld)
+
+    fb = lib.kpp_factor_blocks
+    assert fb(ctypes.byref(mat()), P.handle, 1e-3, 0, None, None) == kpp.ERR_ARG              # no output handle
+    assert fb(ctypes.byref(mat()), None, 1e-3, 0, ctypes.byref(out), None) == kpp.ERR_ARG  # no partition
+    assert fb(ctypes.byref(mat(dtype=7)), P.handle, 1e-3, 0, ctypes.byref(out), None) == kpp.ERR_ARG
+    assert fb(ctypes.byref(mat(ld=32)), P.handle, 1e-3, 0, ctypes.byref(out), None) == kpp.ERR_ARG  # ld < cols
+    assert fb(ctypes.byref(mat(data=None)), P.handle, 1e-3, 0, ctypes.byref(out), None) == kpp.ERR_ARG
+    assert fb(ctypes.byref(mat(rows=63)), P.handle, 1e-3, 0, ctypes.byref(out), None) == kpp.ERR_ARG  # rows != partition
+    assert fb(ctypes.byref(mat()), P.handle, 1e-3, 2, ctypes.byref(out), None) == kpp.ERR_ARG         # mode
+    assert fb(ctypes.byref(mat()), P.handle, -1.0, 0, ctypes.byref(out), None) == kpp.ERR_ARG          # lambda < 0
+    assert fb(ctypes.byref(mat()), P.handle, float("nan"), 0, ctypes.byref(out), None) == kpp.ERR_ARG
+    assert fb(ctypes.byref(mat(cols=32)), P.handle, 1e-3, 1, ctypes.byref(out), None) == kpp.ERR_ARG  # CD++ not square
+    assert "kpp_factor_blocks" in kpp.last_error()
+
+    for f in (lib.kpp_solve, lib.cdpp_solve, lib.cdpp_solve_noalloc):  # no factors
+        assert f(ctypes.byref(mat()), dev, dev, P.handle, None, ctypes.byref(prm), ctypes.byref(rep), None) == kpp.ERR_ARG
+    assert lib.kpp_solve(ctypes.byref(mat()), None, dev, P.handle, dev, ctypes.byref(prm), ctypes.byref(rep),
+                         None) == kpp.ERR_ARG                                                  # no b
+    Bs, Xs, Fs = (vp * 1)(dev), (vp * 1)(dev), (vp * 1)(None)
+    for f in (lib.kpp_solve_batched, lib.cdpp_solve_batched):
+        assert f(0, ctypes.byref(mat()), Bs, Xs, 1, P.handle, Fs, ctypes.byref(prm), ctypes.byref(rep), None) == kpp.ERR_ARG
+        assert f(1, ctypes.byref(mat()), Bs, Xs, 33, P.handle, Fs, ctypes.byref(prm), ctypes.byref(rep), None) == kpp.ERR_ARG
+    assert lib.kpp_plan_create(1, ctypes.byref(mat()), Bs, Xs, 1, P.handle, Fs, ctypes.byref(prm), 2, None,
+                               ctypes.byref(out)) == kpp.ERR_ARG                               # mode
+    assert lib.kpp_plan_create(1, ctypes.byref(mat()), Bs, Xs, 1, P.handle, Fs, ctypes.byref(prm), 0, None,
+                               ctypes.byref(out)) == kpp.ERR_ARG                               # no factors
+    assert lib.kpp_server_create(0, 4, 0, ctypes.byref(out)) == kpp.ERR_ARG                    # no budget
+    assert lib.kpp_server_create(1 << 30, 0, 0, ctypes.byref(out)) == kpp.ERR_ARG              # no slots
+    assert lib.kpp_server_create(1 << 30, 65, 0, ctypes.byref(out)) == kpp.ERR_ARG
+    assert lib.kpp_sample_blocks(1, 0, 0, 10, 0, dev, None) == kpp.ERR_ARG                     # nb < 1
+    assert lib.kpp_sample_blocks(1, 0, 0, -1, 4, dev, None) == kpp.ERR_ARG
+    assert lib.kpp_sample_blocks(1, 0, 0, 10, 4, None, None) == kpp.ERR_ARG
+    for v in (0, 4):
+        assert lib.kpp_set_kernel_variant(v) == kpp.ERR_ARG
+    used = ctypes.c_int32()
+    assert lib.kpp_block_gram(ctypes.byref(mat()), 0, 0.0, 0, dev, ctypes.byref(used), None) == kpp.ERR_ARG
+    assert lib.kpp_block_gram(ctypes.byref(mat()), 2000, 0.0, 0, dev, ctypes.byref(used), None) == kpp.ERR_ARG
+    assert lib.kpp_block_gram(ctypes.byref(mat()), 8, 0.0, 4, dev, ctypes.byref(used), None) == kpp.ERR_ARG
+    assert lib.kpp_block_gram(ctypes.byref(mat()), 8, 0.0, 0, None, ctypes.byref(used), None) == kpp.ERR_ARG
+    r = ctypes.c_double()
+    assert lib.kpp_rel_residual(ctypes.byref(mat()), dev, dev, None, None) == kpp.ERR_ARG
+    assert lib.kpp_rel_residual(ctypes.byref(mat()), None, dev, ctypes.byref(r), None) == kpp.ERR_ARG
+    hb = np.zeros(64)
+    assert lib.kpp_solve_host(ctypes.byref(mat()), hb.ctypes.data, hb.ctypes.data, 8, 2, ctypes.byref(prm),
+                              ctypes.byref(rep), None) == kpp.ERR_ARG                          # mode
+    assert kpp.last_error() != ""
