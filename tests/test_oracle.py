@@ -193,6 +193,46 @@ def test_momentum_matches_lemma_2_3_recursion():
     np.testing.assert_allclose(res.mom, m_T, rtol=1e-9, atol=1e-11)
 
 
+def test_fixed_momentum_meets_the_general_convergence_theorem():
+    """Sec. 2's general convergence theorem: with its mu and nu computed exactly by enumerating the blocks
+    of the partition, rho = rhobar / 2 (c = 1/2) and eta = 1 / (2 nu), the mean of |x_t - x*|^2 over
+    300 independent block sequences stays below 8 (1 - rho/2)^t |x_0 - x*|^2; and 1 <= nu <= 1/mu.  A weak,
+    statistical pin (the bound is loose), kept because it ties the momentum form to the theorem's rate."""
+    rng = np.random.default_rng(41)
+    m, n, s, lam = 60, 20, 6, 0.5
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = U @ np.diag(np.concatenate([np.geomspace(30, 10, 3), rng.uniform(1, 2, n - 3)])) @ V.T * math.sqrt(m / n)
+    xs = rng.standard_normal(n)
+    b = A @ xs
+    nb = m // s
+    Ps = []
+    for j in range(nb):
+        As = A[j * s:(j + 1) * s]
+        Ps.append(As.T @ np.linalg.solve(As @ As.T + lam * np.eye(s), As))
+    Pbar = sum(Ps) / nb
+    ev, Q = np.linalg.eigh(Pbar)
+    mu = ev.min()
+    Ph = Q @ np.diag(ev ** -0.5) @ Q.T
+    nu = np.linalg.eigvalsh(sum((Ph @ P @ Ph) @ (Ph @ P @ Ph) for P in Ps) / nb).max()
+    assert 1.0 <= nu <= 1.0 / mu
+    rho, eta = math.sqrt(mu / nu) / 2, 1.0 / (2.0 * nu)
+    L = oracle.kpp_factor(A, s, lam)
+    x0 = rng.standard_normal(n)
+    e0 = float(np.sum((x0 - xs) ** 2))
+    T, ch, S = 300, 10, 300
+    mean = np.zeros(T // ch)
+    for seed in range(S):
+        x, mom, st = x0.copy(), np.zeros(n), None
+        for c in range(T // ch):
+            r = oracle.run(A, b, L, s, lam=lam, tol=0.0, max_iters=(c + 1) * ch, seed=seed, adaptive=False, eta=eta,
+                           rho=rho, x0=x, mom0=mom, state=st)
+            x, mom, st = r.x, r.mom, r.state
+            mean[c] += float(np.sum((x - xs) ** 2)) / S
+    t = np.arange(1, T // ch + 1) * ch
+    assert np.all(mean <= 8.0 * (1.0 - rho / 2.0) ** t * e0)
+
+
 @pytest.mark.parametrize("adaptive", [False, True])
 def test_cdpp_is_kpp_on_a_square_root(adaptive):
     """Eq. 5.1 / proof of Thm 5.1: CD++ on A = Phi Phi^T is K++ on Phi z = b with z_t = Phi^T x_t."""
