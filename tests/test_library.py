@@ -202,3 +202,41 @@ def test_solver_entry_points_refuse_bad_arguments_on_the_host(lib):
     assert lib.kpp_solve_host(ctypes.byref(mat()), hb.ctypes.data, hb.ctypes.data, 8, 2, ctypes.byref(prm),
                               ctypes.byref(rep), None) == kpp.ERR_ARG                          # mode
     assert kpp.last_error() != ""
+
+
+def test_binding_structs_match_the_c_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets that a C compiler gives the
+    header's struct (gcc on include/kpp.h), so no field is read or written at the wrong place."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    structs = {"kpp_matrix": (kpp.Matrix, ["data", "dtype", "reserved", "rows", "cols", "ld"]),
+               "kpp_params": (kpp.Params, ["lambda", "tol", "max_iters", "seed", "sys_id", "adaptive_rho", "rho0",
+                                           "eta", "grid", "refine", "max_outer", "reserved0", "inner_tol",
+                                           "reserved1"]),
+               "kpp_report": (kpp.Report, ["iters", "outer", "rel_res_true", "rel_res_est", "rho_final", "status",
+                                           "bad_block", "device_ms", "kernel_ms", "launches", "reserved"]),
+               "kpp_serving_stats": (kpp.ServingStats, ["completed", "failed", "p50_ms", "p99_ms", "max_ms",
+                                                        "solves_per_s", "span_s", "peak_bytes", "budget_bytes",
+                                                        "reserved"])}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kpp.h"', "int main(void) {"]
+    for cname, (_, fields) in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, key, val = ln.split()
+        got[(cname, key)] = int(val)
+    for cname, (cls, fields) in structs.items():
+        assert ctypes.sizeof(cls) == got[(cname, "size")], cname
+        pyfields = [f for f, _ in cls._fields_]
+        assert len(pyfields) == len(fields), cname
+        for pf, cf in zip(pyfields, fields):
+            assert getattr(cls, pf).offset == got[(cname, cf)], (cname, cf)
