@@ -518,6 +518,21 @@ def test_rht_definition_holds_for_a_general_matrix(n):
         assert abs(oracle.rht_entry(d, A, i, j) - ref[i, j]) <= 1e-13 * n
 
 
+def test_symfht_count_at_4096_matches_the_papers_printed_rht_cost():
+    """The paper prints the RHT step's cost at n = 4096 as about 2.4e8 FLOPs (tests/golden/rht_flops_n4096.txt).
+    The oracle's SymFHT additions on a 4096 x 4096 symmetric matrix, plus the n^2 multiplications of the
+    scaling D A D, give that figure to its printed digits; the additions alone stay within the SymFHT
+    theorem's n^2 (2.5 + log2 n)."""
+    with open(os.path.join(GOLDEN, "rht_flops_n4096.txt")) as f:
+        n, printed, digits = next(ln.split() for ln in f if ln.strip() and not ln.startswith("#"))
+    n, printed, digits = int(n), float(printed), int(digits)
+    A = _sym(n, 5)
+    _, ops = oracle.symfht(A)
+    assert ops <= n * n * (2.5 + math.log2(n))
+    total = ops + n * n
+    assert float(f"{total:.{digits - 1}e}") == printed
+
+
 def test_rht_keeps_spectrum_and_solution():
     """Q is orthogonal: Q A Q^T has the eigenvalues of A, and Q^T (Q A Q^T)^{-1} Q b = A^{-1} b."""
     n = 32
