@@ -764,6 +764,27 @@ def test_proj_lsqr_converges_monotonically_to_the_regularised_projection():
     assert np.linalg.norm(w - w_star) <= 1e-10 * np.linalg.norm(w_star)
 
 
+@pytest.mark.parametrize("tau", [64, 128, 256])
+def test_proj_lsqr_meets_the_rate_of_its_lemma(tau):
+    """Sec. 4.1's inner-solver lemma, with its kappa measured: for r = A_S e the exact projection has
+    |[w; v]| <= sqrt(2) |e|, and LSQR from zero on the preconditioned system, of condition number kappa,
+    has |z_k - z*| <= kappa |M (z_k - z*)| / sigma_max <= 2 kappa q^k |z*|, q = (kappa - 1)/(kappa + 1).
+    So |w_k - w| <= 2 sqrt(2) kappa q^k |e| for every k."""
+    s, n, lam = 32, 300, 0.05
+    AS, _, _ = _proj_case(s, n, lam, 3)
+    e = np.random.default_rng(4).standard_normal(n)
+    r = AS @ e
+    w_star = np.linalg.solve(np.eye(n) * lam + AS.T @ AS, AS.T @ r)
+    T = np.sort(np.random.default_rng(5).choice(512, tau, replace=False))
+    L = oracle.proj_precond(AS, lam, T, W.rademacher_signs(512, 4))
+    sv = np.linalg.svd(np.linalg.solve(L, np.hstack([AS, math.sqrt(lam) * np.eye(s)])), compute_uv=False)
+    kappa = sv[0] / sv[-1]
+    q = (kappa - 1.0) / (kappa + 1.0)
+    for k in range(1, 9):
+        w, _ = oracle.proj_lsqr(AS, r, lam, L, k)
+        assert np.linalg.norm(w - w_star) <= 2.0 * math.sqrt(2.0) * kappa * q ** k * np.linalg.norm(e)
+
+
 def test_proj_preconditioned_condition_number_shrinks_with_the_sketch():
     """kappa(L^{-1} [A_S, sqrt(lam) I]) is 1 for the whole transform and, averaged over draws, smaller for
     a sketch of 8 s columns than for one of s columns; at 2 s it is a small constant."""
