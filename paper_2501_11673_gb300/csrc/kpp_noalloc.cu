@@ -8,6 +8,7 @@
 // scalars, barrier words, launch descriptor and residual partial sums) carved out of one file-scope
 // device array of fixed size.  The caller still passes the matrix, right-hand side, iterate and the
 // memoised factors.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -51,9 +52,10 @@ constexpr size_t NOALLOC_BYTES = OFF_ARGS + rup(sizeof(SysArgs));
 // stand-in.  The device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
-// Device address of the scratch, looked up once per device with that device current.
+// Device address of the scratch, looked up once per device with that device current.  The cache is
+// atomic so that first calls from several host threads do not race on it (they store the same value).
 static unsigned char *scratch_ptr(kpp_status *rc) {
-    static unsigned char *cached[64] = {nullptr};
+    static std::atomic<unsigned char *> cached[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 64) {
@@ -61,7 +63,8 @@ static unsigned char *scratch_ptr(kpp_status *rc) {
         *rc = KPP_ERR_CUDA;
         return nullptr;
     }
-    if (!cached[dev]) {
+    unsigned char *ptr = cached[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -69,9 +72,10 @@ static unsigned char *scratch_ptr(kpp_status *rc) {
             *rc = KPP_ERR_CUDA;
             return nullptr;
         }
-        cached[dev] = (unsigned char *)p;
+        ptr = (unsigned char *)p;
+        cached[dev].store(ptr, std::memory_order_release);
     }
-    return cached[dev];
+    return ptr;
 }
 
 }  // namespace kpp
