@@ -394,6 +394,8 @@ def test_adaptive_rho_follows_closed_form_windows_on_diagonal_systems(cd, n, s, 
     np.testing.assert_allclose(tr[:, 3], [0.0] + rho[:-1], rtol=0, atol=10 * rtol)
     assert res.state.rhat == pytest.approx(rhat[-1], rel=10 * rtol)
     assert res.state.rho == pytest.approx(rho[-1], rel=0, abs=10 * rtol)
+    # the reported estimate of Eq. 5.2 at the last checkpoint: sqrt(E1) / |b|
+    assert res.rel_res_est == pytest.approx(math.sqrt(ck[-1][2]) / np.linalg.norm(b), rel=rtol)
     np.testing.assert_allclose(res.x, b / d * (1.0 - cfac ** _draw_counts(n, s, 7, T)), rtol=1e-12)
     if kind == "inside":
         assert min(rho) > 0.0 and max(rho) < 1.0 - 1e-12
