@@ -45,10 +45,10 @@ METRIC = "time-to-1e-8 rel. residual & block-iters/s"
 SERVING_METRIC = "solves/s + p99 latency"
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the kernel as
-# built now, on the same workload (the summaries under profiles/ give the commands).  An entry goes
+# built now, on the same workload (the ncu summaries under profiles/ give the commands).  An entry goes
 # when its kernel changes; absent means not captured since (reported as null).  The cd4_kernel capture
-# in profiles/cd4_kernel_cdpp4096.md (7.133e9 bytes) predates the kernel's FP32 instantiation, which
-# changed its shared-memory layout, so it is context there and not reported here.
+# on the n = 4096 CD++ workload (7.133e9 bytes per launch) predates the kernel's FP32 instantiation,
+# which changed its shared-memory layout, so it is context in that summary and not reported here.
 NCU_TRAFFIC_PER_LAUNCH = {}
 
 
