@@ -135,3 +135,14 @@ def test_rademacher_signs():
     assert set(np.unique(d).tolist()) == {-1.0, 1.0} and abs(d.mean()) <= 4 / math.sqrt(4096)
     np.testing.assert_array_equal(d, W.rademacher_signs(4096, 16))
     assert not np.array_equal(d, W.rademacher_signs(4096, 17))
+
+
+def test_stays_spd_flags_a_rounded_matrix_whose_spectrum_crossed_the_margin():
+    """stays_spd(A, margin) is whether A - margin I is positive definite (the check that decides FP32
+    storage for a BF16-rounded serving matrix)."""
+    A, _ = W.torch_spd(32, 2, 1e2, 1e3, 1.0, 2.0, seed=9, dtype="f64", device="cpu")
+    lo = float(torch.linalg.eigvalsh(A).min())
+    assert W.stays_spd(A, 0.5 * lo) and not W.stays_spd(A, 1.5 * lo)
+    Ab, _ = W.torch_spd(32, 2, 1e2, 1e3, 1.0, 2.0, seed=9, dtype="bf16", device="cpu")
+    lob = float(torch.linalg.eigvalsh(Ab.double()).min())
+    assert W.stays_spd(Ab, 0.9 * lob) and not W.stays_spd(Ab, 1.1 * lob)
