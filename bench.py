@@ -336,6 +336,8 @@ class SingleFP64(Workload):
         iters = statistics.mean(st["iters"] for st in steps)
         out = {"cdpp_flops": {"iterations": self.per_iter()[0] * iters,
                               "factor_phase": nb * (s ** 3 / 3 + 2 * s * s * n)}}
+        if not getattr(self, "run_cg_reference", True):
+            return out
         try:
             out["cg_reference"] = cg_reference(self.Ad, self.bd, self.sy.tol)
         except Exception as exc:  # a failed reference point must not lose the bench line
@@ -912,6 +914,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cg-reference", action="store_true",
+                    help="cdpp4096: skip the plain CG reference point after the timed steps (e.g. for ncu)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -938,6 +942,7 @@ def main():
 
     W.HOST_QR = args.host_qr
     wl = make_workload(args)
+    wl.run_cg_reference = not args.no_cg_reference
     wl.setup(kpp, torch, rank)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
