@@ -135,6 +135,14 @@ kpp_status kpp_factor_blocks(const kpp_matrix *A, kpp_partition_t P, double lamb
 void kpp_factors_destroy(kpp_factors_t f);
 /* First block whose factorisation failed, or -1. */
 int64_t kpp_factors_bad_block(kpp_factors_t f);
+/* Device time of the factor phase that made f, in milliseconds, from events recorded on its stream:
+ * ms_out[0] the block Grams G_j = A_Sj A_Sj^T + lambda I (K++) or principal blocks (CD++),
+ * ms_out[1] the Cholesky of every block, ms_out[2] the inverses G_j^{-1}, ms_out[3] the memo
+ * W_j = G_j^{-1} A_Sj where one is built (about 0 otherwise).  NaN for a stage that did not run
+ * (a factor phase that failed early).  For measurement (Sec. 4's factor phase, the s^3/3 per block
+ * the paper counts).  ms_out: host, 4 doubles.  Waits for the phase's last event.
+ * Errors: KPP_ERR_ARG for a null argument. */
+kpp_status kpp_factors_stage_ms(kpp_factors_t f, double *ms_out);
 /* Copy the FP64 factor L_j (len x len, row-major, lower; len = length of block j) to host memory
  * `out` (len*len doubles).  For tests and inspection.  Errors: KPP_ERR_ARG for a bad j. */
 kpp_status kpp_factors_get_block(kpp_factors_t f, int64_t j, double *out_host);
@@ -194,7 +202,9 @@ kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t
  * exists for callers that cannot call cudaMalloc, such as a process whose GPU memory is owned by
  * another allocator (a serving runtime or framework pool that reserved the device) or a request
  * path that must not block on the allocator or fail half way with an out-of-memory error.
- * It runs the same kernel as cdpp_solve, with the same arguments and results.  The scratch
+ * It runs the general CD++ kernel with the launch shape cdpp_solve picks, i.e. what cdpp_solve runs
+ * after kpp_set_kernel_variant(1); the default variant's dataflow kernels reach the same iterates in
+ * another summation order.  Same arguments and results as cdpp_solve.  The scratch
  * (momentum, maintained residuals, projection buffer, scalars, barrier words, partial sums) lives
  * in one fixed device array of about 400 KiB inside the library.  Every GPU that loads the library
  * holds that array until the process exits.
@@ -273,6 +283,19 @@ kpp_status kpp_memo_sequence(uint64_t seed, uint32_t sys_id, int32_t mode, int64
  *   1: the general kernel always.
  * Not thread-safe with concurrent solves.  Errors: KPP_ERR_ARG for another value. */
 kpp_status kpp_set_kernel_variant(int32_t variant);
+
+/* Test hook for the bounded device waits (failure handling; no counterpart in the paper).  Every
+ * spin-wait of the persistent kernels (group barriers, mailbox polls, TMA completion waits) gives up
+ * after a time limit, marks the group's error word KPP_ERR_TIMEOUT, releases the other waiters and
+ * returns; the solve then returns KPP_ERR_TIMEOUT with x holding the last written iterate, and the
+ * CUDA context stays usable.
+ *   wait_ns:  the limit for every later launch; 0 restores the default (2 s).
+ *   hold_cta: -1 (default) off; c >= 0 makes CTA c of every system leave the general kernel before
+ *             its first group barrier without arriving, so that the other CTAs' wait runs out.  A solve
+ *             made while it is set must run the general kernel (kpp_set_kernel_variant(1)) on a grid of
+ *             more than c CTAs per system, else it returns KPP_ERR_UNSUPPORTED without launching.
+ * Process-wide, not thread-safe with concurrent solves.  Errors: KPP_ERR_ARG for hold_cta < -1. */
+kpp_status kpp_set_wait_test(uint64_t wait_ns, int32_t hold_cta);
 
 /* ------------------------------------------------------------------------------------------------
  * Serving: a continuous-batching request loop over registered matrices (host runtime in the library).
@@ -392,6 +415,11 @@ kpp_status kpp_tune_cache_load(const char *path);
 /* Number of kernel launches this library has issued in the process so far (every launch site counts
  * once; a captured graph's replays are not counted).  Host only, never fails. */
 uint64_t kpp_launch_count(void);
+
+/* Number of device allocations (cudaMalloc / cudaMallocAsync calls) this library has made in the
+ * process so far: factor sets, solve scratch, plans, the server's panels and the host-buffer solve.
+ * Allocations that cuBLAS makes on its own are not counted.  Host only, never fails. */
+uint64_t kpp_device_alloc_count(void);
 
 /* Library build information: "sm_103a; <compiler>; <date>". */
 const char *kpp_build_info(void);

@@ -34,6 +34,16 @@ void clear_error() { g_last_error.clear(); }
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static std::atomic<unsigned long long> g_allocs{0};
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(p, bytes);
+}
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocAsync(p, bytes, st);
+}
+
 // SM count of the current device, cached per device (atomic: the server's threads may ask first together).
 int sm_count() {
     static std::atomic<int> cached[64];
@@ -60,6 +70,10 @@ void FactorSet::release() {
     L = nullptr;
     Ginv = nullptr;
     Ginv32 = nullptr;
+    for (cudaEvent_t &e : ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
 }
 
 // |A x - b|^2 and |b|^2 per column (deterministic: fixed grid, host sums in a fixed order).
@@ -97,6 +111,10 @@ int auto_grid(int64_t cols, int nsys) {
 }
 
 int g_variant = 3;
+// The wait test (kpp_set_wait_test): the device wait limit of the persistent kernels (0: 2 s) and
+// the CTA that the general kernel holds back from its first group barrier (-1: none).
+static uint64_t g_wait_ns = 0;
+static int g_hold_cta = -1;
 
 kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, int dtype, bool cd, int k,
                                      int s, double eta, double tol, int adaptive, int confirm, int64_t max_iters,
@@ -182,9 +200,14 @@ kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, i
     cm.init_residual = init_residual ? 1 : 0;
     cm.max_iters = max_iters;
     cm.seed = seed;
-    cm.timeout_ns = 2000000000ull;
+    cm.timeout_ns = g_wait_ns ? g_wait_ns : 2000000000ull;
     cm.t0_state = t0_state ? 1 : 0;
+    cm.test_hold_cta = g_hold_cta;
     L.kind = v6 ? 6 : v4 ? 4 : v3 ? 3 : v2 ? 2 : 1;
+    if (g_hold_cta >= 0 && (L.kind != 1 || g_hold_cta >= G)) {
+        set_error("the wait test runs on the general kernel only (kernel variant 1), with a CTA index < %d", G);
+        return KPP_ERR_UNSUPPORTED;
+    }
     L.dtype = dtype;
     L.KP = KP;
     L.nsys = nsys;
@@ -688,6 +711,7 @@ const char *kpp_last_error(void) { return g_last_error.c_str(); }
 #define KPP_STR2(x) #x
 #define KPP_STR(x) KPP_STR2(x)
 uint64_t kpp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+uint64_t kpp_device_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 const char *kpp_build_info(void) {
     return "sm_103a; nvcc " KPP_STR(__CUDACC_VER_MAJOR__) "." KPP_STR(__CUDACC_VER_MINOR__) "; " __DATE__;
@@ -739,6 +763,23 @@ void kpp_factors_destroy(kpp_factors_t f) {
 
 int64_t kpp_factors_bad_block(kpp_factors_t f) { return f ? f->f.bad_block : -1; }
 
+kpp_status kpp_factors_stage_ms(kpp_factors_t f, double *ms_out) {
+    clear_error();
+    if (!f || !ms_out) {
+        set_error("kpp_factors_stage_ms: null argument");
+        return KPP_ERR_ARG;
+    }
+    for (int i = 0; i < 4; ++i) {
+        ms_out[i] = NAN;
+        float ms = 0.f;
+        const cudaEvent_t a = f->f.ev[i], b = f->f.ev[i + 1];
+        if (a && b && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            ms_out[i] = ms;
+    }
+    cudaGetLastError();
+    return KPP_OK;
+}
+
 kpp_status kpp_factors_get_block(kpp_factors_t f, int64_t j, double *out_host) {
     clear_error();
     if (!f || !out_host || j < 0 || j >= f->f.nb) {
@@ -787,6 +828,17 @@ kpp_status kpp_sample_blocks(uint64_t seed, uint32_t sys_id, int64_t t0, int64_t
         set_error("sample kernel: %s", cudaGetErrorString(e));
         return KPP_ERR_CUDA;
     }
+    return KPP_OK;
+}
+
+kpp_status kpp_set_wait_test(uint64_t wait_ns, int32_t hold_cta) {
+    clear_error();
+    if (hold_cta < -1) {
+        set_error("kpp_set_wait_test: hold_cta must be -1 or a CTA index");
+        return KPP_ERR_ARG;
+    }
+    g_wait_ns = wait_ns;
+    g_hold_cta = hold_cta;
     return KPP_OK;
 }
 
@@ -861,9 +913,9 @@ kpp_status kpp_solve_host(const kpp_matrix *A_host, const double *b_host, double
     kpp_partition_t P = nullptr;
     kpp_factors_t F = nullptr;
     kpp_matrix Ad = *A_host;
-    CUDA_OR(cudaMalloc(&dA, abytes), KPP_ERR_CUDA);
-    CUDA_OR(cudaMalloc((void **)&db, A_host->rows * sizeof(double)), KPP_ERR_CUDA);
-    CUDA_OR(cudaMalloc((void **)&dx, A_host->cols * sizeof(double)), KPP_ERR_CUDA);
+    CUDA_OR(dev_malloc(&dA, abytes), KPP_ERR_CUDA);
+    CUDA_OR(dev_malloc((void **)&db, A_host->rows * sizeof(double)), KPP_ERR_CUDA);
+    CUDA_OR(dev_malloc((void **)&dx, A_host->cols * sizeof(double)), KPP_ERR_CUDA);
     CUDA_OR(cudaMemcpy2DAsync(dA, A_host->cols * es, A_host->data, A_host->ld * es, A_host->cols * es, A_host->rows,
                               cudaMemcpyHostToDevice, st),
             KPP_ERR_CUDA);

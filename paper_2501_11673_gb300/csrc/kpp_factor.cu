@@ -413,18 +413,20 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
             goto done;                                                       \
         }                                                                    \
     } while (0)
-    KPP_TRY(cudaMalloc(&F.L, nb * blk * sizeof(double)));
+    KPP_TRY(dev_malloc((void **)&F.L, nb * blk * sizeof(double)));
     // 64 bytes of slack: the iteration kernels copy G^{-1} rows in 16-byte multiples, which can run up
     // to 8 bytes past the last block when its rows have an odd length
-    if (A.dtype == KPP_F64) KPP_TRY(cudaMalloc(&F.Ginv, nb * blk * sizeof(double) + 64));
-    else KPP_TRY(cudaMalloc(&F.Ginv32, nb * blk * sizeof(float) + 64));
-    KPP_TRY(cudaMalloc(&G, nb * blk * sizeof(double)));
-    KPP_TRY(cudaMalloc(&Linv, nb * blk * sizeof(double)));
-    KPP_TRY(cudaMalloc(&bad, sizeof(int)));
+    if (A.dtype == KPP_F64) KPP_TRY(dev_malloc((void **)&F.Ginv, nb * blk * sizeof(double) + 64));
+    else KPP_TRY(dev_malloc((void **)&F.Ginv32, nb * blk * sizeof(float) + 64));
+    KPP_TRY(dev_malloc((void **)&G, nb * blk * sizeof(double)));
+    KPP_TRY(dev_malloc((void **)&Linv, nb * blk * sizeof(double)));
+    KPP_TRY(dev_malloc((void **)&bad, sizeof(int)));
     {
         int big = 0x7fffffff;
         KPP_TRY(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, st));
     }
+    for (cudaEvent_t &e : F.ev) KPP_TRY(cudaEventCreate(&e));
+    KPP_TRY(cudaEventRecord(F.ev[0], st));
     if (mode == 0) {
         if (block_gram(A, s, lam, G, 0, st) < 0) {
             rc = KPP_ERR_CUDA;
@@ -440,8 +442,10 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     KPP_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(CHOL_PB * s * sizeof(double))));
     note_launch();
+    KPP_TRY(cudaEventRecord(F.ev[1], st));
     cholesky_kernel<<<(unsigned)nb, CHOL_NT, CHOL_PB * s * sizeof(double), st>>>(rows, s, G, F.L, bad);
     KPP_TRY(cudaGetLastError());
+    KPP_TRY(cudaEventRecord(F.ev[2], st));
     if (A.dtype == KPP_F64) {
         const int sm64 = 4 * IT * ITP * (int)sizeof(double);
         KPP_TRY(cudaFuncSetAttribute(inverse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
@@ -454,6 +458,7 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
         inverse_kernel<float><<<(unsigned)nb, INV_NT, sm32, st>>>(rows, s, F.L, (float *)Linv, F.Ginv32);
     }
     KPP_TRY(cudaGetLastError());
+    KPP_TRY(cudaEventRecord(F.ev[3], st));
     {
         int hb = 0;
         KPP_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -466,23 +471,24 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     }
     if (rc == KPP_OK && mode == 0 && A.dtype != KPP_F64 && kw_fits(A.dtype, rows, A.cols, s, 1, sm_count())) {
         // the large-block K++ kernel reads W_S = G^{-1} A_S instead of applying G^{-1} across the group
-        KPP_TRY(cudaMalloc(&F.W32, (size_t)rows * A.cols * sizeof(float)));
+        KPP_TRY(dev_malloc((void **)&F.W32, (size_t)rows * A.cols * sizeof(float)));
         rc = build_w32(A, s, F.Ginv32, F.W32, st);
         if (rc != KPP_OK) goto done;
     }
     if (rc == KPP_OK && mode == 1 && A.dtype != KPP_F64 && rows % s == 0 && s <= 64) {
         // CD++ inner FP32 iterations on one right-hand side read W_S = G^{-1} A_S (FP32), as FP64 reads W
-        KPP_TRY(cudaMalloc(&F.W32, (size_t)rows * A.cols * sizeof(float)));
+        KPP_TRY(dev_malloc((void **)&F.W32, (size_t)rows * A.cols * sizeof(float)));
         rc = build_w32(A, s, F.Ginv32, F.W32, st);
         if (rc != KPP_OK) goto done;
     }
     if (rc == KPP_OK && mode == 1 && A.dtype == KPP_F64) {
-        KPP_TRY(cudaMalloc(&F.W, (size_t)rows * rows * sizeof(double)));
+        KPP_TRY(dev_malloc((void **)&F.W, (size_t)rows * rows * sizeof(double)));
         dim3 grid((unsigned)nb, (unsigned)((rows + 63) / 64));
         note_launch();
         cd_w_kernel<<<grid, 256, 0, st>>>((const double *)A.data, A.ld, rows, s, F.Ginv, F.W);
         KPP_TRY(cudaGetLastError());
     }
+    KPP_TRY(cudaEventRecord(F.ev[4], st));
 done:
 #undef KPP_TRY
     if (G) cudaFree(G);

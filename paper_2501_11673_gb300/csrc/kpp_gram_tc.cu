@@ -307,8 +307,8 @@ bool gram_tc(const kpp_matrix &A, int s, double lam, double *G, cudaStream_t st,
     GramTile *d_tiles = nullptr;
     int *d_err = nullptr;
     int herr = 0;
-    bool ok = cudaMallocAsync((void **)&d_tiles, tl.size() * sizeof(GramTile), st) == cudaSuccess;
-    ok = ok && cudaMallocAsync((void **)&d_err, sizeof(int), st) == cudaSuccess;
+    bool ok = dev_malloc_async((void **)&d_tiles, tl.size() * sizeof(GramTile), st) == cudaSuccess;
+    ok = ok && dev_malloc_async((void **)&d_err, sizeof(int), st) == cudaSuccess;
     ok = ok && cudaMemsetAsync(d_err, 0, sizeof(int), st) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(d_tiles, tl.data(), tl.size() * sizeof(GramTile), cudaMemcpyHostToDevice, st) ==
                    cudaSuccess;

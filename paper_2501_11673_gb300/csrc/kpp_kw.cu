@@ -55,6 +55,11 @@ __device__ __forceinline__ unsigned kw_cluster_rank() {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
 }
+__device__ __forceinline__ unsigned kw_cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
 __device__ __forceinline__ void kw_cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -166,6 +171,13 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
     __shared__ float s_beta;
 
     GroupSync gs{sys.bar, sys.err, 0u, (unsigned)cm.G, cm.timeout_ns};
+    // Every distributed-shared-memory address below assumes clusters of KW_CL CTAs.  A launch without
+    // them (the host always sets the attribute) is refused here, uniformly over the grid, before any
+    // shared-memory window of another CTA or any copy is touched.
+    if (kw_cluster_size() != (unsigned)KW_CL) {
+        if (threadIdx.x == 0) group_fail(gs, KPP_ERR_UNSUPPORTED);
+        return;
+    }
     const int zeta = nb;
     const int64_t t_begin = cm.t0_state ? sys.sc[0].t : sys.t0;
     int64_t t = t_begin;
@@ -217,10 +229,24 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
         __syncthreads();
         if (!group_barrier(gs)) s_fail = 1;
     }
-    if (s_fail) t_end = t;  // uniform: a failed group barrier fails in every CTA
+    // A failure here must end the step loop for all CTAs of a cluster together: a CTA that skipped the
+    // loop would meet its peers' first in-loop cluster barrier with its final one and leave while they
+    // still read its shared memory.  So the flags are OR-ed over the cluster first.
+    if (threadIdx.x == 0) s_flag = s_fail;
+    kw_cluster_sync();
+    if (threadIdx.x < KW_CL && kw_ld_cluster_s32(kw_mapa(&s_flag, threadIdx.x))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) t_end = t;  // uniform over the cluster
 
     {
+        // A buffer whose last copy was never seen complete (its wait timed out) is not given a new copy:
+        // that would arm its barrier a second time while the first copy may still be landing.
         auto issueA = [&](int64_t tt, int i) {
+            if (s_pendA[i]) {
+                s_fail = 1;
+                group_fail(gs, KPP_ERR_TIMEOUT);
+                return;
+            }
             const int j = draw_block(cm.seed, tt, sys.sys_id, nb);
             const int S0 = j * s;
             mbar_arrive_expect_tx(&mbA[i], (unsigned)(s * KW_CW * sizeof(TA)));
@@ -229,6 +255,11 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
             s_pendA[i] = 1;
         };
         auto issueW = [&](int64_t tt, int i) {
+            if (s_pendW[i]) {
+                s_fail = 1;
+                group_fail(gs, KPP_ERR_TIMEOUT);
+                return;
+            }
             const int j = draw_block(cm.seed, tt, sys.sys_id, nb);
             const int S0 = j * s;
             mbar_arrive_expect_tx(&mbW[i], (unsigned)(s * KW_CW * 4));
@@ -451,14 +482,17 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
     __syncthreads();
     kw_cluster_sync();
     for (int c = threadIdx.x; c < KW_CW; c += NT) x[c0 + c] = xc[c];
+    // Drain: every copy issued to this CTA's shared memory lands before the CTA leaves.  A copy
+    // from valid global memory always completes; the (longer) limit only keeps the wait bounded.
     if (threadIdx.x == 0) {
+        const uint64_t drain_ns = 4 * cm.timeout_ns;
         for (int i = 0; i < 2; ++i) {
             if (s_pendA[i]) {
-                if (mbar_wait_bounded(&mbA[i], s_phA[i], cm.timeout_ns)) s_phA[i] ^= 1u;
+                if (mbar_wait_bounded(&mbA[i], s_phA[i], drain_ns)) s_phA[i] ^= 1u;
                 else group_fail(gs, KPP_ERR_TIMEOUT);
             }
             if (s_pendW[i]) {
-                if (mbar_wait_bounded(&mbW[i], s_phW[i], cm.timeout_ns)) s_phW[i] ^= 1u;
+                if (mbar_wait_bounded(&mbW[i], s_phW[i], drain_ns)) s_phW[i] ^= 1u;
                 else group_fail(gs, KPP_ERR_TIMEOUT);
             }
         }
@@ -561,7 +595,7 @@ template <typename TA> static int kw_max_clusters(int s) {
     return ncl;
 }
 
-// Whether nsys systems of `cols` columns fit co-resident as 8-CTA clusters (clusters live inside a GPC).
+// Whether nsys systems of `cols` columns fit co-resident as 4-CTA clusters (clusters live inside a GPC).
 bool kw_can_launch(int dtype, int s, int64_t cols, int nsys) {
     const int need = (int)(nsys * kw_grid(cols) / KW_CL);
     const int have = dtype == KPP_BF16 ? kw_max_clusters<__nv_bfloat16>(s) : kw_max_clusters<float>(s);

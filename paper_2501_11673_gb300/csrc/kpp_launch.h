@@ -50,7 +50,7 @@ struct Scratch {
     std::vector<void *> ptrs;
     explicit Scratch(cudaStream_t s, bool stream_ordered = true) : st(s), ordered(stream_ordered) {}
     cudaError_t alloc(void **p, size_t bytes) {
-        cudaError_t e = ordered ? cudaMallocAsync(p, bytes ? bytes : 16, st) : cudaMalloc(p, bytes ? bytes : 16);
+        cudaError_t e = ordered ? dev_malloc_async(p, bytes ? bytes : 16, st) : dev_malloc(p, bytes ? bytes : 16);
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
     }

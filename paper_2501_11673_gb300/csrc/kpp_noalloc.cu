@@ -3,8 +3,10 @@
 // Some callers cannot call cudaMalloc: a process whose device memory is owned by another allocator
 // (a serving runtime or framework pool that has already reserved the GPU and forbids allocations
 // behind its back), or a request path that must never block on the allocator or fail half way with
-// an out-of-memory error.  For them this entry point runs the same persistent CD++ kernel as
-// cdpp_solve, with all of its scratch (momentum, maintained residuals, projection buffer, per-solve
+// an out-of-memory error.  For them this entry point runs the general persistent CD++ kernel
+// (kpp_solve.cu's solve_kernel: what cdpp_solve runs after kpp_set_kernel_variant(1); the default
+// variant picks the dataflow kernels instead, which reach the same iterates in another summation
+// order), with the same launch shape and all of its scratch (momentum, maintained residuals, projection buffer, per-solve
 // scalars, barrier words, launch descriptor and residual partial sums) carved out of one file-scope
 // device array of fixed size.  The caller still passes the matrix, right-hand side, iterate and the
 // memoised factors.
@@ -13,17 +15,9 @@
 #include <cstring>
 
 #include "kpp_internal.cuh"
+#include "kpp_launch.h"
 #include "kpp_runtime.h"
 #include "kpp_solve.h"
-
-struct kpp_partition_s {
-    int64_t rows;
-    int32_t s;
-    int64_t nb;
-};
-struct kpp_factors_s {
-    kpp::FactorSet f;
-};
 
 namespace kpp {
 
@@ -109,11 +103,13 @@ extern "C" kpp_status cdpp_solve_noalloc(const kpp_matrix *A, const double *b, d
     cudaStream_t st = (cudaStream_t)stream;
     const kpp_params p = *pp;
 
-    // grid and column chunk exactly as cdpp_solve picks them for one system
-    int G = p.grid > 0 ? p.grid : (int)std::max<int64_t>(1, std::min<int64_t>((n + 31) / 32, sm_count()));
+    // grid and column chunk exactly as cdpp_solve picks them for one system (auto_grid, the chunk
+    // rounded to a 32-byte sector, then no CTA without columns)
+    int G = p.grid > 0 ? p.grid : auto_grid(n, 1);
     if (G > NOALLOC_MAX_G) G = NOALLOC_MAX_G;
     int64_t CW = (n + G - 1) / G;
     CW = (CW + 3) / 4 * 4;
+    G = (int)((n + CW - 1) / CW);
     Common cm{};
     cm.rows = n;
     cm.cols = n;
@@ -131,6 +127,7 @@ extern "C" kpp_status cdpp_solve_noalloc(const kpp_matrix *A, const double *b, d
     cm.max_iters = p.max_iters;
     cm.seed = p.seed;
     cm.timeout_ns = 2000000000ull;
+    cm.test_hold_cta = -1;
     if (solve_smem_bytes(s, 1, CW, 8) > 220 * 1024) {
         set_error("cdpp_solve_noalloc: shared memory limit exceeded");
         return KPP_ERR_UNSUPPORTED;

@@ -25,6 +25,9 @@ struct FactorSet {
     float *Ginv32 = nullptr;  // nb x s x s, FP32 copy (FP32/BF16 storage only)
     double *W = nullptr;      // CD++ FP64 only: rows x cols, block j rows = G_j^{-1} A_{S_j} (row-major, ld cols)
     float *W32 = nullptr;     // K++ with FP32/BF16 storage, large-block kernel only: G_j^{-1} A_{S_j} in FP32
+    // Device time of the factor phase's stages (kpp_factors_stage_ms): events recorded on the stream
+    // before the Grams / principal blocks, then after the Cholesky, the inverses and the W memo.
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     void release();
 };
 
@@ -56,5 +59,10 @@ int sm_count();
 
 // Kernel launches issued by the library (every launch site calls note_launch; kpp_launch_count).
 void note_launch();
+
+// Device allocations made by the library: every cudaMalloc / cudaMallocAsync of libkpp goes through
+// these two, which count the calls (kpp_device_alloc_count).
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
 
 }  // namespace kpp

@@ -150,8 +150,8 @@ void run_request(kpp_server_s *sv, const std::shared_ptr<Request> &r) {
             if (fr != KPP_OK) rc = fr;
         }
     }
-    if (rc == KPP_OK && (cudaMallocAsync((void **)&dB, rows * k * 8, st) != cudaSuccess ||
-                         cudaMallocAsync((void **)&dX, cols * k * 8, st) != cudaSuccess))
+    if (rc == KPP_OK && (kpp::dev_malloc_async((void **)&dB, rows * k * 8, st) != cudaSuccess ||
+                         kpp::dev_malloc_async((void **)&dX, cols * k * 8, st) != cudaSuccess))
         rc = KPP_ERR_OOM;
     if (rc == KPP_OK) {
         cudaMemcpyAsync(dB, r->B.data(), rows * k * 8, cudaMemcpyHostToDevice, st);

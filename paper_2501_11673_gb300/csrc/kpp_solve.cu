@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const SysArgs *__restrict_
             double v = block_sum<NT>(acc[c], s_part);
             if (threadIdx.x == 0) sa.rpart[(size_t)g * KP + c] = v;
         }
+        if (g == cm.test_hold_cta) goto finish;  // wait test: leave without arriving
         if (!group_barrier(gs)) goto finish;
         if (threadIdx.x < KP) {
             double t = 0.0;

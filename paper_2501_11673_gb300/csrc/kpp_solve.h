@@ -51,6 +51,8 @@ struct Common {
     uint64_t seed;
     uint64_t timeout_ns;
     int t0_state;          // 1: start at sc[0].t (written by the previous launch) and run max_iters more steps
+    int test_hold_cta;     // wait test (general kernel only): this CTA of each group never arrives at the
+                           // first group barrier, so the others' bounded wait runs out; -1: off
 };
 
 size_t solve_smem_bytes(int s, int KP, int64_t CW, size_t tc_size);

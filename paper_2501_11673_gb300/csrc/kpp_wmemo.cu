@@ -55,7 +55,7 @@ kpp_status build_w32(const kpp_matrix &A, int s, const float *Ginv32, float *W32
         chunk = (int64_t)((512ull << 20) / ((size_t)bsz * 4));
         if (chunk < 1) chunk = 1;
         if (chunk > nb) chunk = nb;
-        if (cudaMallocAsync(&tmp, (size_t)chunk * bsz * 4, st) != cudaSuccess) {
+        if (dev_malloc_async((void **)&tmp, (size_t)chunk * bsz * 4, st) != cudaSuccess) {
             set_error("out of device memory for the W memo");
             return KPP_ERR_OOM;
         }

@@ -29,13 +29,13 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NUMERIC, ERR_NO_CONVERGENCE, ER
 
 # Every symbol include/kpp.h declares (checked by the CPU test suite against the built library).
 EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_partition", "kpp_partition_destroy",
-           "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block",
+           "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block", "kpp_factors_stage_ms",
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
-           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_block_gram", "kpp_server_create", "kpp_server_add_matrix",
+           "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_set_wait_test", "kpp_block_gram", "kpp_server_create", "kpp_server_add_matrix",
            "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_reset_stats", "kpp_server_destroy",
            "cdpp_solve_batched", "kpp_plan_create", "kpp_plan_launch", "kpp_plan_report", "kpp_plan_info",
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
-           "kpp_tune_cache_load", "kpp_launch_count", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
+           "kpp_tune_cache_load", "kpp_launch_count", "kpp_device_alloc_count", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
            "kpp_memo_sequence"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
@@ -107,6 +107,8 @@ def load(path: str | None = None):
         lib.kpp_factors_destroy.argtypes = [vp]
         lib.kpp_factors_bad_block.argtypes = [vp]
         lib.kpp_factors_bad_block.restype = i64
+        lib.kpp_factors_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.kpp_factors_stage_ms.restype = ctypes.c_int
         lib.kpp_factors_get_block.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
         for name in ("kpp_solve", "cdpp_solve", "cdpp_solve_noalloc"):
             f = getattr(lib, name)
@@ -120,6 +122,7 @@ def load(path: str | None = None):
         lib.cdpp_solve_batched.argtypes = lib.kpp_solve_batched.argtypes
         lib.cdpp_solve_batched.restype = ctypes.c_int
         lib.kpp_set_kernel_variant.argtypes = [i32]
+        lib.kpp_set_wait_test.argtypes = [ctypes.c_uint64, i32]
         lib.kpp_server_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)]
         lib.kpp_server_add_matrix.argtypes = [vp, ctypes.POINTER(Matrix), i32, dbl, i32, ctypes.POINTER(i32)]
         lib.kpp_server_submit.argtypes = [vp, i32, vp, i32, ctypes.POINTER(Params), ctypes.POINTER(i64)]
@@ -154,6 +157,7 @@ def load(path: str | None = None):
         lib.kpp_plan_destroy.restype = None
         lib.kpp_tune_cache_size.restype = i64
         lib.kpp_launch_count.restype = ctypes.c_uint64
+        lib.kpp_device_alloc_count.restype = ctypes.c_uint64
         lib.kpp_tune_cache_clear.restype = None
         lib.kpp_tune_cache_save.argtypes = [ctypes.c_char_p]
         lib.kpp_tune_cache_load.argtypes = [ctypes.c_char_p]
@@ -266,6 +270,13 @@ class Factors:
     def bad_block(self) -> int:
         return int(self._lib.kpp_factors_bad_block(self.handle))
 
+    def stage_ms(self) -> dict:
+        """Device time (ms) of the factor phase's stages: Grams (or principal blocks), Cholesky,
+        inverses, W memo."""
+        out = (ctypes.c_double * 4)()
+        _check(self._lib.kpp_factors_stage_ms(self.handle, out))
+        return dict(zip(("gram", "cholesky", "inverse", "wmemo"), list(out)))
+
     def block(self, j: int):
         """FP64 lower Cholesky factor of block j as a numpy array."""
         import numpy as np
@@ -307,8 +318,9 @@ def cdpp_solve(A, b, x, P: Partition, F: Factors, prm: Params, stream=None, allo
 def cdpp_solve_noalloc(A, b, x, P: Partition, F: Factors, prm: Params, stream=None,
                        allow_no_conv: bool = False) -> Report:
     """CD++ FP64 through the entry point that allocates no device memory (fixed internal scratch;
-    n <= 16384, s <= 256).  For callers that cannot allocate device memory; same results as
-    cdpp_solve.  Calls must not overlap on the GPU."""
+    n <= 16384, s <= 256).  For callers that cannot allocate device memory.  It runs the general
+    CD++ kernel with cdpp_solve's launch shape, i.e. what cdpp_solve runs after set_kernel_variant(1).
+    Calls must not overlap on the GPU."""
     rep = Report()
     m = matrix(A)
     rc = load().cdpp_solve_noalloc(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
@@ -379,6 +391,11 @@ class Plan:
 def launch_count() -> int:
     """Kernel launches the library has issued in this process."""
     return int(load().kpp_launch_count())
+
+
+def device_alloc_count() -> int:
+    """Device allocations (cudaMalloc / cudaMallocAsync) the library has made in this process."""
+    return int(load().kpp_device_alloc_count())
 
 
 def tune_cache_size() -> int:
@@ -548,6 +565,12 @@ def set_kernel_variant(v: int) -> None:
     """1: general kernel everywhere; 2: small-block kernel where the shape allows it; 3 (default): as 2,
     and the dataflow kernel for CD++ where the shape allows it."""
     _check(load().kpp_set_kernel_variant(int(v)))
+
+
+def set_wait_test(wait_ns: int = 0, hold_cta: int = -1) -> None:
+    """Test hook: the device wait limit of later launches (0: the default 2 s) and the CTA that the
+    general kernel holds back from its first group barrier (-1: none), so that a bounded wait runs out."""
+    _check(load().kpp_set_wait_test(int(wait_ns), int(hold_cta)))
 
 
 def build_info() -> str:

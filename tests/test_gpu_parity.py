@@ -509,7 +509,7 @@ def test_streaming_kernel_uneven_short_chunks_track_general_kernel(K, dtype, k):
 
 @pytest.mark.parametrize("dtype", ["bf16", "f32"])
 def test_large_block_kernel_tracks_general_kernel_in_fp32(K, dtype):
-    """The large-block K++ kernel (memoised W = G^-1 A_S, one exchange per step over 8-CTA clusters)
+    """The large-block K++ kernel (memoised W = G^-1 A_S, one exchange per step over 4-CTA clusters)
     against the general kernel on the same FP32 iteration: iterates agree to FP32 rounding after T steps,
     and both refine to 1e-8 with the same solution."""
     sy = W.kpp_mixed_lowrank(m=16384, n=512, s=128, n_out=16)
