@@ -7,19 +7,20 @@ Inputs are resident in HBM before the timed region; L2 is flushed (512 MiB write
 outside each step's event pair.
 
 Workloads (synthetic and seeded; recipes in paper_2501_11673_gb300/workloads.py):
-  cdpp4096 (default)  CD++ FP64, dense SPD n=4096, 50 outliers 1e2..1e4 over U[1,10], s=64, lambda=1e-4
-  kpp2000             K++ FP64, 2000x200 consistent LS, 10 outliers 1e2..1e3 over U[1,2], s=20, lambda=1e-3
-  mixed262144         K++ on 262144x4096 LS stored BF16 (--storage f32 for FP32), 100 outliers 10..1000
+  mixed262144 (default)  K++ on 262144x4096 LS stored BF16 (--storage f32 for FP32), 100 outliers 10..1000
                       over U[0.5,1], s=512, lambda=1e-3, FP32 iterations + FP64 refinement, b = A x*
-                      (--noisy: b = A x* + 1e-6 N(0,I); the attained residual is reported, no tolerance)
+                      (--noisy: b = A x* + 1e-6 N(0,I); the attained residual is reported, no tolerance);
+                      after the timed steps the plain FP64 K++ path solves the same system once
+  cdpp4096            CD++ FP64, dense SPD n=4096, 50 outliers 1e2..1e4 over U[1,10], s=64, lambda=1e-4
+  kpp2000             K++ FP64, 2000x200 consistent LS, 10 outliers 1e2..1e3 over U[1,2], s=20, lambda=1e-3
   batched64           64 systems 2048x65536 FP32 (20 rows x100), 8 right-hand sides each, s=256,
                       lambda = 1e-3 median |a_i|^2, refinement; one autotuned plan replayed as a CUDA graph
   serving             1024 CD++ requests, Poisson arrivals (2 ms mean gap) over a catalog of 32 SPD matrices
                       (n log-uniform 512..8192, BF16 / FP32), k = 1..32, refinement, 120 GiB budget
   cdpp4096-f32 / -bf16  the cdpp4096 system stored FP32 / BF16 with FP64 refinement
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a bounded sample of
-the same workload instead (rank 0 only).
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on every host core on a
+bounded sample of the same workload instead (rank 0 only, no GPU).
 """
 from __future__ import annotations
 
@@ -46,10 +47,12 @@ SERVING_METRIC = "solves/s + p99 latency"
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the kernel as
 # built now, on the same workload (the ncu summaries under profiles/ give the commands).  An entry goes
-# when its kernel changes; absent means not captured since (reported as null).  The cd4_kernel capture
-# on the n = 4096 CD++ workload (7.133e9 bytes per launch) predates the kernel's FP32 instantiation,
-# which changed its shared-memory layout, so it is context in that summary and not reported here.
-NCU_TRAFFIC_PER_LAUNCH = {}
+# when its kernel changes; absent means not captured since (reported as null).
+NCU_TRAFFIC_PER_LAUNCH = {
+    # cd4_kernel, n = 4096 CD++ FP64, one launch = one solve of 23168 iterations
+    # (profiles/cd4_kernel_cdpp4096.md: 7.1217e9 read + 0.0203e9 written)
+    "cd4_kernel/cdpp4096": 7.142e9,
+}
 
 
 def _log(msg):
@@ -64,9 +67,24 @@ def _peaks():
         return {}
 
 
-def fp64_peak_gflops(peaks):
-    """FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x the maximum SM clock."""
-    return 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+# FP64 FMA lanes per clock per SM on this GPU, measured by a throughput probe (4+ warps issuing
+# independent DFMA): a warp-wide FP64 instruction holds an SMSP's FP64 pipe for about 76 cycles.
+FP64_LANES_MEASURED = 1.68
+FP64_LANES_NOMINAL = 2.0
+
+
+def fp64_peak_gflops(peaks, lanes=FP64_LANES_MEASURED):
+    """FP64 FMA pipe: 152 SMs x lanes FMA/clk x 2 flop x the maximum SM clock."""
+    return 152 * lanes * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+
+
+FP64_PEAK_SOURCE = ("derived: 152 SMs x 1.68 FP64 FMA lanes/clk/SM (measured by a DFMA throughput probe on this "
+                    "pool's GB300) x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)")
+
+
+def fp64_peak_nominal(peaks):
+    return {"peak": fp64_peak_gflops(peaks, FP64_LANES_NOMINAL),
+            "source": "nominal: 152 SMs x 2 FP64 FMA/clk x 2 flop x sm_max_mhz"}
 
 
 class ClockSampler:
@@ -141,6 +159,85 @@ def _oracle_iter_rate(A, b, L, s, cd, lam, seed, budget_s, it0=64):
         if dt > budget_s / 4 or it >= (1 << 22):
             return it / dt, it, dt
         it *= 4
+
+
+def _cpu_info():
+    """Host cores this process may run on, and the CPU model (lscpu, else the platform's name)."""
+    import platform
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def _oracle_worker(paths, s, cd, lam, seed, sys_id, iters, barrier, q):
+    """One all-cores oracle worker (spawned): maps the sample, waits for the others, times `iters`
+    block iterations of its own Philox stream."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import oracle
+    A = np.load(paths[0], mmap_mode="r")
+    b = np.load(paths[1])
+    L = np.load(paths[2], mmap_mode="r")
+    oracle.run(A, b, L, s, cd=cd, lam=lam, tol=0.0, max_iters=2, seed=seed, sys=sys_id, confirm=False)
+    barrier.wait()
+    t0 = time.perf_counter()
+    oracle.run(A, b, L, s, cd=cd, lam=lam, tol=0.0, max_iters=iters, seed=seed, sys=sys_id, confirm=False)
+    q.put(time.perf_counter() - t0)
+
+
+def _oracle_rate_all_cores(A, b, L, s, cd, lam, seed, one_core_rate, budget_s):
+    """Block iterations per second of the oracle as it stands on every host core: one single-threaded
+    oracle process per core (spawned, so no process is forked from one that holds a CUDA context), each
+    on its own Philox stream of the same sample, started together; value = all iterations / the slowest
+    worker's time.  Returns (value, cores, cpu model, iterations per worker, slowest seconds)."""
+    import multiprocessing as mp
+    import shutil
+    import tempfile
+    cores, model = _cpu_info()
+    iters = max(4, int(one_core_rate * budget_s / 2))
+    tmp = tempfile.mkdtemp(prefix="kpp_oracle_sample_")
+    try:
+        paths = [os.path.join(tmp, nm) for nm in ("A.npy", "b.npy", "L.npy")]
+        for pth, arr in zip(paths, (A, b, L)):
+            np.save(pth, np.ascontiguousarray(arr, dtype=np.float64))
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(cores)
+        q = ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker, args=(paths, s, cd, lam, seed, i, iters, barrier, q))
+                 for i in range(cores)]
+        for pr in procs:
+            pr.start()
+        times = [q.get(timeout=max(600.0, 20 * budget_s)) for _ in procs]
+        for pr in procs:
+            pr.join(timeout=60)
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    slow = max(times)
+    return cores * iters / slow, cores, model, iters, slow
+
+
+def _cpu_baseline_both(A, b, L, s, cd, lam, seed, budget_s, unit, what, it0=16):
+    """The oracle on one host thread and on every host core (the line's value is the all-cores one)."""
+    v1, it1, dt1 = _oracle_iter_rate(A, b, L, s, cd, lam, seed, budget_s, it0=it0)
+    out = {"value": v1, "unit": unit, "cores": 1, "kind": "oracle",
+           "sample": f"{it1} {what}, one host thread ({dt1:.1f} s; factor phase excluded)"}
+    try:
+        va, cores, model, ita, dta = _oracle_rate_all_cores(A, b, L, s, cd, lam, seed, v1, budget_s)
+        out = {"value": va, "unit": unit, "cores": cores, "kind": "oracle", "cpu_model": model,
+               "sample": f"{cores} x {ita} {what}, one single-threaded oracle process per host core on its own "
+                         f"block sequence, started together (slowest {dta:.1f} s; factor phase excluded)",
+               "one_core": out}
+    except Exception as exc:  # the single-thread figure still stands
+        out["all_cores_error"] = f"{type(exc).__name__}: {exc}"
+    return out
 
 
 def _oracle_factors(A, s, lam, cd):
@@ -316,12 +413,13 @@ class SingleFP64(Workload):
         ach = iters / launches * flops / (per_launch_ms / 1e3) / 1e9
         achb = iters / launches * byts / (per_launch_ms / 1e3) / 1e9
         pk = fp64_peak_gflops(peaks)
+        nom = fp64_peak_nominal(peaks)
         hbm = peaks.get("hbm_gbs", 6800.0)
         return {"kernel": self.kernel, "bound": "alu", "achieved": ach, "peak": pk, "unit": "GFLOP/s",
                 "frac": ach / pk, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(f"{self.kernel}/{self.name}"),
                 "launch_ms": per_launch_ms, "per_iter": {"flops": flops, "bytes": byts},
-                "peak_source": "derived: FP64 FMA pipe, 152 SMs x 2 FMA/clk x 2 flop x sm_max_mhz "
-                               "(MEASURED_PEAKS.json sm_max_mhz)",
+                "peak_source": FP64_PEAK_SOURCE,
+                "nominal_peak": {**nom, "frac": ach / nom["peak"]},
                 "hbm_view": {"achieved": achb, "peak": hbm, "unit": "GB/s", "frac": achb / hbm,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
 
@@ -372,11 +470,8 @@ class SingleFP64(Workload):
 
     def cpu_baseline(self, budget_s):
         L = _oracle_factors(self.sy.A, self.sy.s, self.sy.lam, self.cd)
-        v, it, dt = _oracle_iter_rate(self.sy.A, self.sy.b, L, self.sy.s, self.cd, self.sy.lam, self.seed,
-                                      budget_s, it0=256)
-        return {"value": v, "unit": self.unit, "cores": 1, "kind": "oracle",
-                "sample": f"{it} block iterations of the same workload, FP64 C oracle, one host thread "
-                          f"({dt:.1f} s; factor phase excluded)"}
+        return _cpu_baseline_both(self.sy.A, self.sy.b, L, self.sy.s, self.cd, self.sy.lam, self.seed, budget_s,
+                                  self.unit, "block iterations of the same workload (FP64 C oracle)", it0=256)
 
 
 class MixedSPD(SingleFP64):
@@ -493,9 +588,9 @@ class RhtSPD(SingleFP64):
 
 
 class MixedLS(Workload):
-    """K++ on a 262144 x 4096 LS stored BF16 / FP32, FP32 iterations + FP64 refinement."""
-
-    kernel = "kw_kernel"
+    """K++ on a 262144 x 4096 LS stored BF16 / FP32, FP32 iterations + FP64 refinement (the default
+    workload).  After the timed steps the plain FP64 K++ path solves the same system (the stored matrix
+    widened to FP64) once, for the comparison of the two forms on the same GPU."""
 
     def __init__(self, storage="bf16", noisy=False, m=262144, n=4096, s=512):
         self.storage, self.noisy = storage, noisy
@@ -503,14 +598,17 @@ class MixedLS(Workload):
         # BF16 blocks of up to 512 rows take the W-memo kernel; FP32 storage of 512-row blocks does not fit
         # its shared memory and stays on the small-block kernel
         self.kernel = "kw_kernel" if storage == "bf16" else "solve2_kernel"
+        self.name = f"mixed{m}-{storage}"
         self.lam = 1e-3
         self.tol = 1e-8
-        self.dtype = "f32"
+        self.dtype = "f32"  # the arithmetic of the iterations (BF16 entries are widened exactly to FP32)
+        self.run_fp64_reference = True
         noise = ("b = A_stored x* + 1e-6 N(0,I) (noisy variant: attained residual reported, no tolerance)"
                  if noisy else "b = A_stored x* (noise-free headline)")
         self.desc = (f"K++ mixed precision, {m}x{n} LS A=Z D V^T stored {storage.upper()} (Z~N(0,1/m), V Haar, "
                      f"100 outliers log-spaced 10..1000 + U[0.5,1]), {noise}, s={s}, lambda=1e-3, "
-                     "FP32 iterations + FP64 refinement (inner tol 1e-3), tol 1e-8, x0=0")
+                     "tensor-core block Grams, FP64 Cholesky, FP32 iterations + FP64 refinement (inner tol 1e-3), "
+                     "tol 1e-8 on the FP64 residual, x0=0")
 
     def setup(self, kpp, torch, rank):
         self.kpp, self.torch = kpp, torch
@@ -527,32 +625,95 @@ class MixedLS(Workload):
         self.x.zero_()
         F = kpp.Factors(self.A, self.P, self.lam, 0)
         rep = kpp.kpp_solve(self.A, self.b, self.x, self.P, F, self.prm, allow_no_conv=self.noisy)
+        stages = F.stage_ms()
         del F
         ok = rep.rel_res_true <= self.tol if not self.noisy else math.isfinite(rep.rel_res_true)
         return {"units": rep.iters, "ok": ok, "kernel_ms": rep.kernel_ms, "kernel_launches": rep.launches,
-                "iters": rep.iters, "outer": rep.outer, "rel_res": rep.rel_res_true}
+                "iters": rep.iters, "outer": rep.outer, "rel_res": rep.rel_res_true, "stages": stages}
 
     def per_iter_bytes(self):
         esz = 2 if self.storage == "bf16" else 4
         s, n = self.s, self.n
         # the method's bytes: A_S once, G_S^-1 (FP32), x and m read + written (FP32), r_S and y
-        # (the kernel also streams the memoised W_S = G^-1 A_S, s x n FP32, which is not counted here)
         return s * n * esz + s * s * 4 + 4 * n * 4 + 2 * s * 4
 
-    def roofline(self, steps, peaks):
-        byts = self.per_iter_bytes()
+    def per_iter_bytes_kernel(self):
+        """What the block-step kernel reads besides: the memoised W_S = G_S^-1 A_S (s x n FP32) in place of
+        G_S^-1 (the large-block kernel; the small-block kernel reads G_S^-1 as the method does)."""
+        if self.kernel != "kw_kernel":
+            return self.per_iter_bytes()
+        return self.per_iter_bytes() - self.s * self.s * 4 + self.s * self.n * 4
+
+    def block_step(self, steps, peaks):
+        """The block step (S2-S6) against HBM: algorithmic bytes per iteration x iterations / the
+        iteration kernel's device time (CUDA events around its launches)."""
+        byts, kbyts = self.per_iter_bytes(), self.per_iter_bytes_kernel()
         iters = statistics.mean(st["iters"] for st in steps)
         kms = statistics.mean(st["kernel_ms"] for st in steps)
         launches = statistics.mean(st["kernel_launches"] for st in steps)
-        return _hbm_roof(self.kernel, iters * byts / launches, kms / launches, peaks,
-                         f"{self.kernel}/mixed262144-{self.storage}", {"bytes": byts})
+        out = _hbm_roof(self.kernel, iters * byts / launches, kms / launches, peaks, f"{self.kernel}/{self.name}",
+                        {"bytes": byts})
+        ach_k = iters * kbyts / (kms / 1e3) / 1e9
+        out["us_per_iter"] = 1e3 * kms / iters
+        out["with_memo_reads"] = {"bytes_per_iter": kbyts, "achieved": ach_k, "frac": ach_k / out["peak"],
+                                  "note": "counting the memo W_S the kernel streams as well (s x n FP32)"}
+        return out
+
+    def roofline(self, steps, peaks):
+        """The dominant kernel of the step: the FP64 Cholesky of every block, or the block-step kernel,
+        whichever took more device time (events on the launching stream for both)."""
+        st = steps[-1]["stages"]
+        chol_ms = statistics.mean(x["stages"]["cholesky"] for x in steps)
+        kms = statistics.mean(x["kernel_ms"] for x in steps)
+        self._block = self.block_step(steps, peaks)
+        if not (chol_ms > kms):
+            return self._block
+        nb = -(-self.m // self.s)
+        flops = nb * self.s ** 3 / 3.0
+        ach = flops / (chol_ms / 1e3) / 1e9
+        pk = fp64_peak_gflops(peaks)
+        nom = fp64_peak_nominal(peaks)
+        return {"kernel": "cholesky_kernel", "bound": "alu", "achieved": ach, "peak": pk, "unit": "GFLOP/s",
+                "frac": ach / pk, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(f"cholesky_kernel/{self.name}"),
+                "launch_ms": chol_ms, "per_launch": {"flops": flops, "blocks": nb, "s": self.s,
+                                                     "count": "s^3/3 per block (the paper's Cholesky count)"},
+                "peak_source": FP64_PEAK_SOURCE, "nominal_peak": {**nom, "frac": ach / nom["peak"]},
+                "factor_stages_ms": st}
 
     def extra(self, steps):
         x_err = float(((self.x - self.x_star).norm() / self.x_star.norm()).item())
-        out = {"outer_steps": steps[-1]["outer"], "x_rel_err_vs_x_star": x_err}
+        stages = {k: statistics.mean(x["stages"][k] for x in steps) for k in steps[-1]["stages"]}
+        out = {"outer_steps": steps[-1]["outer"], "x_rel_err_vs_x_star": x_err, "factor_stages_ms": stages,
+               "block_step": self._block}
         if self.noisy:
             out["attained_rel_res"] = steps[-1]["rel_res"]
+        if self.run_fp64_reference and not self.noisy:
+            try:
+                out["fp64_reference"] = self.fp64_reference()
+            except Exception as exc:  # a failed reference point must not lose the bench line
+                out["fp64_reference"] = {"error": f"{type(exc).__name__}: {exc}"}
         return out
+
+    def fp64_reference(self):
+        """The plain FP64 K++ path on the same system (the stored matrix widened to FP64, the same b):
+        FP64 block Grams and Cholesky, FP64 iterations to 1e-8, one run timed with events."""
+        kpp, torch = self.kpp, self.torch
+        A64 = self.A.double()
+        x = torch.zeros(self.n, dtype=torch.float64, device="cuda")
+        prm = kpp.params(lam=self.lam, tol=self.tol, seed=0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        F = kpp.Factors(A64, self.P, self.lam, 0)
+        rep = kpp.kpp_solve(A64, self.b, x, self.P, F, prm)
+        e1.record()
+        e1.synchronize()
+        stages = F.stage_ms()
+        del F, A64
+        return {"what": "plain FP64 K++ (FP64 storage of the same stored values, FP64 Grams, Cholesky and "
+                        "iterations, no refinement) on the same system and GPU, one run after the timed steps",
+                "time_to_tol_ms": e0.elapsed_time(e1), "iters": rep.iters, "rel_res_true": rep.rel_res_true,
+                "solve_kernel_ms": rep.kernel_ms, "factor_stages_ms": stages, "status": rep.status}
 
     def e2e(self):
         """Host buffers (pinned) in and out around the public calls: A, b to the device, factor, solve, x back."""
@@ -577,17 +738,34 @@ class MixedLS(Workload):
                 "d2h_bytes_per_step": self.n * 8, "time_to_tol_ms": 1e3 * ets[-1],
                 "note": "pinned host buffers copied in and out around kpp_factor_blocks + kpp_solve"}
 
-    def cpu_baseline(self, budget_s):
-        """Oracle iterations on the first 16 blocks (8192 rows x 4096) of the stored matrix widened to
-        FP64: the same per-iteration work (s x n); factor phase excluded."""
-        rows = 16 * self.s
+    def oracle_sample(self, blocks=16):
+        """The first `blocks` blocks (blocks x s rows x n) of the stored matrix widened to FP64, with b and
+        the block factors; the oracle's per-iteration work is the workload's (one s x n block)."""
+        rows = blocks * self.s
         A = np.ascontiguousarray(self.A[:rows].double().cpu().numpy())
         b = np.ascontiguousarray(self.b[:rows].cpu().numpy())
-        L = _factors_numpy_gram(A, self.s, self.lam)
-        v, it, dt = _oracle_iter_rate(A, b, L, self.s, False, self.lam, 0, budget_s, it0=16)
-        return {"value": v, "unit": self.unit, "cores": 1, "kind": "oracle",
-                "sample": f"{it} FP64 oracle block iterations (s={self.s}, n={self.n}) on the first {rows} rows of "
-                          f"the stored matrix widened to FP64, one host thread ({dt:.1f} s; factor phase excluded)"}
+        return A, b, _factors_numpy_gram(A, self.s, self.lam), rows
+
+    def cpu_baseline(self, budget_s):
+        A, b, L, rows = self.oracle_sample()
+        return _cpu_baseline_both(A, b, L, self.s, False, self.lam, 0, budget_s, self.unit,
+                                  f"FP64 oracle block iterations (s={self.s}, n={self.n}) on the first {rows} rows "
+                                  "of the stored matrix widened to FP64", it0=16)
+
+
+def host_mixed_sample(m=262144, n=4096, s=512, blocks=16, storage="bf16"):
+    """A host-built sample of the mixed-precision workload for the reference arm (no GPU): `blocks`
+    blocks of s rows of A = Z D V^T with Z ~ N(0, 1/m) (the full system's scaling), V Haar n x n and the
+    planted spectrum, rounded to the storage type, b = A_sample x*.  Same shapes and distributions as
+    the device-built system, not the same values."""
+    rng = np.random.default_rng(2)
+    rows = blocks * s
+    z = rng.standard_normal((rows, n)) * (1.0 / math.sqrt(m))
+    v = W.haar_orthogonal(n, rng)
+    d = W.planted_spectrum(n, 100, 10.0, 1000.0, 0.5, 1.0, rng)
+    A = W.round_to_storage(np.ascontiguousarray(z @ (d[:, None] * v.T)), storage)
+    b = A @ np.random.default_rng(103).standard_normal(n)
+    return A, b
 
 
 class Batched(Workload):
@@ -859,33 +1037,46 @@ def aggregate_ranks(total_ms, total_units, dist=None, device="cuda"):
 
 
 def run_reference(args, rank: int):
-    """The FP64 CPU oracle on the host cores, each step a bounded sample of the same workload."""
+    """The FP64 CPU oracle on every host core, each step a bounded sample of the same workload (rank 0
+    only; no GPU is touched).  A step runs one single-threaded oracle process per core, each on its own
+    block sequence, started together; the step's time is the slowest process's."""
     if rank != 0:
         return
-    import oracle
     wl = make_workload(args)
-    if type(wl) is not SingleFP64:
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the FP64 workloads "
-                          "(cdpp4096, kpp2000); the other workloads report it as cpu_baseline"}), flush=True)
+    if isinstance(wl, MixedLS):
+        A, b = host_mixed_sample(wl.m, wl.n, wl.s, 16, wl.storage)
+        s, cd, lam, seed, it0 = wl.s, False, wl.lam, 0, 16
+        L = _factors_numpy_gram(A, s, lam)
+        what = (f"FP64 oracle block iterations (s={s}, n={wl.n}) on a host-built {A.shape[0]}-row sample of the "
+                f"workload (same recipe and scaling, {wl.storage.upper()}-rounded, widened to FP64)")
+        dtype = wl.dtype
+    elif type(wl) is SingleFP64:
+        sy, cd = wl.sy, wl.cd
+        A, b, s, lam, seed, it0 = sy.A, sy.b, sy.s, sy.lam, wl.seed, 256
+        L = _oracle_factors(A, s, lam, cd)
+        what = "FP64 oracle block iterations of the workload"
+        dtype = "f64"
+    else:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-system workloads "
+                          "(mixed262144, cdpp4096, kpp2000); the batched and serving workloads report it as "
+                          "cpu_baseline"}), flush=True)
         return
-    sy, cd = wl.sy, wl.cd
-    L = _oracle_factors(sy.A, sy.s, sy.lam, cd)
-    sample_iters = args.ref_iters
-    times = []
+    v1, _, _ = _oracle_iter_rate(A, b, L, s, cd, lam, seed, 8.0, it0=it0)
+    times, iters, cores, model = [], 0, 1, ""
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        r = oracle.run(sy.A, sy.b, L, sy.s, cd=cd, lam=sy.lam, tol=0.0, max_iters=sample_iters, seed=wl.seed)
-        dt = time.perf_counter() - t0
+        va, cores, model, ita, dta = _oracle_rate_all_cores(A, b, L, s, cd, lam, seed, v1, 8.0)
         if i >= args.warmup:
-            times.append(dt)
-        assert r.iters == sample_iters
-    v = sample_iters / statistics.mean(times)
-    sample = f"{sample_iters} oracle block iterations of the workload per step (factor phase excluded)"
+            times.append(dta)
+            iters = ita
+    v = cores * iters / statistics.mean(times)
+    sample = (f"{cores} x {iters} {what} per step, one single-threaded oracle process per host core "
+              "(factor phase excluded)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "block-iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": wl.desc},
-            "cpu_baseline": {"value": v, "unit": "block-iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "block-iters/s", "cores": cores, "cpu_model": model,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "block-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -896,7 +1087,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cdpp4096",
+    ap.add_argument("--workload", default="mixed262144",
                     choices=["cdpp4096", "kpp2000", "mixed262144", "batched64", "serving", "cdpp4096-f32",
                              "cdpp4096-bf16", "cdpp4096-rht"])
     ap.add_argument("--storage", default="bf16", choices=["bf16", "f32"], help="mixed262144 storage type")
@@ -916,6 +1107,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cg-reference", action="store_true",
                     help="cdpp4096: skip the plain CG reference point after the timed steps (e.g. for ncu)")
+    ap.add_argument("--no-fp64-reference", action="store_true",
+                    help="mixed262144: skip the plain FP64 K++ solve of the same system after the timed steps")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -943,6 +1136,7 @@ def main():
     W.HOST_QR = args.host_qr
     wl = make_workload(args)
     wl.run_cg_reference = not args.no_cg_reference
+    wl.run_fp64_reference = not args.no_fp64_reference
     wl.setup(kpp, torch, rank)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")

@@ -64,6 +64,7 @@ typedef struct {
 /* Library-owned handles. */
 typedef struct kpp_partition_s *kpp_partition_t;
 typedef struct kpp_factors_s *kpp_factors_t;
+typedef struct kpp_state_s *kpp_state_t;
 
 /* Solver parameters.  Fill with kpp_params_default() and override fields as needed. */
 typedef struct {
@@ -135,6 +136,12 @@ kpp_status kpp_factor_blocks(const kpp_matrix *A, kpp_partition_t P, double lamb
 void kpp_factors_destroy(kpp_factors_t f);
 /* First block whose factorisation failed, or -1. */
 int64_t kpp_factors_bad_block(kpp_factors_t f);
+/* Copy rows row0 .. row0+nrows-1 of the FP32 memo W (block j's rows: W_j = G_j^{-1} A_{S_j}, Sec. 4's
+ * projection folded into one operator; rows x cols, row-major) to host memory out_host (nrows * cols
+ * floats).  The memo exists for BF16 / FP32 storage where the large-block K++ kernel or the
+ * single-column CD++ kernel takes the shape.  For tests and inspection.  Errors: KPP_ERR_ARG when f
+ * holds no FP32 memo or the rows are out of range; KPP_ERR_CUDA. */
+kpp_status kpp_factors_get_memo(kpp_factors_t f, int64_t row0, int64_t nrows, float *out_host);
 /* Device time of the factor phase that made f, in milliseconds, from events recorded on its stream:
  * ms_out[0] the block Grams G_j = A_Sj A_Sj^T + lambda I (K++) or principal blocks (CD++),
  * ms_out[1] the Cholesky of every block, ms_out[2] the inverses G_j^{-1}, ms_out[3] the memo
@@ -168,6 +175,68 @@ kpp_status kpp_solve(const kpp_matrix *A, const double *b, double *x, kpp_partit
  * kpp_factor_blocks(mode 1); A is n x n. */
 kpp_status cdpp_solve(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P,
                       kpp_factors_t F, const kpp_params *p, kpp_report *rep, void *stream);
+
+/* ---- Krylov reference solvers (the comparison systems of Sec. 6) --------------------------------
+ * FP64 solves of A x = b on the GPU for the time-to-tolerance comparison with CD++ / K++ on the same
+ * system, one persistent cooperative launch each.  The paper counts their cost in flops: CG
+ * 2n^2 + 11n per iteration, GMRES 2n^2 T + 4n T (T + 1) after T iterations.
+ * kpp_cg: plain conjugate gradients for symmetric positive definite A (n x n FP64, row-major,
+ *   ld >= n), x0 from x: r = b - A x, p = r; per iteration q = A p, alpha = r.r / p.q, x += alpha p,
+ *   r -= alpha q, beta = r'.r' / r.r, p = r + beta p; stops when |r| <= tol |b| for the recurrence
+ *   residual r, or after max_iters iterations.
+ * kpp_gmres: restarted GMRES(restart) for any nonsingular square A (same layout), x0 from x; Arnoldi
+ *   with classical Gram-Schmidt and one reorthogonalisation pass, Givens rotations; an inner step stops
+ *   when the rotated residual |g_{j+1}| <= tol |b|, a cycle ends after `restart` steps with x += V y and
+ *   the true residual starts the next one; max_iters counts Arnoldi steps (1 <= restart <= 512).
+ * b, x: device FP64 vectors of n entries (x in: x0, out: the last iterate).  rep (host): iters
+ *   (iterations / Arnoldi steps), outer (GMRES cycles), rel_res_true (|Ax - b| / |b| in FP64, computed
+ *   after the solve), rel_res_est (the recurrence's estimate), kernel_ms.  Errors: KPP_ERR_ARG;
+ *   KPP_ERR_NO_CONVERGENCE (x holds the last iterate); KPP_ERR_NUMERIC; KPP_ERR_TIMEOUT (a bounded
+ *   device wait ran out); KPP_ERR_CUDA; KPP_ERR_OOM for the scratch (GMRES: (restart + 1) n doubles).
+ *   Synchronises `stream`. */
+kpp_status kpp_cg(const kpp_matrix *A, const double *b, double *x, double tol, int64_t max_iters, kpp_report *rep,
+                  void *stream);
+kpp_status kpp_gmres(const kpp_matrix *A, const double *b, double *x, int32_t restart, double tol, int64_t max_iters,
+                     kpp_report *rep, void *stream);
+
+/* ---- Checkpoint and resume ----------------------------------------------------------------------
+ * The state of the iteration after step t (Alg. 5 for K++, Alg. 3 for CD++): the momentum m of
+ * Eq. 1.4 (cols x k); for CD++ also the maintained residual R_x = A x - b and R_m = A m of Eq. 5.1
+ * (rows x k); and per right-hand-side column the window sums E0 / E1, the weighted ratio rhat and
+ * rho of Eq. 5.2 - 5.3, the checkpoint count, the next step index t, the active flag and the status.
+ * The iterate x stays the caller's (device, cols x k).
+ *
+ * kpp_state_create: a fresh state (t = 0, m = 0) for a system of rows x cols (CD++: cd = 1 and
+ *   rows = cols) with k right-hand sides (1..32); device memory owned by the handle.  Errors: ARG,
+ *   OOM, CUDA.
+ * kpp_solve_resume / cdpp_solve_resume: run p->max_iters more steps from the state, or fewer if every
+ *   column meets the stop rule, then leave the state at the last step.  The first call on a fresh state
+ *   starts from x (x0) with m = 0 (CD++: R_x = A x0 - b, R_m = 0) and takes rho0 from p.  Arguments and
+ *   errors as for kpp_solve / cdpp_solve, with A FP64 (other storage: KPP_ERR_UNSUPPORTED) and b, x
+ *   panels of the state's k columns; the state's shape must match (else KPP_ERR_ARG).  p->refine is
+ *   ignored.  The solve runs on the general persistent kernel, which keeps m, R_x and R_m in the
+ *   state's device memory, so a solve split into calls at any step follows the uninterrupted one
+ *   bitwise when p (seed, sys_id, grid, lambda, tol, eta) is the same in every call.  rep->iters is the
+ *   state's step index t after the call.  Synchronises `stream`.
+ * kpp_state_bytes: size of the flat checkpoint of the state and x.
+ * kpp_state_save: copy the state and x (device, cols x k FP64) into host_buf (at least
+ *   kpp_state_bytes bytes).  kpp_state_load: restore a saved checkpoint into a state of the same
+ *   shape, rows, cols, k and method, and its x into x.  The checkpoint is a header, the per-column
+ *   scalars as this library lays them out, then x, m and for CD++ R_x and R_m, all FP64; it is meant
+ *   for this library on machines of the same byte order.  Errors: ARG (null, short buffer, another
+ *   shape or not a checkpoint), CUDA.  Both synchronise `stream`.
+ * kpp_state_step: the state's next step index t (-1 for a null handle).
+ * There is no counterpart in the paper for the save / load format itself. */
+kpp_status kpp_state_create(int64_t rows, int64_t cols, int32_t k, int32_t cd, kpp_state_t *out);
+void kpp_state_destroy(kpp_state_t st);
+int64_t kpp_state_step(kpp_state_t st);
+size_t kpp_state_bytes(kpp_state_t st);
+kpp_status kpp_state_save(kpp_state_t st, const double *x, void *host_buf, size_t bytes, void *stream);
+kpp_status kpp_state_load(kpp_state_t st, double *x, const void *host_buf, size_t bytes, void *stream);
+kpp_status kpp_solve_resume(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
+                            const kpp_params *p, kpp_state_t st, kpp_report *rep, void *stream);
+kpp_status cdpp_solve_resume(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
+                             const kpp_params *p, kpp_state_t st, kpp_report *rep, void *stream);
 
 /* End-to-end host variants: A (rows x cols, dtype per A->dtype, row-major), b and x are HOST
  * pointers.  The call copies A and b to the device, factors, solves and copies x back.  Device

@@ -237,8 +237,20 @@ kpp_status prepare_persistent(PersistentLaunch &L, std::vector<SysInput> &sys, i
         a.b = sys[i].b;
         a.x = sys[i].x;
         a.Ginv = f64 ? (const void *)sys[i].F->Ginv : (const void *)sys[i].F->Ginv32;
-        CUDA_OR(scr.alloc(&a.m, L.vec_n * tcs), KPP_ERR_CUDA);
-        if (cd) {
+        if (sys[i].m_ext) {
+            if (L.kind != 1 || (cd && (!sys[i].Rx_ext || !sys[i].Rm_ext))) {
+                set_error("a solve with a kept state runs on the general kernel (kernel variant 1)");
+                return KPP_ERR_UNSUPPORTED;
+            }
+            L.keep_state = true;
+            a.m = sys[i].m_ext;
+        } else {
+            CUDA_OR(scr.alloc(&a.m, L.vec_n * tcs), KPP_ERR_CUDA);
+        }
+        if (cd && sys[i].m_ext) {
+            a.Rx = sys[i].Rx_ext;
+            a.Rm = sys[i].Rm_ext;
+        } else if (cd) {
             // v2 keeps two published copies of R_x (steps of even / odd index); v1 and v3 one
             CUDA_OR(scr.alloc(&a.Rx, (L.kind == 2 ? 2 : 1) * L.vec_r * tcs), KPP_ERR_CUDA);
             CUDA_OR(scr.alloc(&a.Rm, L.vec_r * tcs), KPP_ERR_CUDA);
@@ -351,6 +363,7 @@ kpp_status enqueue_persistent(const PersistentLaunch &L, cudaStream_t st, cudaEv
     CUDA_OR(cudaMemsetAsync(L.errs, 0, L.nsys * sizeof(int), st), KPP_ERR_CUDA);
     for (int i = 0; i < L.nsys; ++i) {
         const SysArgs &a = L.args[i];
+        if (L.keep_state) continue;  // the caller's state carries m, R_x and R_m over from the last launch
         CUDA_OR(cudaMemsetAsync(a.m, 0, L.vec_n * L.tcs, st), KPP_ERR_CUDA);
         if (L.cd) {
             CUDA_OR(cudaMemsetAsync(a.Rm, 0, L.vec_r * L.tcs, st), KPP_ERR_CUDA);
@@ -762,6 +775,22 @@ void kpp_factors_destroy(kpp_factors_t f) {
 }
 
 int64_t kpp_factors_bad_block(kpp_factors_t f) { return f ? f->f.bad_block : -1; }
+
+kpp_status kpp_factors_get_memo(kpp_factors_t f, int64_t row0, int64_t nrows, float *out_host) {
+    clear_error();
+    if (!f || !out_host || !f->f.W32 || row0 < 0 || nrows < 0 || row0 + nrows > f->f.rows) {
+        set_error("kpp_factors_get_memo: no FP32 memo in these factors, or rows out of range");
+        return KPP_ERR_ARG;
+    }
+    const int64_t cols = f->f.memo_cols;
+    cudaError_t e = cudaMemcpy(out_host, f->f.W32 + row0 * cols, (size_t)nrows * cols * sizeof(float),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_error("cudaMemcpy: %s", cudaGetErrorString(e));
+        return KPP_ERR_CUDA;
+    }
+    return KPP_OK;
+}
 
 kpp_status kpp_factors_stage_ms(kpp_factors_t f, double *ms_out) {
     clear_error();

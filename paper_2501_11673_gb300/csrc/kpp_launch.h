@@ -75,6 +75,10 @@ struct SysInput {
     uint32_t sys_id;
     SolveScalars *sc_host; // k entries, in/out (one-shot launches)
     SolveScalars *sc_dev = nullptr;  // k entries on the device, owned by the caller (plans); no copies
+    // Solver state kept by the caller between launches (resumable solves, kpp_state_t): momentum
+    // (cols x k) and, for CD++, R_x and R_m (rows x k).  The launch reads and writes them in place and
+    // neither zeroes nor re-initialises them; only the general kernel takes them.
+    void *m_ext = nullptr, *Rx_ext = nullptr, *Rm_ext = nullptr;
 };
 
 // A persistent-kernel launch over nsys systems that share shape, dtype, s and k, prepared once:
@@ -86,6 +90,7 @@ struct PersistentLaunch {
                    // 7 single-column dataflow CD++ over a memo
     int dtype = 0, KP = 1, nsys = 0, k = 1;
     bool cd = false, f64 = false, init_residual = true;
+    bool keep_state = false;  // the systems' m / R_x / R_m are the caller's state (SysInput::m_ext)
     int64_t t0 = 0;
     Common cm{};
     std::vector<SysArgs> args;

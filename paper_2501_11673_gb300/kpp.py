@@ -29,14 +29,15 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NUMERIC, ERR_NO_CONVERGENCE, ER
 
 # Every symbol include/kpp.h declares (checked by the CPU test suite against the built library).
 EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_partition", "kpp_partition_destroy",
-           "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block", "kpp_factors_stage_ms",
+           "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block", "kpp_factors_stage_ms", "kpp_factors_get_memo",
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
            "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_set_wait_test", "kpp_block_gram", "kpp_server_create", "kpp_server_add_matrix",
            "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_reset_stats", "kpp_server_destroy",
            "cdpp_solve_batched", "kpp_plan_create", "kpp_plan_launch", "kpp_plan_report", "kpp_plan_info",
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
            "kpp_tune_cache_load", "kpp_launch_count", "kpp_device_alloc_count", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
-           "kpp_memo_sequence"]
+           "kpp_memo_sequence", "kpp_state_create", "kpp_state_destroy", "kpp_state_step",
+           "kpp_state_bytes", "kpp_state_save", "kpp_state_load", "kpp_solve_resume", "cdpp_solve_resume", "kpp_cg", "kpp_gmres"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
 
@@ -109,6 +110,8 @@ def load(path: str | None = None):
         lib.kpp_factors_bad_block.restype = i64
         lib.kpp_factors_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         lib.kpp_factors_stage_ms.restype = ctypes.c_int
+        lib.kpp_factors_get_memo.argtypes = [vp, i64, i64, ctypes.POINTER(ctypes.c_float)]
+        lib.kpp_factors_get_memo.restype = ctypes.c_int
         lib.kpp_factors_get_block.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
         for name in ("kpp_solve", "cdpp_solve", "cdpp_solve_noalloc"):
             f = getattr(lib, name)
@@ -145,6 +148,26 @@ def load(path: str | None = None):
         lib.kpp_memo_sequence.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i32, i64, i64, i32, i64, i64, i64, i64p,
                                           i64p, i64, i64p]
         lib.kpp_memo_sequence.restype = ctypes.c_int
+        lib.kpp_state_create.argtypes = [i64, i64, i32, i32, ctypes.POINTER(vp)]
+        lib.kpp_state_create.restype = ctypes.c_int
+        lib.kpp_state_destroy.argtypes = [vp]
+        lib.kpp_state_destroy.restype = None
+        lib.kpp_state_step.argtypes = [vp]
+        lib.kpp_state_step.restype = i64
+        lib.kpp_state_bytes.argtypes = [vp]
+        lib.kpp_state_bytes.restype = ctypes.c_size_t
+        lib.kpp_state_save.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
+        lib.kpp_state_save.restype = ctypes.c_int
+        lib.kpp_state_load.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
+        lib.kpp_state_load.restype = ctypes.c_int
+        lib.kpp_cg.argtypes = [ctypes.POINTER(Matrix), vp, vp, dbl, i64, ctypes.POINTER(Report), vp]
+        lib.kpp_cg.restype = ctypes.c_int
+        lib.kpp_gmres.argtypes = [ctypes.POINTER(Matrix), vp, vp, i32, dbl, i64, ctypes.POINTER(Report), vp]
+        lib.kpp_gmres.restype = ctypes.c_int
+        for name in ("kpp_solve_resume", "cdpp_solve_resume"):
+            getattr(lib, name).argtypes = [ctypes.POINTER(Matrix), vp, vp, vp, vp, ctypes.POINTER(Params), vp,
+                                           ctypes.POINTER(Report), vp]
+            getattr(lib, name).restype = ctypes.c_int
         for name in ("kpp_set_kernel_variant", "cdpp_solve_noalloc", "kpp_sample_blocks", "kpp_partition", "kpp_factor_blocks", "kpp_factors_get_block", "kpp_solve", "cdpp_solve",
                      "kpp_solve_host", "kpp_rel_residual", "kpp_solve_batched"):
             getattr(lib, name).restype = ctypes.c_int
@@ -277,6 +300,14 @@ class Factors:
         _check(self._lib.kpp_factors_stage_ms(self.handle, out))
         return dict(zip(("gram", "cholesky", "inverse", "wmemo"), list(out)))
 
+    def memo(self, row0: int, nrows: int, cols: int):
+        """Rows row0 .. row0+nrows-1 of the FP32 memo W (W_j = G_j^-1 A_Sj) as a numpy array."""
+        import numpy as np
+        out = np.zeros((nrows, cols), dtype=np.float32)
+        _check(self._lib.kpp_factors_get_memo(self.handle, int(row0), int(nrows),
+                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
     def block(self, j: int):
         """FP64 lower Cholesky factor of block j as a numpy array."""
         import numpy as np
@@ -326,6 +357,70 @@ def cdpp_solve_noalloc(A, b, x, P: Partition, F: Factors, prm: Params, stream=No
     rc = load().cdpp_solve_noalloc(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                    P.handle, F.handle, ctypes.byref(prm), ctypes.byref(rep), _stream_ptr(stream))
     return _report_or_raise(rc, rep, allow_no_conv)
+
+
+def cg(A, b, x, tol: float = 1e-8, max_iters: int = 100000, stream=None, allow_no_conv: bool = False) -> Report:
+    """kpp_cg: plain FP64 conjugate gradients on the GPU; x holds x0 and receives the result."""
+    rep = Report()
+    m = matrix(A)
+    rc = load().kpp_cg(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol),
+                       int(max_iters), ctypes.byref(rep), _stream_ptr(stream))
+    return _report_or_raise(rc, rep, allow_no_conv)
+
+
+def gmres(A, b, x, restart: int = 256, tol: float = 1e-8, max_iters: int = 100000, stream=None,
+          allow_no_conv: bool = False) -> Report:
+    """kpp_gmres: restarted FP64 GMRES on the GPU; x holds x0 and receives the result."""
+    rep = Report()
+    m = matrix(A)
+    rc = load().kpp_gmres(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                          int(restart), float(tol), int(max_iters), ctypes.byref(rep), _stream_ptr(stream))
+    return _report_or_raise(rc, rep, allow_no_conv)
+
+
+class State:
+    """Solver state between calls (kpp_state_*): momentum, CD++ residuals, per-column window scalars and
+    the next step index, in device memory owned by the handle."""
+
+    def __init__(self, rows: int, cols: int, k: int = 1, cd: bool = False):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.kpp_state_create(int(rows), int(cols), int(k), int(cd), ctypes.byref(h)))
+        self.handle, self.rows, self.cols, self.k, self.cd = h, rows, cols, k, cd
+
+    @property
+    def step(self) -> int:
+        return int(self._lib.kpp_state_step(self.handle))
+
+    def save(self, x, stream=None) -> bytes:
+        """The checkpoint of the state and of x (device FP64, cols x k) as bytes."""
+        n = int(self._lib.kpp_state_bytes(self.handle))
+        buf = ctypes.create_string_buffer(n)
+        _check(self._lib.kpp_state_save(self.handle, ctypes.c_void_p(x.data_ptr()), buf, n, _stream_ptr(stream)))
+        return buf.raw
+
+    def load(self, data: bytes, x, stream=None) -> None:
+        """Restore a checkpoint made by save() into this state and into x."""
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(self._lib.kpp_state_load(self.handle, ctypes.c_void_p(x.data_ptr()), buf, len(data),
+                                        _stream_ptr(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self._lib.kpp_state_destroy(self.handle)
+            self.handle = None
+
+
+def solve_resume(A, b, x, P: Partition, F: Factors, prm: Params, state: State, cd: bool = False, stream=None,
+                 allow_no_conv: bool = True) -> list:
+    """kpp_solve_resume / cdpp_solve_resume: prm.max_iters more steps from `state`; one report per column."""
+    reps = (Report * state.k)()
+    m = matrix(A)
+    fn = load().cdpp_solve_resume if cd else load().kpp_solve_resume
+    rc = fn(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), P.handle, F.handle,
+            ctypes.byref(prm), state.handle, reps, _stream_ptr(stream))
+    _check(rc, allow=(ERR_NO_CONVERGENCE,) if allow_no_conv else ())
+    return list(reps)
 
 
 def kpp_solve_batched(As: list, Bs: list, Xs: list, P: Partition, Fs: list, prm: Params, stream=None,
