@@ -472,12 +472,14 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     if (rc == KPP_OK && mode == 0 && A.dtype != KPP_F64 && kw_fits(A.dtype, rows, A.cols, s, 1, sm_count())) {
         // the large-block K++ kernel reads W_S = G^{-1} A_S instead of applying G^{-1} across the group
         KPP_TRY(dev_malloc((void **)&F.W32, (size_t)rows * A.cols * sizeof(float)));
+        F.memo_cols = A.cols;
         rc = build_w32(A, s, F.Ginv32, F.W32, st);
         if (rc != KPP_OK) goto done;
     }
     if (rc == KPP_OK && mode == 1 && A.dtype != KPP_F64 && rows % s == 0 && s <= 64) {
         // CD++ inner FP32 iterations on one right-hand side read W_S = G^{-1} A_S (FP32), as FP64 reads W
         KPP_TRY(dev_malloc((void **)&F.W32, (size_t)rows * A.cols * sizeof(float)));
+        F.memo_cols = A.cols;
         rc = build_w32(A, s, F.Ginv32, F.W32, st);
         if (rc != KPP_OK) goto done;
     }

@@ -25,6 +25,7 @@ struct FactorSet {
     float *Ginv32 = nullptr;  // nb x s x s, FP32 copy (FP32/BF16 storage only)
     double *W = nullptr;      // CD++ FP64 only: rows x cols, block j rows = G_j^{-1} A_{S_j} (row-major, ld cols)
     float *W32 = nullptr;     // K++ with FP32/BF16 storage, large-block kernel only: G_j^{-1} A_{S_j} in FP32
+    int64_t memo_cols = 0;    // columns of W / W32 (the matrix's columns)
     // Device time of the factor phase's stages (kpp_factors_stage_ms): events recorded on the stream
     // before the Grams / principal blocks, then after the Cholesky, the inverses and the W memo.
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

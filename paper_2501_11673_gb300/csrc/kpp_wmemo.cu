@@ -1,11 +1,14 @@
 // kpp_wmemo.cu -- the memoised W_j = G_j^{-1} A_{S_j} (FP32) of the large-block K++ kernel.
 //
-// A plain batched GEMM per block of the partition (s x s times s x n), so it goes to cuBLAS with the
-// FP32 compute type that splits each operand into three BF16 parts on the tensor cores (FP32
-// accuracy).  BF16 storage is widened to FP32 a chunk of blocks at a time.
+// BF16 storage: the library's own tcgen05 kernel (kpp_wmemo_tc.cu).  FP32 storage, and any shape the
+// tcgen05 kernel does not take: a plain batched GEMM per block of the partition (s x s times s x n)
+// on cuBLAS, with the FP32 compute type that splits each operand into three BF16 parts on the tensor
+// cores (FP32 accuracy); BF16 storage is then widened to FP32 a chunk of blocks at a time.
+// KPP_WMEMO_TC=0 in the environment sends every shape to cuBLAS (for comparisons).
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
@@ -35,7 +38,14 @@ __global__ void widen_bf16_kernel(int64_t rows, int64_t cols, const __nv_bfloat1
     }
 }
 
+kpp_status build_w32_tc(const kpp_matrix &A, int s, const float *Ginv32, float *W32, cudaStream_t st);
+
 kpp_status build_w32(const kpp_matrix &A, int s, const float *Ginv32, float *W32, cudaStream_t st) {
+    const char *tc_env = getenv("KPP_WMEMO_TC");
+    if (A.dtype == KPP_BF16 && !(tc_env && tc_env[0] == '0')) {
+        if (build_w32_tc(A, s, Ginv32, W32, st) == KPP_OK) return KPP_OK;
+        // not taken or failed: the library GEMM below rewrites every block
+    }
     const int64_t rows = A.rows, cols = A.cols;
     const int64_t nb = rows / s;  // whole blocks only (checked by the caller)
     cublasHandle_t h = blas_handle();
