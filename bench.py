@@ -260,55 +260,26 @@ def _factors_numpy_gram(A, s, lam):
     return L
 
 
-def cg_torch(A, b, tol, max_iters):
-    """Plain conjugate gradients (Hestenes and Stiefel, 1952) from x0 = 0 with torch ops, FP64: the
-    Krylov reference point beside CD++ on the SPD workload.  Same update order as the oracle's CG, and
-    the stop test |r| <= tol |b| on the recursively updated residual, checked on the host every
-    iteration.  Returns (x, iterations, |b - A x| / |b| recomputed in FP64)."""
+def krylov_reference(kpp, A, b, tol, method, reps=3, restart=512):
+    """The library's FP64 CG (kpp_cg) or GMRES(restart) (kpp_gmres) on the same system and GPU, from
+    x0 = 0, one persistent launch each; the fastest of `reps` runs by the kernel's events, with the
+    paper's flop model for the method (CG 2n^2 + 11n per iteration, GMRES 2n^2 T + 4n T (T + 1))."""
     import torch
-    x = torch.zeros_like(b)
-    r = b.clone()
-    p = r.clone()
-    bn = float(torch.linalg.vector_norm(b))
-    rr = torch.dot(r, r)
-    it = 0
-    while it < max_iters and math.sqrt(float(rr)) > tol * bn:
-        Ap = torch.mv(A, p)
-        alpha = rr / torch.dot(p, Ap)
-        x.add_(alpha * p)
-        r.sub_(alpha * Ap)
-        rr2 = torch.dot(r, r)
-        p.mul_(rr2 / rr).add_(r)
-        rr = rr2
-        it += 1
-    res = float(torch.linalg.vector_norm(b - torch.mv(A, x))) / bn if bn > 0 else float(torch.linalg.vector_norm(x))
-    return x, it, res
-
-
-def cg_reference(A, b, tol, reps=3, max_iters=20000):
-    """Time-to-tolerance of cg_torch on A, b (device tensors: CUDA events on the current stream around
-    each run, after one warm-up run; host tensors: wall clock).  Median over `reps` runs."""
-    import torch
-    cg_torch(A, b, tol, max_iters)
-    ms = []
-    for _ in range(reps):
-        if A.is_cuda:
-            st = torch.cuda.current_stream()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            _, it, res = cg_torch(A, b, tol, max_iters)
-            e1.record(st)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        else:
-            t0 = time.perf_counter()
-            _, it, res = cg_torch(A, b, tol, max_iters)
-            ms.append(1e3 * (time.perf_counter() - t0))
     n = A.shape[0]
-    return {"what": "plain FP64 conjugate gradients from x0 = 0 on the same system and device (torch / cuBLAS "
-                    "matrix-vector products; stop test on the host every iteration)",
-            "iters": it, "time_to_tol_ms": statistics.median(ms), "rel_res_true": res,
-            "flops_paper_model": (2 * n * n + 11 * n) * it, "flops_model": "(2 n^2 + 11 n) per CG iteration"}
+    best = None
+    for _ in range(reps):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        rep = kpp.cg(A, b, x, tol=tol) if method == "cg" else kpp.gmres(A, b, x, restart=restart, tol=tol)
+        if best is None or rep.kernel_ms < best.kernel_ms:
+            best = rep
+    T = best.iters
+    flops = (2 * n * n + 11 * n) * T if method == "cg" else 2 * n * n * T + 4 * n * T * (T + 1)
+    what = ("plain FP64 conjugate gradients (kpp_cg)" if method == "cg"
+            else f"FP64 GMRES({restart}) with classical Gram-Schmidt + reorthogonalisation (kpp_gmres)")
+    return {"what": what + ", same system and GPU, x0 = 0, one persistent launch, fastest of 3",
+            "iters": T, "time_to_tol_ms": best.kernel_ms, "rel_res_true": best.rel_res_true,
+            "flops_paper_model": flops,
+            "flops_model": "(2 n^2 + 11 n) per iteration" if method == "cg" else "2 n^2 T + 4 n T (T + 1)"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -436,10 +407,11 @@ class SingleFP64(Workload):
                               "factor_phase": nb * (s ** 3 / 3 + 2 * s * s * n)}}
         if not getattr(self, "run_cg_reference", True):
             return out
-        try:
-            out["cg_reference"] = cg_reference(self.Ad, self.bd, self.sy.tol)
-        except Exception as exc:  # a failed reference point must not lose the bench line
-            out["cg_reference"] = {"error": f"{type(exc).__name__}: {exc}"}
+        for name in ("cg", "gmres"):
+            try:
+                out[f"{name}_reference"] = krylov_reference(self.kpp, self.Ad, self.bd, self.sy.tol, name)
+            except Exception as exc:  # a failed reference point must not lose the bench line
+                out[f"{name}_reference"] = {"error": f"{type(exc).__name__}: {exc}"}
         return out
 
     def e2e(self):
@@ -774,9 +746,11 @@ class Batched(Workload):
 
     kernel = "stream_kernel"
 
-    def __init__(self, nsys=64, m=2048, n=65536, k=8, s=256, grid=None):
+    def __init__(self, nsys=64, m=2048, n=65536, k=8, s=256, grid=None, tune_s=False):
         self.nsys, self.m, self.n, self.k, self.s = nsys, m, n, k, s
         self.grid = grid  # CTAs per system; None: the launch autotuner
+        self.tune_s = tune_s  # pick s among 128, 256, 512 with the block-size autotuner (before the steps)
+        self.s_tuning = None
         self.tol = 1e-8
         self.dtype = "f32"
         self.desc = (f"{nsys} under-determined min-norm K++ systems, each {m}x{n} FP32 i.i.d. N(0,1) with 20 seeded "
@@ -794,6 +768,15 @@ class Batched(Workload):
         rn = (self.A[0].double() ** 2).sum(dim=1)
         self.lam = 1e-3 * float(torch.median(rn).item())
         self.X = [torch.zeros(self.n, self.k, dtype=torch.float64, device="cuda") for _ in range(self.nsys)]
+        if self.tune_s:
+            prm = kpp.params(lam=self.lam, tol=self.tol, refine=1, inner_tol=1e-3, seed=0, sys_id=rank * 4096)
+            t0 = time.perf_counter()
+            best, est = kpp.tune_block_size(self.A, self.B, [128, 256, 512], prm)
+            self.s_tuning = {"candidates": {str(k): v for k, v in est.items()}, "chosen": best,
+                             "tuning_s": time.perf_counter() - t0,
+                             "note": "estimated ms to tol per candidate (kpp_tune_block_size), before the timed steps"}
+            self.s = best
+            self.desc = self.desc.replace("s=256", f"s={best} (block-size autotuner over 128, 256, 512)")
         self.P = kpp.Partition(self.m, self.s)
         self.prm = kpp.params(lam=self.lam, tol=self.tol, refine=1, inner_tol=1e-3, seed=0, sys_id=rank * 4096,
                               grid=kpp.GRID_TUNE if self.grid is None else self.grid)
@@ -853,7 +836,8 @@ class Batched(Workload):
         return self._roof
 
     def extra(self, steps):
-        return {"plan": self.info, "max_system_iters": steps[-1]["max_iters"], "outer_steps": steps[-1]["outer"],
+        out = {"block_size_tuning": self.s_tuning} if self.s_tuning else {}
+        return {**out, "plan": self.info, "max_system_iters": steps[-1]["max_iters"], "outer_steps": steps[-1]["outer"],
                 "worst_rel_res": steps[-1]["rel_res"],
                 "gpu_launches_note": "host-side launches plus the captured graph's kernels (one replay per step)"}
 
@@ -1010,7 +994,8 @@ def make_workload(args):
     if args.workload == "mixed262144":
         return MixedLS(args.storage, args.noisy, m=args.mixed_rows)
     if args.workload == "batched64":
-        return Batched(nsys=getattr(args, "systems", 64), grid=getattr(args, "batched_grid", None))
+        return Batched(nsys=getattr(args, "systems", 64), grid=getattr(args, "batched_grid", None),
+                       tune_s=getattr(args, "tune_s", False))
     if args.workload == "serving":
         return Serving(n_req=args.requests)
     if args.workload == "cdpp4096-rht":
@@ -1099,6 +1084,8 @@ def main():
                     help="cdpp4096 / kpp2000: let the launch autotuner pick the CTAs per system")
     ap.add_argument("--systems", type=int, default=64, help="batched64: systems (fewer for profiler captures)")
     ap.add_argument("--batched-grid", type=int, default=None, help="batched64: CTAs per system (default: autotuned)")
+    ap.add_argument("--tune-s", action="store_true",
+                    help="batched64: choose the block size among 128, 256, 512 with the block-size autotuner")
     ap.add_argument("--host-qr", action="store_true",
                     help="Haar factors by a host QR (ncu cannot load torch's device linear algebra)")
     ap.add_argument("--ref-iters", type=int, default=4096)

@@ -465,6 +465,25 @@ kpp_status kpp_plan_info(kpp_plan_t plan, int32_t *kernel, int32_t *grid, int32_
 /* Waits for the device to go idle, then frees the plan's scratch.  NULL is ignored. */
 void kpp_plan_destroy(kpp_plan_t plan);
 
+/* ---- Block-size autotuner ------------------------------------------------------------------------
+ * Picks the block size s of the contiguous partition (the s of Alg. 1 / Alg. 5, which the paper fixes
+ * by hand) for nsys systems A_i (same shape and storage) with right-hand-side panels B_i (device FP64,
+ * rows x k), among the ncand candidates cand[] (1 <= cand <= min(1024, rows)).  For each candidate:
+ * the factor phase of every system (its device time), then two segments of T = 6 zeta steps (24 ..
+ * 1024) of the solve kernel with no stop test (the launch shape the heuristic picks; FP32 iterations
+ * for FP32 / BF16 storage, FP64 otherwise): the first from x = 0 as a burn-in, the second continuing
+ * from its x, each followed by every column's FP64 residual.  The contraction per step q is the
+ * geometric mean over the columns of |r_2T| / |r_T|, to the power 1 / T, and the estimate of the time
+ * to a relative residual p->tol is  factor ms + ms per step * (2T + log(tol / rel_2T) / log(q)).
+ * out_s (host): the candidate with the smallest estimate.  est_ms (host, ncand doubles, may be NULL):
+ * every estimate (INFINITY for a candidate that did not run or did not contract).  p: lambda, tol
+ * (0 < tol < 1), seed, sys_id, eta, rho0 and adaptive_rho as for the solve.  cd = 1 tunes CD++ (square
+ * A).  Errors: KPP_ERR_ARG; KPP_ERR_NO_CONVERGENCE when no candidate contracts; KPP_ERR_CUDA, OOM.
+ * Synchronises `stream`; allocates the candidates' factors one at a time. */
+kpp_status kpp_tune_block_size(int32_t nsys, const kpp_matrix *A, const double *const *B, int32_t k,
+                               const int32_t *cand, int32_t ncand, const kpp_params *p, int32_t cd, int32_t *out_s,
+                               double *est_ms, void *stream);
+
 /* ---- Launch autotuner ------------------------------------------------------------------------------
  *
  * p->grid = KPP_GRID_TUNE in kpp_plan_create, kpp_solve, cdpp_solve or the batched solves times short

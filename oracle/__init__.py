@@ -101,6 +101,9 @@ def _load():
             lib.orc_run.restype = ctypes.c_int
             lib.orc_cg.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_double, ctypes.c_int64, dp]
             lib.orc_cg.restype = ctypes.c_int64
+            lib.orc_gmres.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, dp,
+                                      ctypes.POINTER(ctypes.c_int64)]
+            lib.orc_gmres.restype = ctypes.c_int64
             lib.orc_rht_forward.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int64, dp, dp, dp]
             lib.orc_rht_inverse.argtypes = [ctypes.c_int64, dp, ctypes.c_int64, dp, dp]
             lib.orc_rht_entry.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int64, ctypes.c_int64]
@@ -282,6 +285,18 @@ def cg(A: np.ndarray, b: np.ndarray, tol: float = 1e-8, max_iters: int = 100000,
     rr = ctypes.c_double()
     it = _load().orc_cg(A.shape[0], _dp(A), _dp(_f64(b)), _dp(x), tol, max_iters, ctypes.byref(rr))
     return x, int(it), rr.value
+
+
+def gmres(A: np.ndarray, b: np.ndarray, restart: int = 256, tol: float = 1e-8, max_iters: int = 100000, x0=None):
+    """Restarted FP64 GMRES (context only; textbook Arnoldi with modified Gram-Schmidt and Givens
+    rotations).  Returns (x, steps, |Ax-b|/|b|, cycles)."""
+    A = _f64(A)
+    x = np.zeros(A.shape[0]) if x0 is None else _f64(x0).copy()
+    rr = ctypes.c_double()
+    cyc = ctypes.c_int64()
+    it = _load().orc_gmres(A.shape[0], _dp(A), _dp(_f64(b)), _dp(x), int(restart), tol, max_iters, ctypes.byref(rr),
+                           ctypes.byref(cyc))
+    return x, int(it), rr.value, int(cyc.value)
 
 
 # ----------------------------------------------------------------------------------------------

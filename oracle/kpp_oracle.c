@@ -15,7 +15,7 @@
  *   - CD++ coordinate step                    w = I_S^T (A_SS + lam I)^{-1} (A_S x - b_S)           (Eq. 5.1, Thm 5.1)
  *   - residual estimate, adaptive rho, stop   E0/E1 windows of zeta steps, weighted ratio           (Eq. 5.2, Eq. 5.3, Alg. 3 / Alg. 5)
  *   - memoised per-block Cholesky factors     one factor per block of a fixed partition             (Sec. 4, Sec. 5.2)
- *   - plain conjugate gradients (context only; Sec. 6 compares against CG)
+ *   - plain conjugate gradients and restarted GMRES (context only; Sec. 6 compares against both)
  *   - Philox4x32-10 block sampling (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
  *     1, 2, 3", SC'11): a counter-based generator, implemented here from its published definition.
  *
@@ -334,6 +334,83 @@ int64_t orc_cg(int64_t n, const double *A, const double *b, double *x, double to
     free(r);
     free(pv);
     free(Ap);
+    return it;
+}
+
+/* Restarted GMRES(restart) (Saad and Schultz), the other Krylov method Sec. 6 compares with:
+ * the textbook algorithm written out.  A cycle starts from r0 = b - A x, v_1 = r0 / beta, g = beta e_1;
+ * step j forms w = A v_j, orthogonalises it against v_1 .. v_j one vector at a time (modified
+ * Gram-Schmidt), h_{j+1,j} = |w|, v_{j+1} = w / h_{j+1,j}; the earlier Givens rotations are applied to
+ * column j of H and a new one zeroes h_{j+1,j}, updating g; the cycle ends when |g_{j+1}| <= tol |b|,
+ * after `restart` steps or at max_iters steps in all, with x += V y, R y = g.  Returns the steps taken;
+ * *cycles_out the cycles, *rel_res_out the true |A x - b| / |b|. */
+int64_t orc_gmres(int64_t n, const double *A, const double *b, double *x, int64_t restart, double tol,
+                  int64_t max_iters, double *rel_res_out, int64_t *cycles_out) {
+    const int64_t m = restart;
+    double *V = (double *)malloc(sizeof(double) * (size_t)(m + 1) * (size_t)n);
+    double *H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double)); /* H[i * m + j] = h_{i,j} */
+    double *cs = (double *)malloc(sizeof(double) * (size_t)m);
+    double *sn = (double *)malloc(sizeof(double) * (size_t)m);
+    double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    double *y = (double *)malloc(sizeof(double) * (size_t)m);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    const double bn = sqrt(dot(n, b, b));
+    int64_t it = 0, cycles = 0;
+    for (;;) {
+        for (int64_t i = 0; i < n; ++i) w[i] = b[i] - dot(n, A + (size_t)i * n, x);
+        const double beta = sqrt(dot(n, w, w));
+        if (!(beta > tol * bn) || it >= max_iters) break;
+        for (int64_t i = 0; i < n; ++i) V[i] = w[i] / beta;
+        for (int64_t i = 0; i <= m; ++i) g[i] = 0.0;
+        g[0] = beta;
+        int64_t k = 0;
+        for (int64_t j = 0; j < m; ++j) {
+            const double *vj = V + (size_t)j * (size_t)n;
+            for (int64_t i = 0; i < n; ++i) w[i] = dot(n, A + (size_t)i * n, vj);
+            for (int64_t l = 0; l <= j; ++l) {
+                const double *vl = V + (size_t)l * (size_t)n;
+                const double h = dot(n, vl, w);
+                H[l * m + j] = h;
+                for (int64_t i = 0; i < n; ++i) w[i] -= h * vl[i];
+            }
+            const double hn = sqrt(dot(n, w, w));
+            H[(j + 1) * m + j] = hn;
+            if (hn > 0.0)
+                for (int64_t i = 0; i < n; ++i) V[(size_t)(j + 1) * (size_t)n + i] = w[i] / hn;
+            for (int64_t l = 0; l < j; ++l) {
+                const double t = cs[l] * H[l * m + j] + sn[l] * H[(l + 1) * m + j];
+                H[(l + 1) * m + j] = -sn[l] * H[l * m + j] + cs[l] * H[(l + 1) * m + j];
+                H[l * m + j] = t;
+            }
+            const double d = sqrt(H[j * m + j] * H[j * m + j] + hn * hn);
+            cs[j] = d > 0.0 ? H[j * m + j] / d : 1.0;
+            sn[j] = d > 0.0 ? hn / d : 0.0;
+            H[j * m + j] = d;
+            H[(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++it;
+            k = j + 1;
+            if (fabs(g[j + 1]) <= tol * bn || hn == 0.0 || it >= max_iters) break;
+        }
+        for (int64_t i = k - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int64_t l = i + 1; l < k; ++l) t -= H[i * m + l] * y[l];
+            y[i] = t / H[i * m + i];
+        }
+        for (int64_t l = 0; l < k; ++l)
+            for (int64_t i = 0; i < n; ++i) x[i] += y[l] * V[(size_t)l * (size_t)n + i];
+        ++cycles;
+    }
+    *rel_res_out = orc_rel_residual(n, n, A, b, x);
+    *cycles_out = cycles;
+    free(V);
+    free(H);
+    free(cs);
+    free(sn);
+    free(g);
+    free(y);
+    free(w);
     return it;
 }
 

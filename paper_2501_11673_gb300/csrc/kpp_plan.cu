@@ -592,3 +592,170 @@ kpp_status kpp_tune_cache_load(const char *path) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Block-size autotuner
+// ---------------------------------------------------------------------------------------------
+// For each candidate block size (contiguous partition): the factor phase of every system (event
+// time), then two segments of T steps of the persistent kernel with no stop test (the launch shape
+// the heuristic picks for that s), each followed by the residual of every column.  The contraction per
+// step over the second segment, q = (prod_c |r_2T| / |r_T|)^(1 / (T * columns)), gives the steps
+// still needed to a relative residual tol, and the estimate factor_ms + ms_per_step * steps.  FP32 /
+// BF16 storage runs the inner FP32 iteration (the refinement's cost per step), FP64 storage the FP64
+// one.
+extern "C" kpp_status kpp_tune_block_size(int32_t nsys, const kpp_matrix *A, const double *const *B, int32_t k,
+                                          const int32_t *cand, int32_t ncand, const kpp_params *pp, int32_t cd,
+                                          int32_t *out_s, double *est_ms, void *stream) {
+    clear_error();
+    if (nsys < 1 || !A || !B || k < 1 || k > 32 || !cand || ncand < 1 || !pp || !out_s || !(pp->tol > 0.0) ||
+        pp->tol >= 1.0) {
+        set_error("kpp_tune_block_size: invalid argument (needs 0 < tol < 1, 1 <= k <= 32, candidates)");
+        return KPP_ERR_ARG;
+    }
+    for (int i = 0; i < nsys; ++i)
+        if (!matrix_ok(&A[i]) || !B[i] || A[i].rows != A[0].rows || A[i].cols != A[0].cols ||
+            A[i].dtype != A[0].dtype || (cd && A[i].rows != A[i].cols)) {
+            set_error("kpp_tune_block_size: system %d does not match system 0 (or CD++ needs square)", i);
+            return KPP_ERR_ARG;
+        }
+    for (int c = 0; c < ncand; ++c)
+        if (cand[c] < 1 || cand[c] > 1024 || cand[c] > A[0].rows) {
+            set_error("kpp_tune_block_size: candidate %d out of range", cand[c]);
+            return KPP_ERR_ARG;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    const kpp_params p = *pp;
+    const int dtype = A[0].dtype;
+    const size_t tcs = dtype == KPP_F64 ? 8 : 4;
+    const int64_t rows = A[0].rows, cols = A[0].cols;
+    kpp_status rc = KPP_OK;
+    double best = INFINITY;
+    int best_s = -1;
+    Scratch scr(st);
+    std::vector<void *> xb(nsys), bb(nsys);
+    std::vector<double> b2(nsys * k, 0.0);
+    for (int i = 0; i < nsys; ++i) {
+        CUDA_OR(scr.alloc(&xb[i], (size_t)cols * k * tcs), KPP_ERR_CUDA);
+        if (dtype == KPP_F64) {
+            bb[i] = (void *)B[i];
+        } else {
+            CUDA_OR(scr.alloc(&bb[i], (size_t)rows * k * tcs), KPP_ERR_CUDA);
+            CUDA_OR(launch_f64_to_f32((int64_t)rows * k, B[i], (float *)bb[i], st), KPP_ERR_CUDA);
+        }
+        std::vector<double> r2, bn2;
+        kpp_status r3 = residual_norms(A[i], k, B[i], nullptr, nullptr, r2, &bn2, st);
+        if (r3 != KPP_OK) return r3;
+        for (int c = 0; c < k; ++c) b2[(size_t)i * k + c] = bn2[c];
+    }
+    for (int ci = 0; ci < ncand; ++ci) {
+        const int s = cand[ci];
+        if (est_ms) est_ms[ci] = INFINITY;
+        kpp_partition_s P{rows, s, (rows + s - 1) / s};
+        std::vector<kpp_factors_t> F(nsys, nullptr);
+        double fac_ms = 0.0;
+        bool ok = true;
+        for (int i = 0; i < nsys && ok; ++i) {
+            kpp_status fr = kpp_factor_blocks(&A[i], &P, p.lambda, cd ? 1 : 0, &F[i], stream);
+            if (fr != KPP_OK) {
+                ok = false;
+                break;
+            }
+            double sm[4];
+            kpp_factors_stage_ms(F[i], sm);
+            for (double v : sm)
+                if (std::isfinite(v)) fac_ms += v;
+        }
+        if (ok) {
+            // two segments of T steps (six sweeps over the blocks, 24 .. 1024): the first from x = 0 as a
+            // burn-in (a Kaczmarz iteration shrinks the error, not always the residual, at first), the
+            // second continuing from its x (momentum restarted, the Philox counter continuing); the
+            // contraction is measured over the second
+            const int64_t nb = P.nb;
+            const int64_t T = std::max<int64_t>(24, std::min<int64_t>(6 * nb, 1024));
+            std::vector<std::vector<SolveScalars>> sc(nsys);
+            std::vector<SysInput> in(nsys);
+            std::vector<int> errs(nsys, 0);
+            std::vector<std::vector<double>> rr(2, std::vector<double>((size_t)nsys * k, 0.0));
+            double seg_ms = 0.0;
+            for (int i = 0; i < nsys; ++i)
+                if (cudaMemsetAsync(xb[i], 0, (size_t)cols * k * tcs, st) != cudaSuccess) ok = false;
+            for (int seg = 0; seg < 2 && ok; ++seg) {
+                for (int i = 0; i < nsys; ++i) {
+                    init_scalars(sc[i], k, p.rho0);
+                    in[i] = SysInput{&A[i], bb[i], xb[i], &F[i]->f, p.sys_id + (uint32_t)i, sc[i].data()};
+                }
+                float ms = 0.f;
+                kpp_status r = run_persistent(in, dtype, cd, k, s, default_eta(p, s, rows, cols), 0.0, p.adaptive_rho,
+                                              0, seg * T + T, p.seed, 0, true, seg * T, st, &ms, errs.data(), -1);
+                if (r == KPP_ERR_UNSUPPORTED || r == KPP_ERR_NUMERIC) {
+                    ok = false;
+                    break;
+                }
+                if (r != KPP_OK && r != KPP_ERR_NO_CONVERGENCE) {
+                    rc = r;
+                    ok = false;
+                    break;
+                }
+                if (seg == 1) seg_ms = ms;
+                for (int i = 0; i < nsys && ok; ++i) {
+                    std::vector<double> r2;
+                    kpp_status r3;
+                    if (dtype == KPP_F64) {
+                        r3 = residual_norms(A[i], k, B[i], (const double *)xb[i], nullptr, r2, nullptr, st);
+                    } else {
+                        double *x64 = nullptr;
+                        r3 = scr.alloc((void **)&x64, (size_t)cols * k * 8) == cudaSuccess ? KPP_OK : KPP_ERR_OOM;
+                        if (r3 == KPP_OK && (cudaMemsetAsync(x64, 0, (size_t)cols * k * 8, st) != cudaSuccess ||
+                                             launch_axpy((int64_t)cols * k, (const float *)xb[i], x64, st) != cudaSuccess))
+                            r3 = KPP_ERR_CUDA;
+                        if (r3 == KPP_OK) r3 = residual_norms(A[i], k, B[i], x64, nullptr, r2, nullptr, st);
+                    }
+                    if (r3 != KPP_OK) {
+                        ok = false;
+                        break;
+                    }
+                    for (int c = 0; c < k; ++c) rr[seg][(size_t)i * k + c] = r2[c];
+                }
+            }
+            if (ok) {
+                // log of the contraction per step over the second segment (geometric mean over columns),
+                // and the steps still needed after it to reach tol
+                double lq = 0.0, lrel = 0.0;
+                int cnt = 0;
+                for (size_t c = 0; c < rr[0].size(); ++c) {
+                    const double b0 = b2[c];
+                    if (b0 > 0.0 && rr[0][c] > 0.0 && rr[1][c] > 0.0) {
+                        lq += 0.5 * std::log(rr[1][c] / rr[0][c]);
+                        lrel += 0.5 * std::log(rr[1][c] / b0);
+                        ++cnt;
+                    }
+                }
+                if (cnt > 0) {
+                    lq /= (double)cnt * (double)T;
+                    lrel /= (double)cnt;
+                    if (lq < 0.0 && std::isfinite(lq)) {
+                        const double more = std::max(0.0, (std::log(p.tol) - lrel) / lq);
+                        const double est = fac_ms + seg_ms / (double)T * (2.0 * (double)T + more);
+                        if (est_ms) est_ms[ci] = est;
+                        if (est < best) {
+                            best = est;
+                            best_s = s;
+                        }
+                    }
+                }
+            }
+        }
+        for (kpp_factors_t f : F)
+            if (f) kpp_factors_destroy(f);
+        clear_error();
+        if (rc != KPP_OK) return rc;
+    }
+    if (best_s < 0) {
+        set_error("kpp_tune_block_size: no candidate reduced the residual");
+        return KPP_ERR_NO_CONVERGENCE;
+    }
+    *out_s = best_s;
+    return KPP_OK;
+cleanup:
+    return rc;
+}

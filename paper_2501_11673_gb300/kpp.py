@@ -37,7 +37,7 @@ EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_par
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
            "kpp_tune_cache_load", "kpp_launch_count", "kpp_device_alloc_count", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
            "kpp_memo_sequence", "kpp_state_create", "kpp_state_destroy", "kpp_state_step",
-           "kpp_state_bytes", "kpp_state_save", "kpp_state_load", "kpp_solve_resume", "cdpp_solve_resume", "kpp_cg", "kpp_gmres"]
+           "kpp_state_bytes", "kpp_state_save", "kpp_state_load", "kpp_solve_resume", "cdpp_solve_resume", "kpp_cg", "kpp_gmres", "kpp_tune_block_size"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
 
@@ -160,6 +160,10 @@ def load(path: str | None = None):
         lib.kpp_state_save.restype = ctypes.c_int
         lib.kpp_state_load.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
         lib.kpp_state_load.restype = ctypes.c_int
+        lib.kpp_tune_block_size.argtypes = [i32, ctypes.POINTER(Matrix), ctypes.POINTER(vp), i32,
+                                             ctypes.POINTER(i32), i32, ctypes.POINTER(Params), i32,
+                                             ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
+        lib.kpp_tune_block_size.restype = ctypes.c_int
         lib.kpp_cg.argtypes = [ctypes.POINTER(Matrix), vp, vp, dbl, i64, ctypes.POINTER(Report), vp]
         lib.kpp_cg.restype = ctypes.c_int
         lib.kpp_gmres.argtypes = [ctypes.POINTER(Matrix), vp, vp, i32, dbl, i64, ctypes.POINTER(Report), vp]
@@ -357,6 +361,20 @@ def cdpp_solve_noalloc(A, b, x, P: Partition, F: Factors, prm: Params, stream=No
     rc = load().cdpp_solve_noalloc(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                    P.handle, F.handle, ctypes.byref(prm), ctypes.byref(rep), _stream_ptr(stream))
     return _report_or_raise(rc, rep, allow_no_conv)
+
+
+def tune_block_size(As: list, Bs: list, candidates: list, prm: Params, cd: bool = False, stream=None):
+    """kpp_tune_block_size: (best s, {s: estimated ms to prm.tol}) over the candidate block sizes."""
+    n = len(As)
+    k = Bs[0].shape[1] if Bs[0].dim() == 2 else 1
+    mats = (Matrix * n)(*[matrix(a) for a in As])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in Bs])
+    cand = (ctypes.c_int32 * len(candidates))(*candidates)
+    est = (ctypes.c_double * len(candidates))()
+    out = ctypes.c_int32()
+    _check(load().kpp_tune_block_size(n, mats, bp, k, cand, len(candidates), ctypes.byref(prm), int(cd),
+                                      ctypes.byref(out), est, _stream_ptr(stream)))
+    return out.value, dict(zip(candidates, list(est)))
 
 
 def cg(A, b, x, tol: float = 1e-8, max_iters: int = 100000, stream=None, allow_no_conv: bool = False) -> Report:

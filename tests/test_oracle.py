@@ -466,6 +466,53 @@ def test_cg_matches_direct_solve():
     np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-8)
 
 
+def _krylov_minres_iterate(A, b, x0, k):
+    """The definition of the k-th GMRES iterate: x0 + Q y with Q an orthonormal basis of
+    K_k(A, r0) = span(r0, A r0, ..., A^(k-1) r0) (QR of the power basis) and y the least-squares
+    minimiser of |b - A (x0 + Q y)|."""
+    r0 = b - A @ x0
+    Kb = np.empty((A.shape[0], k))
+    v = r0 / np.linalg.norm(r0)
+    for j in range(k):
+        Kb[:, j] = v
+        v = A @ v
+        v = v / np.linalg.norm(v)
+    Q, _ = np.linalg.qr(Kb)
+    y = np.linalg.lstsq(A @ Q, r0, rcond=None)[0]
+    return x0 + Q @ y
+
+
+def test_gmres_iterates_are_the_krylov_minimal_residual_ones():
+    rng = np.random.default_rng(52)
+    n = 40
+    A = np.eye(n) * 3.0 + rng.standard_normal((n, n)) * (0.6 / np.sqrt(n))  # nonsymmetric, well conditioned
+    b = rng.standard_normal(n)
+    x0 = rng.standard_normal(n) * 0.1
+    for k in (1, 2, 4, 7):
+        x, it, _, cyc = oracle.gmres(A, b, restart=50, tol=0.0, max_iters=k, x0=x0)
+        assert it == k and cyc == 1
+        xd = _krylov_minres_iterate(A, b, x0, k)
+        assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd), k
+    # the residual never grows with the steps of one cycle, and n steps solve the system
+    res = [np.linalg.norm(b - A @ oracle.gmres(A, b, restart=n, tol=0.0, max_iters=k, x0=x0)[0]) for k in range(1, 12)]
+    assert all(r2 <= r1 * (1 + 1e-12) for r1, r2 in zip(res, res[1:]))
+    x, it, rr, _ = oracle.gmres(A, b, restart=n, tol=0.0, max_iters=n, x0=x0)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-12)
+
+
+def test_gmres_restarted_reaches_the_direct_solution():
+    rng = np.random.default_rng(53)
+    n = 80
+    A = np.eye(n) * 2.0 + rng.standard_normal((n, n)) * (0.5 / np.sqrt(n))
+    b = rng.standard_normal(n)
+    x, it, rr, cyc = oracle.gmres(A, b, restart=6, tol=1e-11)
+    assert rr <= 1e-11 * 1.001 and cyc > 1
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-8, atol=1e-12)
+    # a cycle that ends on the tolerance: the last cycle's estimate and the true residual agree
+    x2, it2, rr2, _ = oracle.gmres(A, b, restart=200, tol=1e-8)
+    assert rr2 <= 1e-8 * 1.001 and it2 < it
+
+
 def test_storage_rounding_is_exact_widening():
     rng = np.random.default_rng(61)
     A = rng.standard_normal((5, 7))
