@@ -504,10 +504,23 @@ kpp_status kpp_tune_cache_load(const char *path);
  * once; a captured graph's replays are not counted).  Host only, never fails. */
 uint64_t kpp_launch_count(void);
 
-/* Number of device allocations (cudaMalloc / cudaMallocAsync calls) this library has made in the
- * process so far: factor sets, solve scratch, plans, the server's panels and the host-buffer solve.
- * Allocations that cuBLAS makes on its own are not counted.  Host only, never fails. */
+/* Number of device allocation requests this library has made in the process so far: factor sets,
+ * solve scratch, plans, the server's panels and the host-buffer solve.  A request served from the
+ * library's caches (kpp_device_cache_bytes) counts as well.  Allocations that cuBLAS makes on its own
+ * are not counted.  Host only, never fails. */
 uint64_t kpp_device_alloc_count(void);
+
+/* Device memory the library holds for reuse on the current device, in bytes (runtime memory
+ * management; no counterpart in the paper).  Released long-lived buffers (factor sets, states, device
+ * copies of host inputs) stay on a free list, up to a quarter of the device's memory, and are handed
+ * out again for a request of the same size: repeated solves of one shape map their memory once.
+ * Stream-ordered scratch comes from a pool that keeps freed memory across synchronisations.  Never
+ * fails (0 without a device). */
+size_t kpp_device_cache_bytes(void);
+
+/* Return the memory of both caches on the current device to the driver.  Synchronises the device
+ * first.  Errors: KPP_ERR_CUDA if the synchronisation or the pool trim fails. */
+kpp_status kpp_device_cache_trim(void);
 
 /* Library build information: "sm_103a; <compiler>; <date>". */
 const char *kpp_build_info(void);

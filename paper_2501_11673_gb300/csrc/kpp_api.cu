@@ -34,15 +34,6 @@ void clear_error() { g_last_error.clear(); }
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-static std::atomic<unsigned long long> g_allocs{0};
-cudaError_t dev_malloc(void **p, size_t bytes) {
-    g_allocs.fetch_add(1, std::memory_order_relaxed);
-    return cudaMalloc(p, bytes);
-}
-cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
-    g_allocs.fetch_add(1, std::memory_order_relaxed);
-    return cudaMallocAsync(p, bytes, st);
-}
 
 // SM count of the current device, cached per device (atomic: the server's threads may ask first together).
 int sm_count() {
@@ -60,12 +51,12 @@ int sm_count() {
 }
 
 void FactorSet::release() {
-    if (L) cudaFree(L);
-    if (Ginv) cudaFree(Ginv);
-    if (Ginv32) cudaFree(Ginv32);
-    if (W32) cudaFree(W32);
+    dev_free(L);
+    dev_free(Ginv);
+    dev_free(Ginv32);
+    dev_free(W32);
     W32 = nullptr;
-    if (W) cudaFree(W);
+    dev_free(W);
     W = nullptr;
     L = nullptr;
     Ginv = nullptr;
@@ -724,7 +715,7 @@ const char *kpp_last_error(void) { return g_last_error.c_str(); }
 #define KPP_STR2(x) #x
 #define KPP_STR(x) KPP_STR2(x)
 uint64_t kpp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
-uint64_t kpp_device_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }
+uint64_t kpp_device_alloc_count(void) { return dev_alloc_requests(); }
 
 const char *kpp_build_info(void) {
     return "sm_103a; nvcc " KPP_STR(__CUDACC_VER_MAJOR__) "." KPP_STR(__CUDACC_VER_MINOR__) "; " __DATE__;
@@ -968,9 +959,9 @@ kpp_status kpp_solve_host(const kpp_matrix *A_host, const double *b_host, double
 cleanup:
     if (F) kpp_factors_destroy(F);
     if (P) kpp_partition_destroy(P);
-    if (dA) cudaFree(dA);
-    if (db) cudaFree(db);
-    if (dx) cudaFree(dx);
+    dev_free(dA);
+    dev_free(db);
+    dev_free(dx);
     return rc;
 }
 

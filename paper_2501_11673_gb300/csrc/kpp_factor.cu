@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(CHOL_NT) cholesky_kernel(int64_t rows, int s, 
     double *Lj = L + (size_t)j * s * s;
     extern __shared__ double panelT[];  // CHOL_PB x s: panelT[c][i - jb]
     __shared__ int s_fail;
+    __shared__ double s_rinv;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = CHOL_NT / 32;
     if (threadIdx.x == 0) s_fail = 0;
     __syncthreads();
@@ -113,13 +114,18 @@ __global__ void __launch_bounds__(CHOL_NT) cholesky_kernel(int64_t rows, int s, 
         for (int c = jb; c < jb + pw; ++c) {
             if (threadIdx.x == 0) {
                 const double d = Gj[(size_t)c * len + c];
-                if (!(d > 0.0) || !isfinite(d)) s_fail = 1;
-                else Gj[(size_t)c * len + c] = sqrt(d);
+                if (!(d > 0.0) || !isfinite(d)) {
+                    s_fail = 1;
+                } else {
+                    const double l = sqrt(d);
+                    Gj[(size_t)c * len + c] = l;
+                    s_rinv = 1.0 / l;  // one division per column; the column is scaled by the reciprocal
+                }
             }
             __syncthreads();
             if (s_fail) break;
-            const double ljj = Gj[(size_t)c * len + c];
-            for (int i = c + 1 + threadIdx.x; i < len; i += CHOL_NT) Gj[(size_t)i * len + c] /= ljj;
+            const double rinv = s_rinv;
+            for (int i = c + 1 + threadIdx.x; i < len; i += CHOL_NT) Gj[(size_t)i * len + c] *= rinv;
             __syncthreads();
             // update the rest of the panel: G[i][c2] -= L[i][c] L[c2][c], c < c2 < jb + pw, i >= c2
             for (int c2 = c + 1; c2 < jb + pw; ++c2) {
@@ -493,9 +499,9 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     KPP_TRY(cudaEventRecord(F.ev[4], st));
 done:
 #undef KPP_TRY
-    if (G) cudaFree(G);
-    if (Linv) cudaFree(Linv);
-    if (bad) cudaFree(bad);
+    dev_free(G);
+    dev_free(Linv);
+    dev_free(bad);
     return rc;
 }
 

@@ -61,9 +61,14 @@ int sm_count();
 // Kernel launches issued by the library (every launch site calls note_launch; kpp_launch_count).
 void note_launch();
 
-// Device allocations made by the library: every cudaMalloc / cudaMallocAsync of libkpp goes through
-// these two, which count the calls (kpp_device_alloc_count).
+// Device allocations made by the library (kpp_memory.cu): every device allocation of libkpp goes
+// through these, which count the requests (kpp_device_alloc_count).  dev_malloc / dev_free serve
+// long-lived buffers from a cache of released ones of the same size (dev_free synchronises the device,
+// as cudaFree does); dev_malloc_async serves stream-ordered scratch from the library's pool, released
+// with cudaFreeAsync.
 cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
 cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+unsigned long long dev_alloc_requests();
 
 }  // namespace kpp

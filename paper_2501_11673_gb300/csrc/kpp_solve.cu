@@ -354,7 +354,8 @@ finish:
 // Standalone FP64 residual r = b - A x (rows x k) with per-CTA partial sums of |r|^2 (fixed grid and
 // fixed order: deterministic).  Optionally stores r rounded to FP32 (the inner right-hand side of a
 // refinement step).  Warp per row; each lane reads 16-byte vectors of the row (8 bf16 / 4 fp32 /
-// 2 fp64 entries), several in flight; x comes from shared memory when it fits (k = 1, cols <= 24576).
+// 2 fp64 entries), several in flight; x comes from shared memory when it fits (k = 1, cols <= 24576),
+// and when that x is exactly zero the row products are skipped (r = b; A is not read).
 // Stored entries are widened exactly and every product and sum is FP64.
 // ---------------------------------------------------------------------------------------------
 template <typename TA> struct Vec16;
@@ -378,8 +379,14 @@ __global__ void __launch_bounds__(256) residual_kernel(const TA *__restrict__ A,
     const bool vec_ok = ((lda * (int64_t)sizeof(TA)) % 16 == 0) && (((uintptr_t)A & 15) == 0);
     const bool x_in_smem = (k == 1) && x && cols <= RES_SMEM_COLS;
     if (x_in_smem) {
-        for (int64_t i = threadIdx.x; i < cols; i += blockDim.x) xs[i] = x[i];
-        __syncthreads();
+        int nz = 0;
+        for (int64_t i = threadIdx.x; i < cols; i += blockDim.x) {
+            const double v = x[i];
+            xs[i] = v;
+            nz |= v != 0.0;
+        }
+        // x = 0 (the first refinement step from x0 = 0): r = b, and A is not read
+        if (!__syncthreads_or(nz)) x = nullptr;
     }
     double acc2[32];
 #pragma unroll

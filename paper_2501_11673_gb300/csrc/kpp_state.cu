@@ -46,10 +46,10 @@ static size_t state_bytes(const kpp_state_s &s) {
 }
 
 static void state_free(kpp_state_s *s) {
-    if (s->m) cudaFree(s->m);
-    if (s->Rx) cudaFree(s->Rx);
-    if (s->Rm) cudaFree(s->Rm);
-    if (s->sc) cudaFree(s->sc);
+    dev_free(s->m);
+    dev_free(s->Rx);
+    dev_free(s->Rm);
+    dev_free(s->sc);
     delete s;
 }
 

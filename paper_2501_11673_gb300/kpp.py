@@ -35,7 +35,7 @@ EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_par
            "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_reset_stats", "kpp_server_destroy",
            "cdpp_solve_batched", "kpp_plan_create", "kpp_plan_launch", "kpp_plan_report", "kpp_plan_info",
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
-           "kpp_tune_cache_load", "kpp_launch_count", "kpp_device_alloc_count", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
+           "kpp_tune_cache_load", "kpp_launch_count", "kpp_device_alloc_count", "kpp_device_cache_bytes", "kpp_device_cache_trim", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
            "kpp_memo_sequence", "kpp_state_create", "kpp_state_destroy", "kpp_state_step",
            "kpp_state_bytes", "kpp_state_save", "kpp_state_load", "kpp_solve_resume", "cdpp_solve_resume", "kpp_cg", "kpp_gmres", "kpp_tune_block_size"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
@@ -185,6 +185,10 @@ def load(path: str | None = None):
         lib.kpp_tune_cache_size.restype = i64
         lib.kpp_launch_count.restype = ctypes.c_uint64
         lib.kpp_device_alloc_count.restype = ctypes.c_uint64
+        lib.kpp_device_cache_bytes.argtypes = []
+        lib.kpp_device_cache_bytes.restype = ctypes.c_size_t
+        lib.kpp_device_cache_trim.argtypes = []
+        lib.kpp_device_cache_trim.restype = ctypes.c_int
         lib.kpp_tune_cache_clear.restype = None
         lib.kpp_tune_cache_save.argtypes = [ctypes.c_char_p]
         lib.kpp_tune_cache_load.argtypes = [ctypes.c_char_p]
@@ -507,8 +511,18 @@ def launch_count() -> int:
 
 
 def device_alloc_count() -> int:
-    """Device allocations (cudaMalloc / cudaMallocAsync) the library has made in this process."""
+    """Device allocation requests the library has made in this process (cached ones included)."""
     return int(load().kpp_device_alloc_count())
+
+
+def device_cache_bytes() -> int:
+    """kpp_device_cache_bytes: device memory the library holds for reuse on the current device."""
+    return int(load().kpp_device_cache_bytes())
+
+
+def device_cache_trim() -> None:
+    """kpp_device_cache_trim: return the library's cached device memory to the driver."""
+    _check(load().kpp_device_cache_trim())
 
 
 def tune_cache_size() -> int:
