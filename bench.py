@@ -649,6 +649,9 @@ class MixedLS(Workload):
                 "frac": ach / pk, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(f"cholesky_kernel/{self.name}"),
                 "launch_ms": chol_ms, "per_launch": {"flops": flops, "blocks": nb, "s": self.s,
                                                      "count": "s^3/3 per block (the paper's Cholesky count)"},
+                "launches": "cholesky_kernel over the whole rounds of blocks (one CTA per block, 3 per SM), then "
+                            "cholesky_pair_kernel over the last round (nb mod SMs blocks, a 2-CTA cluster each); "
+                            "the time is the stage's events around both",
                 "peak_source": FP64_PEAK_SOURCE, "nominal_peak": {**nom, "frac": ach / nom["peak"]},
                 "factor_stages_ms": st}
 

@@ -97,8 +97,8 @@ constexpr int CHOL_PB = 8;
 constexpr int CHOL_NT = 512;
 
 __global__ void __launch_bounds__(CHOL_NT) cholesky_kernel(int64_t rows, int s, double *__restrict__ G,
-                                                          double *__restrict__ L, int *__restrict__ bad) {
-    const int j = blockIdx.x;
+                                                          double *__restrict__ L, int *__restrict__ bad, int j0) {
+    const int j = j0 + (int)blockIdx.x;  // blocks j0 .. j0 + gridDim.x - 1
     const int len = (int)min64(s, rows - (int64_t)j * s);
     double *Gj = G + (size_t)j * s * s;
     double *Lj = L + (size_t)j * s * s;
@@ -169,6 +169,118 @@ __global__ void __launch_bounds__(CHOL_NT) cholesky_kernel(int64_t rows, int s, 
     }
 }
 
+// The same factorisation with each block split over a cluster of two CTAs on two SMs, for the last
+// round of blocks, which would otherwise leave most SMs idle.  Per panel: rank 0 factors the panel
+// columns (as above); a cluster barrier makes them visible; both CTAs copy the panel rows into their
+// own shared memory and update half of the trailing rows each (warp w of rank r takes rows
+// t0 + 16 r + w, then every 32nd); a second cluster barrier precedes the next panel.  A failed pivot is
+// seen by both CTAs after the first barrier (rank 1 reads rank 0's flag through distributed shared
+// memory), so both leave the panel loop at the same point, and they leave the kernel through one more
+// cluster barrier, so that rank 0's shared memory outlives rank 1's last read of it.  Hardware cluster
+// barriers have no time limit; both CTAs always reach the same ones.
+__device__ __forceinline__ void chol_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CHOL_NT)
+    cholesky_pair_kernel(int64_t rows, int s, double *__restrict__ G, double *__restrict__ L, int *__restrict__ bad,
+                         int j0) {
+    unsigned rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const int j = j0 + (int)(blockIdx.x >> 1);
+    const int len = (int)min64(s, rows - (int64_t)j * s);
+    double *Gj = G + (size_t)j * s * s;
+    double *Lj = L + (size_t)j * s * s;
+    extern __shared__ double panelT[];  // CHOL_PB x s: panelT[c][i - jb]
+    __shared__ int s_fail;
+    __shared__ double s_rinv;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = CHOL_NT / 32;
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+    uint32_t fail0;  // rank 0's s_fail in the cluster's shared window
+    asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(fail0) : "r"((uint32_t)__cvta_generic_to_shared(&s_fail)));
+    chol_cluster_sync();  // both CTAs are running before either reads the other's shared memory
+    bool failed = false;
+    for (int jb = 0; jb < len; jb += CHOL_PB) {
+        const int pw = min(CHOL_PB, len - jb);
+        if (rank == 0) {
+            for (int c = jb; c < jb + pw; ++c) {
+                if (threadIdx.x == 0) {
+                    const double d = Gj[(size_t)c * len + c];
+                    if (!(d > 0.0) || !isfinite(d)) {
+                        s_fail = 1;
+                    } else {
+                        const double l = sqrt(d);
+                        Gj[(size_t)c * len + c] = l;
+                        s_rinv = 1.0 / l;
+                    }
+                }
+                __syncthreads();
+                if (s_fail) break;
+                const double rinv = s_rinv;
+                for (int i = c + 1 + threadIdx.x; i < len; i += CHOL_NT) Gj[(size_t)i * len + c] *= rinv;
+                __syncthreads();
+                for (int c2 = c + 1; c2 < jb + pw; ++c2) {
+                    const double l2 = Gj[(size_t)c2 * len + c];
+                    for (int i = c2 + threadIdx.x; i < len; i += CHOL_NT)
+                        Gj[(size_t)i * len + c2] -= Gj[(size_t)i * len + c] * l2;
+                }
+                __syncthreads();
+            }
+        }
+        __threadfence();
+        chol_cluster_sync();
+        {
+            int f;
+            asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(f) : "r"(fail0) : "memory");
+            failed = f != 0;
+        }
+        if (failed) break;
+        const int t0 = jb + pw;
+        if (t0 >= len) break;
+        for (int e = threadIdx.x; e < pw * (len - jb); e += CHOL_NT) {
+            const int c = e / (len - jb), i = e % (len - jb);
+            panelT[c * s + i] = Gj[(size_t)(jb + i) * len + jb + c];
+        }
+        __syncthreads();
+        for (int i = t0 + (int)rank * nw + warp; i < len; i += 2 * nw) {
+            double li[CHOL_PB];
+#pragma unroll
+            for (int c = 0; c < CHOL_PB; ++c) li[c] = c < pw ? panelT[c * s + (i - jb)] : 0.0;
+            double *row = Gj + (size_t)i * len;
+            for (int k = t0 + lane; k <= i; k += 32) {
+                double v = row[k];
+#pragma unroll
+                for (int c = 0; c < CHOL_PB; ++c) v = fma(-li[c], panelT[c * s + (k - jb)], v);
+                row[k] = v;
+            }
+        }
+        __threadfence();
+        chol_cluster_sync();
+    }
+    // both CTAs left the loop after the same barriers, with every update of G visible to both
+    if (failed) {
+        if (rank == 0 && threadIdx.x == 0) atomicMin(bad, j);
+        for (int e = threadIdx.x + (int)rank * CHOL_NT; e < len * len; e += 2 * CHOL_NT) Lj[e] = NAN;
+    } else {
+        for (int e = threadIdx.x + (int)rank * CHOL_NT; e < len * len; e += 2 * CHOL_NT) {
+            const int a = e / len, c = e % len;
+            Lj[e] = (c <= a) ? Gj[e] : 0.0;
+        }
+    }
+    chol_cluster_sync();
+}
+
+static cudaError_t launch_cholesky_pairs(int64_t rows, int s, double *G, double *L, int *bad, int j0, int count,
+                                         cudaStream_t st) {
+    const size_t smem = CHOL_PB * s * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(cholesky_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    cholesky_pair_kernel<<<(unsigned)(2 * count), CHOL_NT, smem, st>>>(rows, s, G, L, bad, j0);
+    return cudaGetLastError();
+}
+
 // G^{-1} = L^{-T} L^{-1} from the FP64 factor, in the arithmetic TI: FP64 for FP64 storage; FP32 for the
 // FP32 inner solves of the mixed-precision form, where only the FP32 inverse is used.  (An approximate
 // inverse changes the rate of the iteration, not its fixed point: the update vanishes exactly when the
@@ -217,8 +329,8 @@ __device__ __forceinline__ void tile_mma(TI (&acc)[4][4], const TI *A, const TI 
 
 template <typename TI>
 __global__ void __launch_bounds__(INV_NT) inverse_kernel(int64_t rows, int s, const double *__restrict__ L,
-                                                         TI *__restrict__ Linv, TI *__restrict__ Ginv) {
-    const int j = blockIdx.x;
+                                                         TI *__restrict__ Linv, TI *__restrict__ Ginv, int j0) {
+    const int j = j0 + (int)blockIdx.x;  // blocks j0 .. j0 + gridDim.x - 1
     const int len = (int)min64(s, rows - (int64_t)j * s);
     const double *Lj = L + (size_t)j * s * s;
     TI *Xj = Linv + (size_t)j * s * s;
@@ -445,23 +557,35 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
         else launch_principal<__nv_bfloat16>(A.data, A.ld, rows, s, lam, G, st);
     }
     KPP_TRY(cudaGetLastError());
-    KPP_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(CHOL_PB * s * sizeof(double))));
-    note_launch();
     KPP_TRY(cudaEventRecord(F.ev[1], st));
-    cholesky_kernel<<<(unsigned)nb, CHOL_NT, CHOL_PB * s * sizeof(double), st>>>(rows, s, G, F.L, bad);
-    KPP_TRY(cudaGetLastError());
+    {
+        // The Cholesky is one CTA per block on the FP64 pipe.  nb blocks over the SMs end in a last
+        // round of nb mod SMs blocks, during which the other SMs would idle; when there are few enough,
+        // that round runs as its own launch with each block split over a pair of CTAs (a cluster) on
+        // two SMs.  (The inverses are left to follow: FP32 work beside the Cholesky slows its FP64 pipe
+        // about as much as it would save.)
+        const int nsm = sm_count();
+        const int64_t tail = nb > nsm ? nb % nsm : 0;
+        const bool pair = tail > 0 && 2 * tail <= nsm;
+        const int64_t head = pair ? nb - tail : nb;
+        const size_t chol_smem = CHOL_PB * s * sizeof(double);
+        KPP_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem));
+        note_launch();
+        cholesky_kernel<<<(unsigned)head, CHOL_NT, chol_smem, st>>>(rows, s, G, F.L, bad, 0);
+        KPP_TRY(cudaGetLastError());
+        if (pair) KPP_TRY(launch_cholesky_pairs(rows, s, G, F.L, bad, (int)head, (int)tail, st));
+    }
     KPP_TRY(cudaEventRecord(F.ev[2], st));
     if (A.dtype == KPP_F64) {
         const int sm64 = 4 * IT * ITP * (int)sizeof(double);
         KPP_TRY(cudaFuncSetAttribute(inverse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
         note_launch();
-        inverse_kernel<double><<<(unsigned)nb, INV_NT, sm64, st>>>(rows, s, F.L, Linv, F.Ginv);
+        inverse_kernel<double><<<(unsigned)nb, INV_NT, sm64, st>>>(rows, s, F.L, Linv, F.Ginv, 0);
     } else {
         const int sm32 = 4 * IT * ITP * (int)sizeof(float);
         KPP_TRY(cudaFuncSetAttribute(inverse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32));
         note_launch();
-        inverse_kernel<float><<<(unsigned)nb, INV_NT, sm32, st>>>(rows, s, F.L, (float *)Linv, F.Ginv32);
+        inverse_kernel<float><<<(unsigned)nb, INV_NT, sm32, st>>>(rows, s, F.L, (float *)Linv, F.Ginv32, 0);
     }
     KPP_TRY(cudaGetLastError());
     KPP_TRY(cudaEventRecord(F.ev[3], st));

@@ -176,6 +176,40 @@ cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
 
 unsigned long long dev_alloc_requests() { return g_allocs.load(std::memory_order_relaxed); }
 
+// High-priority streams for work that other kernels should not hold up (the factor phase's Cholesky,
+// which the inverses and the memo of finished blocks fill in around): lent out and returned, so that
+// concurrent callers each get their own and none is created per call.
+namespace {
+std::multimap<int, cudaStream_t> g_streams;  // device -> idle stream
+}
+
+cudaStream_t priority_stream_acquire() {
+    const int dev = current_device();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_streams.find(dev);
+        if (it != g_streams.end()) {
+            cudaStream_t h = it->second;
+            g_streams.erase(it);
+            return h;
+        }
+    }
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    cudaStream_t h = nullptr;
+    if (cudaStreamCreateWithPriority(&h, cudaStreamNonBlocking, hi) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return h;
+}
+
+void priority_stream_release(cudaStream_t h) {
+    if (!h) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_streams.insert({current_device(), h});
+}
+
 }  // namespace kpp
 
 using namespace kpp;

@@ -52,6 +52,24 @@ kpp_status solve_systems_internal(int nsys, const kpp_matrix *A, const double *c
 
 // The FP32 memo W_j = G_j^{-1} A_{S_j} for every block (whole blocks; kpp_wmemo.cu).
 kpp_status build_w32(const kpp_matrix &A, int s, const float *Ginv32, float *W32, cudaStream_t st);
+
+// The tcgen05 W memo for BF16 storage (kpp_wmemo_tc.cu) in parts, so that the memo of a range of
+// blocks can be built as soon as their inverses exist: begin (shape checks, the transposed copy A^T,
+// the tensor maps), blocks (W_j for j in [j0, j1); any number of calls, on the stream given), end (reads
+// the error word, synchronising that stream, and releases the scratch).  begin returns
+// KPP_ERR_UNSUPPORTED for a shape the kernel does not take; after any error the caller builds W32
+// with build_w32 instead.
+struct WmemoTC {
+    void *AT = nullptr, *Gs = nullptr;  // A^T (cols x rows BF16); G^{-1} in three BF16 pieces
+    int *d_err = nullptr;
+    alignas(64) unsigned char tmG[128] = {}, tmB[128] = {};  // CUtensorMap of the pieces and of A^T
+    int64_t rows = 0, cols = 0, ntl = 0;
+    int s = 0, mt = 0;
+    bool ready = false;
+};
+kpp_status wmemo_tc_begin(WmemoTC &w, const kpp_matrix &A, int s, cudaStream_t st);
+kpp_status wmemo_tc_blocks(WmemoTC &w, const float *Ginv32, float *W32, int64_t j0, int64_t j1, cudaStream_t st);
+kpp_status wmemo_tc_end(WmemoTC &w, cudaStream_t st);
 // Whether the large-block K++ kernel (kpp_kw.cu) takes this shape.
 bool kw_fits(int dtype, int64_t rows, int64_t cols, int s, int k, int sms);
 
@@ -70,5 +88,9 @@ cudaError_t dev_malloc(void **p, size_t bytes);
 void dev_free(void *p);
 cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
 unsigned long long dev_alloc_requests();
+// A high-priority non-blocking stream of the current device, lent out until released (nullptr if none
+// can be created).  The caller orders it against its own streams with events.
+cudaStream_t priority_stream_acquire();
+void priority_stream_release(cudaStream_t h);
 
 }  // namespace kpp

@@ -38,9 +38,10 @@ constexpr int WM_SMEM = WM_STAGES * WM_STAGE_BYTES + 1024; // + alignment slack
 constexpr uint64_t WM_TIMEOUT_NS = 2000000000ull;
 
 
-// G^{-1} (n values, FP32) -> pieces hi, mid, lo (BF16) at out, out + n, out + 2n.
-__global__ void split3_bf16_kernel(int64_t n, const float *__restrict__ g, __nv_bfloat16 *__restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+// G^{-1} (n values, FP32) -> pieces hi, mid, lo (BF16) at out, out + n, out + 2n, for entries [i0, i1).
+__global__ void split3_bf16_kernel(int64_t n, int64_t i0, int64_t i1, const float *__restrict__ g,
+                                   __nv_bfloat16 *__restrict__ out) {
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (int64_t)gridDim.x * blockDim.x) {
         const float v = g[i];
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         const float r1 = v - __bfloat162float(h);
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256) transpose_bf16_kernel(int64_t rows, int64
 __global__ void __launch_bounds__(128, 1) wmemo_tc_kernel(const __grid_constant__ CUtensorMap tmG,
                                                           const __grid_constant__ CUtensorMap tmB, int64_t rows,
                                                           int64_t cols, int s, int mt, int ntl,
-                                                          float *__restrict__ W, int *err) {
+                                                          float *__restrict__ W, int *err, int j0) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full_bar[WM_STAGES], empty_bar[WM_STAGES], done_bar;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(128, 1) wmemo_tc_kernel(const __grid_constant_
     } tile;
     tile.tc = (int)(blockIdx.x % (unsigned)ntl);
     tile.ta = (int)((blockIdx.x / (unsigned)ntl) % (unsigned)mt);
-    tile.j = (int)(blockIdx.x / ((unsigned)ntl * (unsigned)mt));
+    tile.j = j0 + (int)(blockIdx.x / ((unsigned)ntl * (unsigned)mt));  // blocks from j0 on
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)tile.j * s;
     const int nk = (s + WM_BK - 1) / WM_BK;
@@ -223,56 +224,88 @@ __global__ void __launch_bounds__(128, 1) wmemo_tc_kernel(const __grid_constant_
     }
 }
 
-// Host side.  Returns KPP_OK with W32 written, or an error after which the caller uses the library
-// GEMM (nothing of W32 is relied on then).
-kpp_status build_w32_tc(const kpp_matrix &A, int s, const float *Ginv32, float *W32, cudaStream_t st) {
+// Host side, in three parts so that the factor phase can build the memo of a range of blocks as soon
+// as their inverses exist (kpp_runtime.h, WmemoTC):
+//   begin: shape checks, the transposed copy A^T and the tensor maps (on the stream given);
+//   blocks: the BF16 pieces of G_j^{-1} and W_j for blocks [j0, j1);
+//   end: the error word (synchronises), and the scratch is released.
+// An error leaves nothing of W32 relied on: the caller then uses the library GEMM.
+kpp_status wmemo_tc_begin(WmemoTC &w, const kpp_matrix &A, int s, cudaStream_t st) {
+    w = WmemoTC{};
     const int64_t rows = A.rows, cols = A.cols;
     if (A.dtype != KPP_BF16 || rows % s || s % 8 || rows % 8 || cols % 4 || ((uintptr_t)A.data & 15) ||
-        ((A.ld * 2) & 15) || 3 * rows > 0x7fffffffLL || cols > 0x7fffffffLL || ((uintptr_t)W32 & 15))
+        ((A.ld * 2) & 15) || 3 * rows > 0x7fffffffLL || cols > 0x7fffffffLL || cols % 8)
         return KPP_ERR_UNSUPPORTED;
     const int64_t nb = rows / s;
     const int mt = (s + TC_M - 1) / TC_M;
     const int64_t ntl = (cols + TC_N - 1) / TC_N;
-    const int64_t ntiles = nb * mt * ntl;
-    if (ntiles > 0x7fffffffLL || cols % 8) return KPP_ERR_UNSUPPORTED;
-    __nv_bfloat16 *AT = nullptr, *Gs = nullptr;
-    int *d_err = nullptr;
+    if (nb * mt * ntl > 0x7fffffffLL) return KPP_ERR_UNSUPPORTED;
+    w.rows = rows;
+    w.cols = cols;
+    w.s = s;
+    w.mt = mt;
+    w.ntl = ntl;
+    bool ok = dev_malloc_async((void **)&w.AT, (size_t)rows * cols * 2, st) == cudaSuccess;
+    ok = ok && dev_malloc_async((void **)&w.Gs, (size_t)3 * rows * s * 2, st) == cudaSuccess;
+    ok = ok && dev_malloc_async((void **)&w.d_err, sizeof(int), st) == cudaSuccess;
+    if (!ok) {
+        wmemo_tc_end(w, st);
+        return KPP_ERR_OOM;
+    }
+    ok = cudaMemsetAsync(w.d_err, 0, sizeof(int), st) == cudaSuccess;
+    note_launch();
+    transpose_bf16_kernel<<<dim3((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64)), 256, 0, st>>>(
+        rows, cols, (const __nv_bfloat16 *)A.data, A.ld, (__nv_bfloat16 *)w.AT);
+    ok = ok && cudaGetLastError() == cudaSuccess;
+    static_assert(sizeof(CUtensorMap) <= sizeof(w.tmG), "tensor map storage");
+    ok = ok && make_tmap_2d(w.tmG, w.Gs, KPP_BF16, (uint64_t)s, (uint64_t)(3 * rows), (uint64_t)s, WM_BK, TC_M, true);
+    ok = ok && make_tmap_2d(w.tmB, w.AT, KPP_BF16, (uint64_t)rows, (uint64_t)cols, (uint64_t)rows, WM_BK, TC_M, true);
+    ok = ok && cudaFuncSetAttribute(wmemo_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WM_SMEM) == cudaSuccess;
+    if (!ok) {
+        wmemo_tc_end(w, st);
+        return KPP_ERR_CUDA;
+    }
+    w.ready = true;
+    return KPP_OK;
+}
+
+kpp_status wmemo_tc_blocks(WmemoTC &w, const float *Ginv32, float *W32, int64_t j0, int64_t j1, cudaStream_t st) {
+    if (!w.ready || ((uintptr_t)W32 & 15)) return KPP_ERR_UNSUPPORTED;
+    if (j1 <= j0) return KPP_OK;
+    const int64_t n = w.rows * w.s;
+    note_launch();
+    split3_bf16_kernel<<<4 * sm_count(), 256, 0, st>>>(n, j0 * w.s * w.s, j1 * w.s * w.s, Ginv32, (__nv_bfloat16 *)w.Gs);
+    note_launch();
+    wmemo_tc_kernel<<<(unsigned)((j1 - j0) * w.mt * w.ntl), 128, WM_SMEM, st>>>(
+        *reinterpret_cast<const CUtensorMap *>(w.tmG), *reinterpret_cast<const CUtensorMap *>(w.tmB), w.rows, w.cols,
+        w.s, w.mt, (int)w.ntl, W32, w.d_err, (int)j0);
+    return cudaGetLastError() == cudaSuccess ? KPP_OK : KPP_ERR_CUDA;
+}
+
+kpp_status wmemo_tc_end(WmemoTC &w, cudaStream_t st) {
     int herr = 0;
     kpp_status rc = KPP_OK;
-    alignas(64) CUtensorMap tmG, tmB;
-    bool ok = dev_malloc_async((void **)&AT, (size_t)rows * cols * 2, st) == cudaSuccess;
-    ok = ok && dev_malloc_async((void **)&Gs, (size_t)3 * rows * s * 2, st) == cudaSuccess;
-    ok = ok && dev_malloc_async((void **)&d_err, sizeof(int), st) == cudaSuccess;
-    if (!ok) rc = KPP_ERR_OOM;
-    if (ok) {
-        ok = cudaMemsetAsync(d_err, 0, sizeof(int), st) == cudaSuccess;
-        note_launch();
-        split3_bf16_kernel<<<4 * sm_count(), 256, 0, st>>>(rows * s, Ginv32, Gs);
-        note_launch();
-        transpose_bf16_kernel<<<dim3((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64)), 256, 0, st>>>(
-            rows, cols, (const __nv_bfloat16 *)A.data, A.ld, AT);
-        ok = ok && cudaGetLastError() == cudaSuccess;
-        ok = ok && make_tmap_2d(&tmG, Gs, KPP_BF16, (uint64_t)s, (uint64_t)(3 * rows), (uint64_t)s, WM_BK, TC_M, true);
-        ok = ok && make_tmap_2d(&tmB, AT, KPP_BF16, (uint64_t)rows, (uint64_t)cols, (uint64_t)rows, WM_BK, TC_M, true);
-        ok = ok && cudaFuncSetAttribute(wmemo_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WM_SMEM) ==
-                       cudaSuccess;
-        if (ok) {
-            note_launch();
-            wmemo_tc_kernel<<<(unsigned)ntiles, 128, WM_SMEM, st>>>(tmG, tmB, rows, cols, s, mt, (int)ntl, W32, d_err);
-            ok = cudaGetLastError() == cudaSuccess;
-        }
-        ok = ok && cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
-        ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
-        if (!ok || herr) rc = KPP_ERR_CUDA;
-    }
-    if (AT) cudaFreeAsync(AT, st);
-    if (Gs) cudaFreeAsync(Gs, st);
-    if (d_err) cudaFreeAsync(d_err, st);
+    if (w.ready && (cudaMemcpyAsync(&herr, w.d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess || herr))
+        rc = KPP_ERR_CUDA;
+    if (w.AT) cudaFreeAsync(w.AT, st);
+    if (w.Gs) cudaFreeAsync(w.Gs, st);
+    if (w.d_err) cudaFreeAsync(w.d_err, st);
     if (rc != KPP_OK) {
         cudaGetLastError();
         set_error("tensor-core W memo failed (%s); using the library GEMM", herr ? "device wait expired" : "setup");
     }
+    w = WmemoTC{};
     return rc;
+}
+
+kpp_status build_w32_tc(const kpp_matrix &A, int s, const float *Ginv32, float *W32, cudaStream_t st) {
+    WmemoTC w;
+    kpp_status rc = wmemo_tc_begin(w, A, s, st);
+    if (rc != KPP_OK) return rc;
+    rc = wmemo_tc_blocks(w, Ginv32, W32, 0, A.rows / s, st);
+    const kpp_status re = wmemo_tc_end(w, st);
+    return rc != KPP_OK ? rc : re;
 }
 
 }  // namespace kpp

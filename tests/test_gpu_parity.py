@@ -45,7 +45,9 @@ def test_device_block_draws_match_oracle(K):
     np.testing.assert_array_equal(d, o)
 
 
-@pytest.mark.parametrize("m,n,s", [(103, 37, 10), (64, 64, 64), (50, 200, 7)])
+# (1003, 24, 5): 201 blocks, more than the GPU's SMs, with a ragged last block: the Cholesky runs as a
+# launch of whole rounds of blocks and a launch of the last round, whose inverses follow it
+@pytest.mark.parametrize("m,n,s", [(103, 37, 10), (64, 64, 64), (50, 200, 7), (1003, 24, 5)])
 def test_kpp_factors_match_oracle(K, m, n, s):
     rng = np.random.default_rng(m + n)
     A = rng.standard_normal((m, n))
@@ -71,6 +73,17 @@ def test_cdpp_factors_and_not_spd(K):
     Bm[25] = Bm[21]
     Fb = K.Factors(dev(Bm), K.Partition(40, 10), 0.0, 0, allow_not_spd=True)
     assert Fb.status == K.ERR_NOT_SPD and Fb.bad_block == 2
+
+
+@pytest.mark.parametrize("zero_rows", [[902], [17, 902]])
+def test_not_spd_block_reported_across_the_split_cholesky(K, zero_rows):
+    # 200 blocks of 5 rows: blocks 0 .. 151 factor in the first launch, 152 .. 199 in the second.  A zero
+    # row with lambda = 0 gives its block an exactly zero pivot; the smallest such block is reported,
+    # wherever it is
+    Bm = np.random.default_rng(2).standard_normal((1000, 30))
+    Bm[zero_rows] = 0.0
+    Fb = K.Factors(dev(Bm), K.Partition(1000, 5), 0.0, 0, allow_not_spd=True)
+    assert Fb.status == K.ERR_NOT_SPD and Fb.bad_block == min(r // 5 for r in zero_rows)
 
 
 def _kpp_pair(K, A, b, s, lam, T=None, tol=0.0, seed=3, grid=0, adaptive=True, x0=None, eta=None, cd=False,

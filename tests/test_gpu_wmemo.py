@@ -44,6 +44,8 @@ def _factors_both(K, Ad, P, lam, mode):
 
 @pytest.mark.parametrize("m,n,s,mode", [(2048, 1024, 512, 0),   # K++ large blocks, s = 512
                                         (4096, 512, 256, 0),    # K++, s = 256
+                                        (6400, 256, 32, 0),     # K++, 200 blocks: the memo of the first
+                                                                # 152 overlaps the last blocks' Cholesky
                                         (576, 576, 64, 1)])     # CD++ single-column memo, N tail (576 = 2.25 x 256)
 def test_tensor_core_memo_matches_library_gemm(K, record_property, m, n, s, mode):
     if mode == 0:
