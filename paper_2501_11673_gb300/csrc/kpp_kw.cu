@@ -6,11 +6,13 @@
 // factor phase builds it next to G^{-1}), the only value a CTA needs from the others in a step is the
 // s-vector r, so a step is:
 //   1. exchange: the per-chunk partials of r are summed by a reduce-scatter inside each 4-CTA cluster
-//      (distributed shared memory), a tagged mailbox between the clusters (each CTA publishes s/4
-//      cluster sums and reads the same slice from every cluster), and an all-gather inside the cluster;
+//      (each CTA pushes the rows of its partial into the owner's shared memory), a tagged mailbox
+//      between the clusters (each CTA publishes s/4 cluster sums and reads the same slice from every
+//      cluster), and an all-gather inside the cluster (each CTA pushes its slice of r to the others);
 //   2. w = W_S^T r on my 32 columns, then m and x there;
 //   3. the partial r of the next block on my columns (its A tile is already in shared memory).
-// A and W tiles are prefetched two steps ahead by TMA.  The window sums and checkpoints (Eq. 5.2 -
+// A tiles are prefetched two steps ahead and W tiles one step ahead by TMA; the copies, the block draws
+// and the loads of b are issued while the mailbox is polled, off the step's critical path.  The window sums and checkpoints (Eq. 5.2 -
 // 5.3, Alg. 3) are computed by every CTA from the same r in the same order, so every CTA takes the
 // same decisions without a grid barrier.  Hardware cluster barriers cannot time out, so every exit
 // from the step loop is taken by all CTAs of a cluster together (failures are OR-ed over the cluster
@@ -77,6 +79,12 @@ __device__ __forceinline__ int kw_ld_cluster_s32(uint32_t a) {
     int v;
     asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
     return v;
+}
+__device__ __forceinline__ void kw_st_cluster_f32(uint32_t a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void kw_st_cluster_s32(uint32_t a, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long kw_ld_relaxed(const unsigned long long *p) {
     unsigned long long v;
@@ -154,9 +162,8 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
     const SmemK L = kw_layout(s, (int)sizeof(TA));
 #define KW_W(i) ((const float *)(sm + L.w[i]))
 #define KW_A(i) ((const TA *)(sm + L.a[i]))
-    __shared__ float s_p[KW_SMAX];      // my partial of r (read by the cluster)
+    __shared__ float s_in[KW_CL][KW_SMAX / KW_CL];  // partials of my slice of r, by source rank (pushed)
     __shared__ __align__(16) float s_r[KW_SMAX];  // r of the step (read as float4)
-    __shared__ float s_rs[KW_SMAX / KW_CL];  // my slice of r (read by the cluster)
     __shared__ float s_mail[KW_MAILMAX];     // my slice from every cluster (cluster-major)
     __shared__ float s_red[NW][KW_CW];
     __shared__ float s_rn[NW];
@@ -165,6 +172,8 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
     __shared__ ColState st[1];
     __shared__ double s_part[NW];
     __shared__ int s_flag;              // my failure flag (read by the cluster)
+    __shared__ int s_flags[KW_CL];      // every CTA's failure flag of the step (pushed)
+    __shared__ int s_jq[4];             // block of steps t .. t + 3 (ring by t mod 4)
     __shared__ int s_fail, s_stop;
     __shared__ unsigned s_phW[2], s_phA[2];
     __shared__ int s_pendW[2], s_pendA[2];
@@ -247,8 +256,7 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
                 group_fail(gs, KPP_ERR_TIMEOUT);
                 return;
             }
-            const int j = draw_block(cm.seed, tt, sys.sys_id, nb);
-            const int S0 = j * s;
+            const int S0 = s_jq[tt & 3] * s;
             mbar_arrive_expect_tx(&mbA[i], (unsigned)(s * KW_CW * sizeof(TA)));
             for (int r0 = 0; r0 < s; r0 += box)
                 tma_load_2d((void *)(KW_A(i) + (size_t)r0 * KW_CW), &sys.tmA, (int)c0, S0 + r0, &mbA[i]);
@@ -260,8 +268,7 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
                 group_fail(gs, KPP_ERR_TIMEOUT);
                 return;
             }
-            const int j = draw_block(cm.seed, tt, sys.sys_id, nb);
-            const int S0 = j * s;
+            const int S0 = s_jq[tt & 3] * s;
             mbar_arrive_expect_tx(&mbW[i], (unsigned)(s * KW_CW * 4));
             for (int r0 = 0; r0 < s; r0 += box)
                 tma_load_2d((void *)(KW_W(i) + (size_t)r0 * KW_CW), &sys.tmW, (int)c0, S0 + r0, &mbW[i]);
@@ -279,7 +286,8 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
             }
             __syncthreads();
         };
-        // my partial of r for the block whose A tile is in buffer i: p[a] = sum_c A[a][c] x_c (c my columns)
+        // my partial of r for the block whose A tile is in buffer i: p[a] = sum_c A[a][c] x_c (c my columns),
+        // pushed into the shared memory of row a's owner (rank a / SL), at my rank's place
         auto partial = [&](int i) {
             const TA *tl = KW_A(i);
             const int rs = lane / CG, cgi = lane % CG;
@@ -292,17 +300,16 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
                 float acc = KwRow<TA>::dot(tl + (size_t)a * KW_CW + cgi * PER, xv);
 #pragma unroll
                 for (int o = 1; o < CG; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (cgi == 0) s_p[a] = acc;
+                if (cgi == 0) kw_st_cluster_f32(kw_mapa(&s_in[q][a % SL], (unsigned)(a / SL)), acc);
             }
         };
 
+        // A of steps t, t + 1 and W of step t now; then, at step t, A of t + 2 and W of t + 1
         if (threadIdx.x == 0 && t < t_end) {
+            for (int d = 0; d < 2; ++d) s_jq[(t + d) & 3] = draw_block(cm.seed, t + d, sys.sys_id, nb);
             issueA(t, (int)(t & 1));
             issueW(t, (int)(t & 1));
-            if (t + 1 < t_end) {
-                issueA(t + 1, (int)((t + 1) & 1));
-                issueW(t + 1, (int)((t + 1) & 1));
-            }
+            if (t + 1 < t_end) issueA(t + 1, (int)((t + 1) & 1));
         }
         __syncthreads();
         if (t < t_end) {
@@ -312,19 +319,29 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
 
         while (t < t_end) {
             const int bi = (int)(t & 1);
-            const int j = draw_block(cm.seed, t, sys.sys_id, nb);
-            const int S0 = j * s;
+            const int S0 = s_jq[t & 3] * s;
+            // my slice of b_S, loaded now and used after the mailbox
+            const float bv = threadIdx.x < SL ? b[S0 + (int)q * SL + threadIdx.x] : 0.0f;
 
             // ---- 1. exchange: reduce-scatter in the cluster, mailbox between clusters, all-gather ----
             __syncthreads();
-            kw_cluster_sync();  // partials of every CTA of the cluster are written
+            kw_cluster_sync();  // partials of every CTA of the cluster have been pushed
             if (threadIdx.x < SL) {
                 const int e = (int)q * SL + threadIdx.x;
                 float v = 0.0f;
 #pragma unroll
-                for (unsigned rr = 0; rr < KW_CL; ++rr) v += kw_ld_cluster_f32(kw_mapa(&s_p[e], rr));
+                for (int rr = 0; rr < KW_CL; ++rr) v += s_in[rr][threadIdx.x];
                 unsigned long long *slot = sys.mail + ((size_t)(t % KW_RING) * ncl + cl) * s;
                 kw_st_relaxed(slot + e, ((unsigned long long)(unsigned)(t + 1) << 32) | __float_as_uint(v));
+            }
+            // while the mailbox fills: the block of step t + 2 and the copies whose buffers are free (A of
+            // step t went into my partial before this step; W of step t - 1 into its update)
+            if (threadIdx.x == NT - 32) {
+                if (t + 2 < t_end) {
+                    s_jq[(t + 2) & 3] = draw_block(cm.seed, t + 2, sys.sys_id, nb);
+                    issueA(t + 2, bi);
+                }
+                if (t + 1 < t_end) issueW(t + 1, bi ^ 1);
             }
             {
                 // read my slice from every cluster: all threads issue their loads first, then re-poll the
@@ -376,20 +393,15 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
                 const int eg = (int)q * SL + threadIdx.x;
                 float v = 0.0f;
                 for (int c = 0; c < ncl; ++c) v += s_mail[c * SL + threadIdx.x];  // cluster order
-                s_rs[threadIdx.x] = v - b[S0 + eg];
+                v -= bv;
+#pragma unroll
+                for (int rr = 0; rr < KW_CL; ++rr) kw_st_cluster_f32(kw_mapa(&s_r[eg], (unsigned)rr), v);
             }
-            if (threadIdx.x == 0) s_flag = s_fail;
-            kw_cluster_sync();  // slices and failure flags of every CTA of the cluster are written
-            for (int e = threadIdx.x; e < s; e += NT) s_r[e] = kw_ld_cluster_f32(kw_mapa(&s_rs[e % SL], e / SL));
-            if (threadIdx.x < KW_CL) {
-                const int f = kw_ld_cluster_s32(kw_mapa(&s_flag, threadIdx.x));
-                if (f) s_fail = 1;  // benign race: every writer writes 1
-            }
+            if (threadIdx.x < KW_CL) kw_st_cluster_s32(kw_mapa(&s_flags[q], threadIdx.x), s_fail);
+            kw_cluster_sync();  // slices of r and failure flags of every CTA of the cluster have been pushed
+            if (threadIdx.x < KW_CL && s_flags[threadIdx.x]) s_fail = 1;  // benign race: every writer writes 1
             __syncthreads();
             if (s_fail) break;  // uniform over the cluster (every CTA saw every flag)
-
-            // the A buffer of step t is free: prefetch the A tile of step t + 2 into it
-            if (threadIdx.x == NT - 32 && t + 2 < t_end) issueA(t + 2, bi);
 
             // |r|^2 (FP32 in a fixed order, accumulated in FP64)
             {
@@ -449,8 +461,6 @@ __global__ void __launch_bounds__(NT, 1) kw_kernel(const SysK *__restrict__ syst
                 else cs.E1 += (double)rn;
             }
             __syncthreads();
-            // the W buffer of step t is free: prefetch the W tile of step t + 2 into it
-            if (threadIdx.x == NT - 32 && t + 2 < t_end) issueW(t + 2, bi);
 
             // ---- 3. my partial of r_{t+1} ----
             if (t + 1 < t_end) {
