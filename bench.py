@@ -446,6 +446,64 @@ class SingleFP64(Workload):
                                   self.unit, "block iterations of the same workload (FP64 C oracle)", it0=256)
 
 
+class MemoSPD(SingleFP64):
+    """The cdpp4096 system solved by CD++ with the online block memoisation (random s-subsets memoised
+    as they are drawn) instead of the fixed partition: kpp_solve_memo, to 1e-8."""
+
+    def __init__(self):
+        super().__init__("cdpp4096")
+        self.name = "cdpp4096-memo"
+        self.kernel = "memo_kernel"
+        self.desc = self.desc.replace("s=64 contiguous", "s=64 random subsets memoised online (Sec. 4)")
+        self.run_cg_reference = False
+
+    def step(self):
+        kpp = self.kpp
+        self.x.zero_()
+        rep, nb = kpp.solve_memo(self.Ad, self.bd, self.x, self.sy.s, self.prm, cd=True)
+        self.nblocks = nb
+        return {"units": rep.iters, "ok": rep.status == kpp.OK and rep.rel_res_true <= self.sy.tol,
+                "kernel_ms": rep.kernel_ms, "kernel_launches": rep.launches, "iters": rep.iters,
+                "outer": 0, "rel_res": rep.rel_res_true, "blocks": nb}
+
+    def per_iter(self):
+        """One memo CD++ step: r = A_S x - b_S from the stored rows (s x n), y = G^-1 r (s x s), x and the
+        momentum on every column (read + written)."""
+        n, s = self.sy.A.shape[1], self.sy.s
+        return 2 * s * n + 2 * s * s + 5 * n, 8 * (s * n + s * s + 4 * n + 2 * s)
+
+    def roofline(self, steps, peaks):
+        flops, byts = self.per_iter()
+        iters = statistics.mean(st["iters"] for st in steps)
+        kms = statistics.mean(st["kernel_ms"] for st in steps)
+        out = _hbm_roof(self.kernel, iters * byts, kms, peaks, f"{self.kernel}/{self.name}", {"bytes": byts},
+                        {"note": "all window launches of the step; the stored rows of the memoised blocks "
+                                 "(blocks x s x n FP64) exceed L2, so each step reads A_S from HBM"})
+        return out
+
+    def extra(self, steps):
+        return {"memoised_blocks": statistics.mean(st["blocks"] for st in steps),
+                "fixed_partition_blocks": -(-self.sy.A.shape[0] // self.sy.s)}
+
+    def e2e(self):
+        return None
+
+    def cpu_baseline(self, budget_s):
+        import oracle
+        A, b, s = self.sy.A, self.sy.b, self.sy.s
+        k = 64
+        while True:
+            t0 = time.perf_counter()
+            oracle.run_memo(A, b, s, cd=True, lam=self.sy.lam, tol=0.0, max_iters=k, seed=self.seed)
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 4 or k >= 1 << 20:
+                break
+            k *= 4
+        return {"value": k / dt, "unit": self.unit, "cores": 1, "kind": "oracle",
+                "sample": f"{k} steps of the oracle's memo CD++ (oracle.run_memo) on the same system, one host "
+                          f"thread, new blocks factored as drawn ({dt:.1f} s)"}
+
+
 class MixedSPD(SingleFP64):
     """The cdpp4096 system stored FP32 / BF16 with FP32 iterations and FP64 refinement."""
 
@@ -1003,6 +1061,8 @@ def make_workload(args):
         return Serving(n_req=args.requests)
     if args.workload == "cdpp4096-rht":
         return RhtSPD()
+    if args.workload == "cdpp4096-memo":
+        return MemoSPD()
     if args.workload in ("cdpp4096-f32", "cdpp4096-bf16"):
         return MixedSPD(args.workload.split("-")[1])
     raise SystemExit(f"unknown workload {args.workload}")
@@ -1077,7 +1137,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed262144",
                     choices=["cdpp4096", "kpp2000", "mixed262144", "batched64", "serving", "cdpp4096-f32",
-                             "cdpp4096-bf16", "cdpp4096-rht"])
+                             "cdpp4096-bf16", "cdpp4096-rht", "cdpp4096-memo"])
     ap.add_argument("--storage", default="bf16", choices=["bf16", "f32"], help="mixed262144 storage type")
     ap.add_argument("--noisy", action="store_true", help="mixed262144: b = A x* + 1e-6 N(0,I)")
     ap.add_argument("--mixed-rows", type=int, default=262144,

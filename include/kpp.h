@@ -338,6 +338,28 @@ kpp_status kpp_rht_inverse(int64_t n, const double *d, const double *xbar, doubl
  * Host only: no device memory and no stream.  Errors: KPP_ERR_ARG for an invalid argument, or when
  * the window draws more than subsets_cap new blocks (subsets_cap >= count always suffices; *nb_out
  * then holds the count reached). */
+/* K++ (mode 0) or CD++ (mode 1) with the online block memoisation (Sec. 4 "Block memoization", Sec.
+ * 5.2; the sampling steps of Alg. 3 and Alg. 5) instead of a fixed partition: step t samples a new
+ * uniformly random s-subset S of the rows with probability p_t (as kpp_memo_sequence draws it) and
+ * memoises the factor of its block (K++: chol(A_S A_S^T + lambda I), CD++: chol(A_SS + lambda I)), or
+ * reuses a memoised block picked uniformly.  The step on S is Eq. 1.3 - 1.4 (K++) or Eq. 5.1 (CD++,
+ * with the block residual r = A_S x - b_S computed directly); zeta = ceil(rows / s) sets the windows of
+ * the residual estimate, the adaptive rho and the stop rule (Eq. 5.2 - 5.3), and a stop is confirmed
+ * by the FP64 residual of the whole system.
+ * A: device FP64, rows x cols, row-major (ld >= cols); CD++: square and symmetric.  b (rows) and x
+ * (cols; in: x0, out: the result): device FP64, one right-hand side.  s: 1 <= s <= min(rows, 1024).
+ * p: lambda, tol, max_iters, seed, sys_id, eta, rho0, adaptive_rho as for kpp_solve (grid and refine
+ * are ignored).  rep (host, may be NULL): iters, rel_res_true (FP64, after the solve), rel_res_est,
+ * rho_final, status, kernel_ms, launches.  *nblocks_out (may be NULL): the number of blocks memoised
+ * by the steps that ran (a window's draws beyond a stop are not counted).
+ * The solve runs in windows of max(256, min(16 zeta, 8192)) steps: the host draws the window's block
+ * sequence, the rows of the new subsets are gathered into a device store (about blocks x s x (cols + s)
+ * doubles) and factored in one batch, and a persistent kernel runs the window's steps from a table.
+ * Errors: KPP_ERR_ARG; KPP_ERR_NOT_SPD (rep->bad_block: the memo index); KPP_ERR_NO_CONVERGENCE (x
+ * holds the last iterate); KPP_ERR_OOM; KPP_ERR_CUDA; KPP_ERR_TIMEOUT.  Synchronises `stream`. */
+kpp_status kpp_solve_memo(const kpp_matrix *A, const double *b, double *x, int32_t s, int32_t mode, const kpp_params *p,
+                          kpp_report *rep, int64_t *nblocks_out, void *stream);
+
 kpp_status kpp_memo_sequence(uint64_t seed, uint32_t sys_id, int32_t mode, int64_t rows, int64_t cols, int32_t s,
                              int64_t t0, int64_t count, int64_t nb0, int64_t *blocks, int64_t *subsets,
                              int64_t subsets_cap, int64_t *nb_out);

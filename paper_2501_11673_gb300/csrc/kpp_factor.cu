@@ -508,6 +508,55 @@ int block_gram(const kpp_matrix &A, int s, double lam, double *G, int engine, cu
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
+// FP64 Cholesky factors and inverses of nblk Grams given in G (block i: s x s, row-major, packed), for
+// blocks formed elsewhere (the online memo's new subsets).  G is factored in place; Ginv receives
+// G_i^{-1} (nblk x s x s).  A block with a non-positive pivot sets *bad_block to its index (the smallest
+// such) and the call returns KPP_ERR_NOT_SPD.
+kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *bad_block, cudaStream_t st) {
+    *bad_block = -1;
+    if (nblk <= 0) return KPP_OK;
+    const int64_t rows = nblk * s;
+    const size_t blk = (size_t)s * s;
+    double *L = nullptr, *Linv = nullptr;
+    int *bad = nullptr;
+    kpp_status rc = KPP_OK;
+    const int big = 0x7fffffff;
+    int hb = big;
+    const size_t chol_smem = CHOL_PB * s * sizeof(double);
+    const int sm64 = 4 * IT * ITP * (int)sizeof(double);
+    if (dev_malloc_async((void **)&L, nblk * blk * sizeof(double), st) != cudaSuccess ||
+        dev_malloc_async((void **)&Linv, nblk * blk * sizeof(double), st) != cudaSuccess ||
+        dev_malloc_async((void **)&bad, sizeof(int), st) != cudaSuccess) {
+        rc = KPP_ERR_OOM;
+        set_error("factor_grams: out of device memory for %lld blocks", (long long)nblk);
+    }
+    if (rc == KPP_OK &&
+        (cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem) !=
+             cudaSuccess ||
+         cudaFuncSetAttribute(inverse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64) != cudaSuccess))
+        rc = KPP_ERR_CUDA;
+    if (rc == KPP_OK) {
+        note_launch();
+        cholesky_kernel<<<(unsigned)nblk, CHOL_NT, chol_smem, st>>>(rows, s, G, L, bad, 0);
+        note_launch();
+        inverse_kernel<double><<<(unsigned)nblk, INV_NT, sm64, st>>>(rows, s, L, Linv, Ginv, 0);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = KPP_ERR_CUDA;
+            set_error("factor_grams: launch failed");
+        } else if (hb != big) {
+            *bad_block = hb;
+            rc = KPP_ERR_NOT_SPD;
+        }
+    }
+    if (L) cudaFreeAsync(L, st);
+    if (Linv) cudaFreeAsync(Linv, st);
+    if (bad) cudaFreeAsync(bad, st);
+    return rc;
+}
+
 kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, FactorSet &F, cudaStream_t st) {
     const int64_t rows = A.rows;
     const int64_t nb = (rows + s - 1) / s;

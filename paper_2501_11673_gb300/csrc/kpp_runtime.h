@@ -33,6 +33,9 @@ struct FactorSet {
 };
 
 kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, FactorSet &F, cudaStream_t st);
+// FP64 Cholesky and inverse of nblk packed s x s Grams (G factored in place, G^{-1} into Ginv); the
+// smallest block with a non-positive pivot goes to *bad_block and the call returns KPP_ERR_NOT_SPD.
+kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *bad_block, cudaStream_t st);
 
 // Tensor-core block Gram for FP32/BF16 storage (kpp_gram_tc.cu).  Writes G (nb x s x s, FP64,
 // block j packed with leading dimension len) and returns true, or returns false when the shape is

@@ -37,7 +37,7 @@ EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_par
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
            "kpp_tune_cache_load", "kpp_launch_count", "kpp_device_alloc_count", "kpp_device_cache_bytes", "kpp_device_cache_trim", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
            "kpp_memo_sequence", "kpp_state_create", "kpp_state_destroy", "kpp_state_step",
-           "kpp_state_bytes", "kpp_state_save", "kpp_state_load", "kpp_solve_resume", "cdpp_solve_resume", "kpp_cg", "kpp_gmres", "kpp_tune_block_size"]
+           "kpp_state_bytes", "kpp_state_save", "kpp_state_load", "kpp_solve_resume", "cdpp_solve_resume", "kpp_cg", "kpp_gmres", "kpp_tune_block_size", "kpp_solve_memo"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
 
@@ -164,6 +164,9 @@ def load(path: str | None = None):
                                              ctypes.POINTER(i32), i32, ctypes.POINTER(Params), i32,
                                              ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
         lib.kpp_tune_block_size.restype = ctypes.c_int
+        lib.kpp_solve_memo.argtypes = [ctypes.POINTER(Matrix), vp, vp, i32, i32, ctypes.POINTER(Params),
+                                       ctypes.POINTER(Report), ctypes.POINTER(i64), vp]
+        lib.kpp_solve_memo.restype = ctypes.c_int
         lib.kpp_cg.argtypes = [ctypes.POINTER(Matrix), vp, vp, dbl, i64, ctypes.POINTER(Report), vp]
         lib.kpp_cg.restype = ctypes.c_int
         lib.kpp_gmres.argtypes = [ctypes.POINTER(Matrix), vp, vp, i32, dbl, i64, ctypes.POINTER(Report), vp]
@@ -379,6 +382,17 @@ def tune_block_size(As: list, Bs: list, candidates: list, prm: Params, cd: bool 
     _check(load().kpp_tune_block_size(n, mats, bp, k, cand, len(candidates), ctypes.byref(prm), int(cd),
                                       ctypes.byref(out), est, _stream_ptr(stream)))
     return out.value, dict(zip(candidates, list(est)))
+
+
+def solve_memo(A, b, x, s: int, prm: Params, cd: bool = False, stream=None, allow_no_conv: bool = False):
+    """kpp_solve_memo: K++ (cd=False) or CD++ with the online block memoisation; returns (report,
+    number of memoised blocks)."""
+    rep = Report()
+    nb = ctypes.c_int64()
+    m = matrix(A)
+    rc = load().kpp_solve_memo(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), int(s),
+                               int(cd), ctypes.byref(prm), ctypes.byref(rep), ctypes.byref(nb), _stream_ptr(stream))
+    return _report_or_raise(rc, rep, allow_no_conv), int(nb.value)
 
 
 def cg(A, b, x, tol: float = 1e-8, max_iters: int = 100000, stream=None, allow_no_conv: bool = False) -> Report:
