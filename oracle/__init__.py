@@ -132,6 +132,10 @@ def _load():
             lib.orc_proj_precond.restype = ctypes.c_int
             lib.orc_proj_lsqr.argtypes = [ctypes.c_int64, dp, ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_int, dp]
             lib.orc_proj_lsqr.restype = ctypes.c_int
+            lib.orc_run_lsqr.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, dp, ctypes.c_int,
+                                         ctypes.POINTER(_Params), ctypes.POINTER(_State), dp, dp,
+                                         ctypes.POINTER(_Report)]
+            lib.orc_run_lsqr.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -443,3 +447,39 @@ def proj_lsqr(AS: np.ndarray, r: np.ndarray, lam: float, L: np.ndarray, t_max: i
     w = np.empty(n)
     it = _load().orc_proj_lsqr(n, _dp(AS), s, _dp(_f64(r)), lam, _dp(_f64(L)), int(t_max), _dp(w))
     return w, int(it)
+
+
+
+def lsqr_factors(A: np.ndarray, s: int, lam: float, T, d) -> np.ndarray:
+    """The sketch preconditioner of every block of the contiguous partition (proj_precond per block),
+    stacked as nb x s x s (block j: len x len, leading dimension len, as the exact factors)."""
+    A = _f64(A)
+    rows = A.shape[0]
+    nb = -(-rows // s)
+    L = np.zeros((nb, s, s))
+    for j in range(nb):
+        ln = min(s, rows - j * s)
+        Lj = proj_precond(A[j * s:j * s + ln], lam, T, d)
+        L[j].reshape(-1)[:ln * ln] = Lj.reshape(-1)
+    return L
+
+
+def run_lsqr(A: np.ndarray, b: np.ndarray, Lsk: np.ndarray, s: int, t_max: int, *, lam: float = 0.0,
+             tol: float = 1e-8, max_iters: int = 100000, seed: int = 0, sys: int = 0, adaptive: bool = True,
+             eta: float | None = None, confirm: bool = True) -> Result:
+    """K++ from x0 = 0 with the block step's projection computed by t_max iterations of
+    sketch-preconditioned LSQR (Sec. 4.1; orc_run_lsqr); Lsk from lsqr_factors."""
+    lib = _load()
+    A, b = _f64(A), _f64(b)
+    rows, n = A.shape
+    x, mom = np.zeros(n), np.zeros(n)
+    cst = _State(0, 0, 0.0, 0.0, 0.0, 0.0)
+    p = _Params(s=s, cd=0, lam=lam, tol=tol, max_iters=max_iters, seed=seed, sys=sys, adaptive=int(adaptive),
+                eta=default_eta(rows, n, s) if eta is None else eta, confirm=int(confirm))
+    rep = _Report()
+    rc = lib.orc_run_lsqr(rows, n, _dp(A), _dp(b), _dp(_f64(Lsk)), int(t_max), ctypes.byref(p), ctypes.byref(cst),
+                          _dp(x), _dp(mom), ctypes.byref(rep))
+    if rc == 3:  # ORC_BAD_ARG
+        raise ValueError("orc_run_lsqr: bad argument")
+    st = State(cst.t, cst.ci, cst.E0, cst.E1, cst.rhat, cst.rho)
+    return Result(x, mom, st, rep.iters, rep.rel_res_true, rep.rel_res_est, rep.status, np.zeros((0, 5)))

@@ -883,3 +883,71 @@ int orc_proj_lsqr(int64_t n, const double *AS, int s, const double *r, double la
     free(x);
     return it;
 }
+
+/* K++ with the inexact projection of Sec. 4.1: as orc_run (the block draw, the momentum update of
+ * Alg. 1, the window sums, checkpoints, stop rule and adaptive rho of Alg. 3), with the block step's
+ * w = A_S^T (A_S A_S^T + lam I)^{-1} r replaced by t_max iterations of sketch-preconditioned LSQR on
+ * min |A_S w - r|^2 + lam |w|^2 (orc_proj_lsqr).  Lsk: the preconditioners from orc_proj_precond, block
+ * j at Lsk + j s s (len x len, leading dimension len).  K++ only. */
+int orc_run_lsqr(int64_t rows, int64_t n, const double *A, const double *b, const double *Lsk, int t_max,
+                 const orc_params *p, orc_state *st, double *x, double *mom, orc_report *rep) {
+    if (p->s <= 0 || rows <= 0 || n <= 0 || p->cd || t_max < 1) return ORC_BAD_ARG;
+    const int s = p->s;
+    const int64_t nb = nblocks(rows, s), zeta = nb;
+    const double bn2 = dot(rows, b, b);
+    double *r = (double *)malloc(sizeof(double) * (size_t)s);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    const int64_t it0 = st->t;
+    int status = ORC_NO_CONVERGENCE;
+    rep->rel_res_est = NAN;
+    while (st->t < p->max_iters) {
+        const int64_t t = st->t;
+        const int64_t j = orc_sample_block(p->seed, t, p->sys, (int32_t)nb);
+        const int len = block_len(rows, s, j);
+        const double *AS = A + (size_t)j * s * n;
+        double rn2 = 0.0;
+        for (int a = 0; a < len; ++a) {
+            r[a] = dot(n, AS + (size_t)a * n, x) - b[j * s + a];
+            rn2 += r[a] * r[a];
+        }
+        orc_proj_lsqr(n, AS, len, r, p->lam, Lsk + (size_t)j * s * s, t_max, w);
+        const double beta = (1.0 - st->rho) / (1.0 + st->rho);
+        for (int64_t k = 0; k < n; ++k) {
+            mom[k] = beta * (mom[k] - w[k]);
+            x[k] = x[k] - w[k] + p->eta * mom[k];
+        }
+        st->t = t + 1;
+        if ((t % (2 * zeta)) < zeta) st->E0 += rn2; else st->E1 += rn2;
+        if ((t % (2 * zeta)) == 2 * zeta - 1) {
+            st->ci += 1;
+            rep->rel_res_est = bn2 > 0.0 ? sqrt(st->E1 / bn2) : sqrt(st->E1);
+            if (p->tol > 0.0 && st->E1 <= p->tol * p->tol * bn2 &&
+                (!p->confirm || orc_rel_residual(rows, n, A, b, x) <= p->tol)) {
+                status = ORC_OK;
+                break;
+            }
+            if (p->adaptive) {
+                const double q = st->E0 > 0.0 ? st->E1 / st->E0 : 0.0;
+                if (st->ci == 1) {
+                    st->rhat = q;
+                } else {
+                    const double li = log((double)st->ci), li1 = log((double)st->ci + 1.0);
+                    const double wgt = exp(li * li - li1 * li1);
+                    st->rhat = wgt * st->rhat + (1.0 - wgt) * q;
+                }
+                double rho = 1.0 - pow(st->rhat, 1.0 / (double)zeta);
+                if (!(rho > 0.0)) rho = 0.0;
+                if (rho > 1.0 - 1e-12) rho = 1.0 - 1e-12;
+                st->rho = rho;
+            }
+            st->E0 = 0.0;
+            st->E1 = 0.0;
+        }
+    }
+    rep->iters = st->t - it0;
+    rep->rel_res_true = orc_rel_residual(rows, n, A, b, x);
+    rep->status = status;
+    free(r);
+    free(w);
+    return status;
+}

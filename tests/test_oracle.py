@@ -852,3 +852,38 @@ def test_proj_preconditioned_condition_number_shrinks_with_the_sketch():
           for tau in (s, 2 * s, 8 * s)}
     assert ks[8 * s] < ks[s]
     assert ks[2 * s] <= 10.0
+
+
+def test_run_lsqr_with_converged_projections_is_the_exact_kpp_run():
+    """K++ with the inexact projection (Sec. 4.1) and enough LSQR iterations for the projection to reach
+    rounding level (3 s, see the test above) follows the exact K++ run (Alg. 1 with Cholesky
+    projections) step for step: same block draws, same momentum and windows."""
+    rng = np.random.default_rng(21)
+    m, n, s, lam = 120, 40, 12, 0.05
+    A = rng.standard_normal((m, n)) @ np.diag(np.geomspace(1, 20, n))
+    b = A @ rng.standard_normal(n)
+    T = np.sort(rng.choice(64, 2 * s, replace=False))
+    d = W.rademacher_signs(64, 3)
+    Lsk = oracle.lsqr_factors(A, s, lam, T, d)
+    Lex = oracle.kpp_factor(A, s, lam)
+    for steps in (1, 7, 43):
+        ri = oracle.run_lsqr(A, b, Lsk, s, 3 * s, lam=lam, tol=0.0, max_iters=steps, seed=2)
+        re = oracle.run(A, b, Lex, s, lam=lam, tol=0.0, max_iters=steps, seed=2)
+        assert ri.iters == re.iters == steps
+        np.testing.assert_allclose(ri.x, re.x, rtol=1e-9, atol=1e-12 * np.abs(re.x).max())
+
+
+def test_run_lsqr_with_eight_iterations_converges():
+    """The supplement's setting (tau = 2 s, t_max = 8): the inexact-projection K++ still reaches 1e-8 on a
+    consistent system, confirmed by the true residual, in a number of steps close to the exact run's."""
+    rng = np.random.default_rng(22)
+    m, n, s, lam = 400, 60, 20, 1e-3
+    A = rng.standard_normal((m, n)) @ np.diag(np.geomspace(1, 30, n))
+    b = A @ rng.standard_normal(n)
+    T = np.sort(rng.choice(64, 2 * s, replace=False))
+    Lsk = oracle.lsqr_factors(A, s, lam, T, W.rademacher_signs(64, 5))
+    ri = oracle.run_lsqr(A, b, Lsk, s, 8, lam=lam, tol=1e-8, max_iters=200000, seed=4)
+    re = oracle.run(A, b, oracle.kpp_factor(A, s, lam), s, lam=lam, tol=1e-8, max_iters=200000, seed=4)
+    assert ri.status == oracle.OK and re.status == oracle.OK
+    assert ri.rel_res_true <= 1e-8
+    assert ri.iters <= 3 * re.iters
