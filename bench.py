@@ -504,6 +504,99 @@ class MemoSPD(SingleFP64):
                           f"thread, new blocks factored as drawn ({dt:.1f} s)"}
 
 
+class LsqrLS(Workload):
+    """K++ with the inexact projection of Sec. 4.1 (sketch-preconditioned LSQR, tau = 2 s, t_max = 8) on
+    large blocks of an FP64 least-squares system: the sketch preconditioners of every block, then the
+    solve to 1e-8.  After the timed steps the exact K++ (Cholesky projections) solves the same system
+    once, for comparison."""
+    dtype = "f64"
+
+    def __init__(self, m=65536, n=2048, s=512, t_max=8):
+        self.m, self.n, self.s, self.t_max = m, n, s, t_max
+        self.name = "kpp-lsqr"
+        self.kernel = "lsqr_kernel"
+        self.lam, self.tol = 1e-3, 1e-8
+        self.desc = (f"K++ FP64 with the inexact projection (sketch-preconditioned LSQR, Sec. 4.1): {m}x{n} LS "
+                     "A=Z D V^T (Z~N(0,1/m), V Haar, 100 outliers log-spaced 10..1000 + U[0.5,1]) stored FP32 and "
+                     f"widened, b = A x*, s={s} contiguous, SRHT sketch tau=2s, t_max={t_max}, lambda=1e-3, "
+                     "tol 1e-8 on the FP64 residual, x0=0")
+
+    def setup(self, kpp, torch, rank):
+        self.kpp, self.torch = kpp, torch
+        A32, self.b, self.x_star, _ = W.torch_lowrank_ls(self.m, self.n, 100, 10.0, 1000.0, 0.5, 1.0,
+                                                        seed=7 + 1000 * rank, dtype="f32")
+        self.A = A32.double()
+        del A32
+        self.x = torch.zeros(self.n, dtype=torch.float64, device="cuda")
+        self.P = kpp.Partition(self.m, self.s)
+        np2 = 1 << (self.n - 1).bit_length()
+        rng = np.random.default_rng(11 + rank)
+        self.T = np.sort(rng.choice(np2, 2 * self.s, replace=False))
+        self.d = torch.as_tensor(W.rademacher_signs(np2, 12 + rank), device="cuda")
+        self.prm = kpp.params(lam=self.lam, tol=self.tol, seed=0, sys_id=rank)
+
+    def step(self):
+        kpp = self.kpp
+        self.x.zero_()
+        F = kpp.LsqrFactors(self.A, self.P, self.lam, self.T, self.d)
+        rep = kpp.solve_lsqr(self.A, self.b, self.x, self.P, F, self.t_max, self.prm)
+        del F
+        return {"units": rep.iters, "ok": rep.status == kpp.OK and rep.rel_res_true <= self.tol,
+                "kernel_ms": rep.kernel_ms, "kernel_launches": rep.launches, "iters": rep.iters,
+                "outer": 0, "rel_res": rep.rel_res_true}
+
+    def per_iter_bytes(self):
+        """The method's bytes of one step: A_S once, L_j^{-1} twice per LSQR iteration, the n-vectors."""
+        s, n = self.s, self.n
+        return 8 * (s * n + 2 * self.t_max * s * s + 6 * n)
+
+    def roofline(self, steps, peaks):
+        iters = statistics.mean(st["iters"] for st in steps)
+        kms = statistics.mean(st["kernel_ms"] for st in steps)
+        byts = self.per_iter_bytes()
+        return _hbm_roof(self.kernel, iters * byts, kms, peaks, f"{self.kernel}/{self.name}", {"bytes": byts},
+                         {"note": "one launch per solve; A_S stays in L2 for the 2 t_max + 2 products of a step, "
+                                  "which are counted once; the step is bound by its group barriers "
+                                  "(5 per LSQR iteration)"})
+
+    def extra(self, steps):
+        kpp, torch = self.kpp, self.torch
+        x = torch.zeros(self.n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F = kpp.Factors(self.A, self.P, self.lam, 0)
+        rep = kpp.kpp_solve(self.A, self.b, x, self.P, F, kpp.params(lam=self.lam, tol=self.tol, seed=0))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        stages = F.stage_ms()
+        del F
+        return {"exact_kpp_reference": {"what": "K++ with exact Cholesky projections (kpp_factor_blocks + "
+                                                "kpp_solve) on the same system, one run after the timed steps",
+                                        "time_to_tol_ms": 1e3 * dt, "iters": rep.iters,
+                                        "rel_res_true": rep.rel_res_true, "factor_stages_ms": stages,
+                                        "solve_kernel_ms": rep.kernel_ms}}
+
+    def cpu_baseline(self, budget_s):
+        import oracle
+        rows = 8 * self.s
+        A = self.A[:rows].cpu().numpy()
+        b = self.b[:rows].cpu().numpy()
+        d = self.d.cpu().numpy()
+        Lsk = oracle.lsqr_factors(A, self.s, self.lam, self.T, d)
+        k = 16
+        while True:
+            t0 = time.perf_counter()
+            oracle.run_lsqr(A, b, Lsk, self.s, self.t_max, lam=self.lam, tol=0.0, max_iters=k, seed=0)
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 4 or k >= 1 << 16:
+                break
+            k *= 4
+        return {"value": k / dt, "unit": self.unit, "cores": 1, "kind": "oracle",
+                "sample": f"{k} steps of the oracle's inexact-projection K++ (oracle.run_lsqr, t_max={self.t_max}) "
+                          f"on the first {rows} rows of the same matrix, one host thread (preconditioners "
+                          f"excluded; {dt:.1f} s)"}
+
+
 class MixedSPD(SingleFP64):
     """The cdpp4096 system stored FP32 / BF16 with FP32 iterations and FP64 refinement."""
 
@@ -1061,6 +1154,8 @@ def make_workload(args):
         return Serving(n_req=args.requests)
     if args.workload == "cdpp4096-rht":
         return RhtSPD()
+    if args.workload == "kpp-lsqr":
+        return LsqrLS()
     if args.workload == "cdpp4096-memo":
         return MemoSPD()
     if args.workload in ("cdpp4096-f32", "cdpp4096-bf16"):
@@ -1137,7 +1232,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed262144",
                     choices=["cdpp4096", "kpp2000", "mixed262144", "batched64", "serving", "cdpp4096-f32",
-                             "cdpp4096-bf16", "cdpp4096-rht", "cdpp4096-memo"])
+                             "cdpp4096-bf16", "cdpp4096-rht", "cdpp4096-memo", "kpp-lsqr"])
     ap.add_argument("--storage", default="bf16", choices=["bf16", "f32"], help="mixed262144 storage type")
     ap.add_argument("--noisy", action="store_true", help="mixed262144: b = A x* + 1e-6 N(0,I)")
     ap.add_argument("--mixed-rows", type=int, default=262144,

@@ -364,6 +364,40 @@ kpp_status kpp_memo_sequence(uint64_t seed, uint32_t sys_id, int32_t mode, int64
                              int64_t t0, int64_t count, int64_t nb0, int64_t *blocks, int64_t *subsets,
                              int64_t subsets_cap, int64_t *nb_out);
 
+/* The inexact block projection of Sec. 4.1 ("Computing the projection step"; the supplement's Proj
+ * algorithm): K++ on large blocks without an exact factor of A_S A_S^T.  The projection's
+ * w = argmin |A_S w - r|^2 + lambda |w|^2 is taken from t_max iterations of LSQR (Paige and Saunders)
+ * on M [w; v] = L^{-1} r, M = L^{-1} [A_S, sqrt(lambda) I], preconditioned by L L^T = Ahat Ahat^T +
+ * lambda I with the subsampled randomized Hadamard sketch Ahat = (A_S D H_{n'})[:, T] / sqrt(tau):
+ * n' = the smallest power of 2 >= cols (A_S padded with zero columns), H_{n'} the Sylvester Hadamard
+ * matrix, D = diag(d).  FP64 only.
+ *
+ * kpp_factor_lsqr: the preconditioner of every block of P (whole blocks: rows a multiple of s,
+ * 1 <= s <= 1024), memoised as a factor set (kpp_factors_get_block returns L_j).  A: device FP64,
+ * rows x cols with n' <= 16384.  tau: 1 .. n' (the paper takes 2 s).  T (host, tau entries): the
+ * sampled columns, in [0, n').  d (device, n' entries): the signs (entries beyond cols are unused).
+ * *out: the factor set, or NULL on error; it is not accepted by kpp_solve or cdpp_solve.  Errors:
+ * KPP_ERR_ARG; KPP_ERR_NOT_SPD (kpp_factors_bad_block; the handle is returned); KPP_ERR_OOM;
+ * KPP_ERR_CUDA.  Synchronises `stream`. */
+kpp_status kpp_factor_lsqr(const kpp_matrix *A, kpp_partition_t P, double lambda, int64_t tau, const int64_t *T,
+                           const double *d, kpp_factors_t *out, void *stream);
+
+/* One inexact projection: w (device, cols) from t_max LSQR iterations for block j and the residual r
+ * (device, s entries), from zero.  F from kpp_factor_lsqr on A and P.  Errors: KPP_ERR_ARG; KPP_ERR_CUDA;
+ * KPP_ERR_TIMEOUT.  Synchronises `stream`. */
+kpp_status kpp_proj_lsqr(const kpp_matrix *A, kpp_partition_t P, kpp_factors_t F, int64_t j, const double *r,
+                         int32_t t_max, double *w, void *stream);
+
+/* K++ with the inexact projection: Alg. 1's step with w from t_max LSQR iterations (above) in place of
+ * the exact projection.  The block draw, the momentum, the windows of the residual estimate, the
+ * adaptive rho and the stop rule (Eq. 5.2 - 5.3, confirmed by the FP64 residual) are those of
+ * kpp_solve.  A (device FP64), b (rows) and x (cols; in: x0, out: the result) on the device; F from
+ * kpp_factor_lsqr with p->lambda.  p: lambda, tol, max_iters, seed, sys_id, eta, rho0, adaptive_rho.
+ * rep (may be NULL) as for kpp_solve.  Errors: KPP_ERR_ARG; KPP_ERR_NO_CONVERGENCE (x holds the last
+ * iterate); KPP_ERR_NUMERIC; KPP_ERR_TIMEOUT; KPP_ERR_CUDA.  Synchronises `stream`. */
+kpp_status kpp_solve_lsqr(const kpp_matrix *A, const double *b, double *x, kpp_partition_t P, kpp_factors_t F,
+                          int32_t t_max, const kpp_params *p, kpp_report *rep, void *stream);
+
 /* Select the solve kernel for later calls in this process.  All variants compute the same iteration.
  *   3 (default): CD++ uses the dataflow kernel (no per-step barrier: the owners of the next block
  *     hand r over through a tagged mailbox; FP64 streams the memoised W_j = G_j^{-1} A_{S_j}); K++ uses

@@ -58,6 +58,8 @@ void FactorSet::release() {
     W32 = nullptr;
     dev_free(W);
     W = nullptr;
+    dev_free(Linv);
+    Linv = nullptr;
     L = nullptr;
     Ginv = nullptr;
     Ginv32 = nullptr;

@@ -509,10 +509,12 @@ int block_gram(const kpp_matrix &A, int s, double lam, double *G, int engine, cu
 }
 
 // FP64 Cholesky factors and inverses of nblk Grams given in G (block i: s x s, row-major, packed), for
-// blocks formed elsewhere (the online memo's new subsets).  G is factored in place; Ginv receives
-// G_i^{-1} (nblk x s x s).  A block with a non-positive pivot sets *bad_block to its index (the smallest
+// blocks formed elsewhere (the online memo's new subsets, the LSQR sketch preconditioners).  G is
+// factored in place; Ginv receives G_i^{-1} (nblk x s x s); L_out and Linv_out, when given, keep the
+// lower factors L_i and their inverses L_i^{-1} (lower, zero above the diagonal).  A block with a non-positive pivot sets *bad_block to its index (the smallest
 // such) and the call returns KPP_ERR_NOT_SPD.
-kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *bad_block, cudaStream_t st) {
+kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *bad_block, cudaStream_t st,
+                        double *L_out, double *Linv_out) {
     *bad_block = -1;
     if (nblk <= 0) return KPP_OK;
     const int64_t rows = nblk * s;
@@ -524,8 +526,10 @@ kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *b
     int hb = big;
     const size_t chol_smem = CHOL_PB * s * sizeof(double);
     const int sm64 = 4 * IT * ITP * (int)sizeof(double);
-    if (dev_malloc_async((void **)&L, nblk * blk * sizeof(double), st) != cudaSuccess ||
-        dev_malloc_async((void **)&Linv, nblk * blk * sizeof(double), st) != cudaSuccess ||
+    L = L_out;
+    Linv = Linv_out;
+    if ((!L && dev_malloc_async((void **)&L, nblk * blk * sizeof(double), st) != cudaSuccess) ||
+        (!Linv && dev_malloc_async((void **)&Linv, nblk * blk * sizeof(double), st) != cudaSuccess) ||
         dev_malloc_async((void **)&bad, sizeof(int), st) != cudaSuccess) {
         rc = KPP_ERR_OOM;
         set_error("factor_grams: out of device memory for %lld blocks", (long long)nblk);
@@ -551,8 +555,8 @@ kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *b
             rc = KPP_ERR_NOT_SPD;
         }
     }
-    if (L) cudaFreeAsync(L, st);
-    if (Linv) cudaFreeAsync(Linv, st);
+    if (L && L != L_out) cudaFreeAsync(L, st);
+    if (Linv && Linv != Linv_out) cudaFreeAsync(Linv, st);
     if (bad) cudaFreeAsync(bad, st);
     return rc;
 }

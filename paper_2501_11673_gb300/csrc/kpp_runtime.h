@@ -16,7 +16,7 @@ void clear_error();
 struct FactorSet {
     int64_t nb = 0, rows = 0;
     int s = 0;
-    int mode = 0;        // 0: K++ block Gram, 1: CD++ principal block
+    int mode = 0;        // 0: K++ block Gram, 1: CD++ principal block, 2: LSQR sketch preconditioner
     int dtype = 0;       // storage dtype of the matrix the factors came from
     double lambda = 0.0;
     int64_t bad_block = -1;
@@ -26,6 +26,7 @@ struct FactorSet {
     double *W = nullptr;      // CD++ FP64 only: rows x cols, block j rows = G_j^{-1} A_{S_j} (row-major, ld cols)
     float *W32 = nullptr;     // K++ with FP32/BF16 storage, large-block kernel only: G_j^{-1} A_{S_j} in FP32
     int64_t memo_cols = 0;    // columns of W / W32 (the matrix's columns)
+    double *Linv = nullptr;   // mode 2 (sketch preconditioners of the LSQR projection): nb x s x s L_j^{-1}
     // Device time of the factor phase's stages (kpp_factors_stage_ms): events recorded on the stream
     // before the Grams / principal blocks, then after the Cholesky, the inverses and the W memo.
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -35,7 +36,8 @@ struct FactorSet {
 kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, FactorSet &F, cudaStream_t st);
 // FP64 Cholesky and inverse of nblk packed s x s Grams (G factored in place, G^{-1} into Ginv); the
 // smallest block with a non-positive pivot goes to *bad_block and the call returns KPP_ERR_NOT_SPD.
-kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *bad_block, cudaStream_t st);
+kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *bad_block, cudaStream_t st,
+                        double *L_out = nullptr, double *Linv_out = nullptr);  // optional: keep L and L^{-1}
 
 // Tensor-core block Gram for FP32/BF16 storage (kpp_gram_tc.cu).  Writes G (nb x s x s, FP64,
 // block j packed with leading dimension len) and returns true, or returns false when the shape is

@@ -37,7 +37,7 @@ EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_par
            "kpp_plan_destroy", "kpp_tune_cache_size", "kpp_tune_cache_clear", "kpp_tune_cache_save",
            "kpp_tune_cache_load", "kpp_launch_count", "kpp_device_alloc_count", "kpp_device_cache_bytes", "kpp_device_cache_trim", "kpp_build_info", "kpp_rht_forward", "kpp_rht_inverse",
            "kpp_memo_sequence", "kpp_state_create", "kpp_state_destroy", "kpp_state_step",
-           "kpp_state_bytes", "kpp_state_save", "kpp_state_load", "kpp_solve_resume", "cdpp_solve_resume", "kpp_cg", "kpp_gmres", "kpp_tune_block_size", "kpp_solve_memo"]
+           "kpp_state_bytes", "kpp_state_save", "kpp_state_load", "kpp_solve_resume", "cdpp_solve_resume", "kpp_cg", "kpp_gmres", "kpp_tune_block_size", "kpp_solve_memo", "kpp_factor_lsqr", "kpp_proj_lsqr", "kpp_solve_lsqr"]
 GRID_TUNE = -1  # Params.grid: let the launch autotuner choose the CTAs per system
 
 
@@ -167,6 +167,14 @@ def load(path: str | None = None):
         lib.kpp_solve_memo.argtypes = [ctypes.POINTER(Matrix), vp, vp, i32, i32, ctypes.POINTER(Params),
                                        ctypes.POINTER(Report), ctypes.POINTER(i64), vp]
         lib.kpp_solve_memo.restype = ctypes.c_int
+        lib.kpp_factor_lsqr.argtypes = [ctypes.POINTER(Matrix), vp, dbl, i64, ctypes.POINTER(i64), vp,
+                                        ctypes.POINTER(vp), vp]
+        lib.kpp_factor_lsqr.restype = ctypes.c_int
+        lib.kpp_proj_lsqr.argtypes = [ctypes.POINTER(Matrix), vp, vp, i64, vp, i32, vp, vp]
+        lib.kpp_proj_lsqr.restype = ctypes.c_int
+        lib.kpp_solve_lsqr.argtypes = [ctypes.POINTER(Matrix), vp, vp, vp, vp, i32, ctypes.POINTER(Params),
+                                       ctypes.POINTER(Report), vp]
+        lib.kpp_solve_lsqr.restype = ctypes.c_int
         lib.kpp_cg.argtypes = [ctypes.POINTER(Matrix), vp, vp, dbl, i64, ctypes.POINTER(Report), vp]
         lib.kpp_cg.restype = ctypes.c_int
         lib.kpp_gmres.argtypes = [ctypes.POINTER(Matrix), vp, vp, i32, dbl, i64, ctypes.POINTER(Report), vp]
@@ -393,6 +401,44 @@ def solve_memo(A, b, x, s: int, prm: Params, cd: bool = False, stream=None, allo
     rc = load().kpp_solve_memo(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), int(s),
                                int(cd), ctypes.byref(prm), ctypes.byref(rep), ctypes.byref(nb), _stream_ptr(stream))
     return _report_or_raise(rc, rep, allow_no_conv), int(nb.value)
+
+
+class LsqrFactors(Factors):
+    """Sketch preconditioners of the LSQR projection for every block (kpp_factor_lsqr): tau sampled
+    columns T (host integers in [0, n')) of the Hadamard transform, signs d (device, n' values)."""
+
+    def __init__(self, A, P: Partition, lam: float, T, d, stream=None, allow_not_spd: bool = False):
+        import numpy as np
+        self._lib = load()
+        self._A, self._d = A, d
+        Tv = np.ascontiguousarray(T, dtype=np.int64)
+        h = ctypes.c_void_p()
+        m = matrix(A)
+        rc = self._lib.kpp_factor_lsqr(ctypes.byref(m), P.handle, float(lam), int(len(Tv)),
+                                       Tv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.c_void_p(d.data_ptr()),
+                                       ctypes.byref(h), _stream_ptr(stream))
+        self.handle = h if h.value else None
+        self.status = rc
+        _check(rc, allow=(ERR_NOT_SPD,) if allow_not_spd else ())
+        self.lam, self.mode, self.P = lam, 2, P
+
+
+def proj_lsqr(A, P: Partition, F: LsqrFactors, j: int, r, t_max: int, w, stream=None) -> None:
+    """kpp_proj_lsqr: w (device, cols) from t_max LSQR iterations for block j and residual r (device, s)."""
+    m = matrix(A)
+    _check(load().kpp_proj_lsqr(ctypes.byref(m), P.handle, F.handle, int(j), ctypes.c_void_p(r.data_ptr()),
+                                int(t_max), ctypes.c_void_p(w.data_ptr()), _stream_ptr(stream)))
+
+
+def solve_lsqr(A, b, x, P: Partition, F: LsqrFactors, t_max: int, prm: Params, stream=None,
+               allow_no_conv: bool = False) -> Report:
+    """kpp_solve_lsqr: K++ with the sketch-preconditioned LSQR projection; x holds x0 and the result."""
+    rep = Report()
+    m = matrix(A)
+    rc = load().kpp_solve_lsqr(ctypes.byref(m), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                               P.handle, F.handle, int(t_max), ctypes.byref(prm), ctypes.byref(rep),
+                               _stream_ptr(stream))
+    return _report_or_raise(rc, rep, allow_no_conv)
 
 
 def cg(A, b, x, tol: float = 1e-8, max_iters: int = 100000, stream=None, allow_no_conv: bool = False) -> Report:
