@@ -60,6 +60,8 @@ void FactorSet::release() {
     W = nullptr;
     dev_free(Linv);
     Linv = nullptr;
+    dev_free(LinvT);
+    LinvT = nullptr;
     L = nullptr;
     Ginv = nullptr;
     Ginv32 = nullptr;

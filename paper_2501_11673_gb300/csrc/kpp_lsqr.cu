@@ -42,7 +42,6 @@ constexpr int LT = 256;             // threads per CTA
 constexpr int LW = LT / 32;
 constexpr int LSQR_SMAX = 1024;     // block size at most (s-vectors in shared memory)
 constexpr int64_t SKETCH_NMAX = 16384;  // padded row length at most (one row in shared memory)
-constexpr int LRB = 8;              // rows a warp handles at a time in a product with A_S
 
 // Ahat[row][q] = (A[row] * d, padded to np2, times H_np2)[T[q]] / sqrt(tau).  One CTA per row; the
 // transform runs in shared memory, stage by stage from the widest butterfly down (Sylvester order).
@@ -70,6 +69,28 @@ __global__ void __launch_bounds__(256) sketch_kernel(const double *__restrict__ 
     }
 }
 
+// B_j = A_j^T for nb blocks of s x s (one CTA per block at a time, 32 x 32 tiles through shared memory).
+__global__ void transpose_blocks_kernel(const double *__restrict__ A, double *__restrict__ B, int64_t nb, int s) {
+    __shared__ double tile[32][33];
+    const int ntile = (s + 31) / 32;
+    for (int64_t j = blockIdx.x; j < nb; j += gridDim.x) {
+        const double *Aj = A + (size_t)j * s * s;
+        double *Bj = B + (size_t)j * s * s;
+        for (int tr = 0; tr < ntile; ++tr)
+            for (int tc = 0; tc < ntile; ++tc) {
+                for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+                    const int r = tr * 32 + e / 32, c = tc * 32 + e % 32;
+                    tile[e / 32][e % 32] = (r < s && c < s) ? Aj[(size_t)r * s + c] : 0.0;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+                    const int r = tc * 32 + e / 32, c = tr * 32 + e % 32;
+                    if (r < s && c < s) Bj[(size_t)r * s + c] = tile[e % 32][e / 32];
+                }
+                __syncthreads();
+            }
+    }
+}
 
 struct LsqrScalars {  // the stopping rule's state (Alg. 3)
     double E0, E1, rhat, rho, bn2, res_est, res_true;
@@ -83,6 +104,7 @@ struct LsqrArgs {
     const double *b;        // m
     double *x, *mom;        // n
     const double *Linv;     // nb x s x s, L_j^{-1} (lower)
+    const double *LinvT;    // nb x s x s, L_j^{-T} (upper)
     double *part;           // 2 x G x s: partials of a product with A_S over the column chunks
     double *pub;            // 2 x s: a published s-vector
     double *npart;          // 2 x G: partial squared norms
@@ -133,25 +155,17 @@ __global__ void __launch_bounds__(LT, 1) lsqr_kernel(const LsqrArgs a) {
     auto product_AS = [&](const double *As, const double *vsrc, const double *addv, double add_scale,
                           const double *sub, double *out) -> bool {
         double *part = a.part + (size_t)(pc & 1) * G * s;
-        for (int r0 = warp; r0 < s; r0 += LW * LRB) {
-            double v[LRB];
-#pragma unroll
-            for (int k = 0; k < LRB; ++k) v[k] = 0.0;
-            for (int64_t c = c0 + lane; c < c1; c += 32) {
-                const double xc = vsrc[c];
-#pragma unroll
-                for (int k = 0; k < LRB; ++k) {
-                    const int r = r0 + k * LW;
-                    if (r < s) v[k] = fma(As[(size_t)r * a.lda + c], xc, v[k]);
-                }
+        // a thread per row: the row's entries on my columns share a few cache lines, and no shuffles
+        for (int r = threadIdx.x; r < s; r += LT) {
+            const double *row = As + (size_t)r * a.lda;
+            double v0 = 0.0, v1 = 0.0;
+            int64_t c = c0;
+            for (; c + 1 < c1; c += 2) {
+                v0 = fma(row[c], vsrc[c], v0);
+                v1 = fma(row[c + 1], vsrc[c + 1], v1);
             }
-#pragma unroll
-            for (int k = 0; k < LRB; ++k) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-                const int r = r0 + k * LW;
-                if (lane == 0 && r < s) part[(size_t)g * s + r] = v[k];
-            }
+            if (c < c1) v0 = fma(row[c], vsrc[c], v0);
+            part[(size_t)g * s + r] = v0 + v1;
         }
         if (!group_barrier(gs)) return false;
         ++pc;
@@ -174,15 +188,22 @@ __global__ void __launch_bounds__(LT, 1) lsqr_kernel(const LsqrArgs a) {
         return true;
     };
     // out = Lj^{-1} in (trans = false) or Lj^{-T} in (trans = true): entry i by CTA i mod G, published.
+    // (Lj is L_j^{-1} for trans = false and L_j^{-T} for trans = true: a row either way)
     auto product_Linv = [&](const double *Lj, const double *in, double *out, bool trans) -> bool {
         double *pub = a.pub + (size_t)(pc & 1) * s;
         for (int i = g + G * warp; i < s; i += G * LW) {
-            double v = 0.0;
-            if (!trans) {
-                for (int k = lane; k <= i; k += 32) v = fma(Lj[(size_t)i * s + k], in[k], v);
-            } else {
-                for (int k = i + lane; k < s; k += 32) v = fma(Lj[(size_t)k * s + i], in[k], v);
+            const double *row = Lj + (size_t)i * s;
+            const int k0 = trans ? i : 0, k1 = trans ? s : i + 1;  // the nonzero part of the row
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            int k = k0 + lane;
+            for (; k + 96 < k1; k += 128) {
+                v0 = fma(row[k], in[k], v0);
+                v1 = fma(row[k + 32], in[k + 32], v1);
+                v2 = fma(row[k + 64], in[k + 64], v2);
+                v3 = fma(row[k + 96], in[k + 96], v3);
             }
+            for (; k < k1; k += 32) v0 = fma(row[k], in[k], v0);
+            double v = (v0 + v1) + (v2 + v3);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) pub[i] = v;
@@ -226,10 +247,18 @@ __global__ void __launch_bounds__(LT, 1) lsqr_kernel(const LsqrArgs a) {
     auto product_AST = [&](const double *As, const double *z, double *dst, const double *sub, double sub_scale) {
         for (int64_t cb = c0; cb < c1; cb += 32) {
             const int64_t c = cb + lane;
-            double v = 0.0;
-            if (c < c1)
-                for (int r = warp; r < s; r += LW) v = fma(As[(size_t)r * a.lda + c], z[r], v);
-            s_red[warp][lane] = v;
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            if (c < c1) {
+                int r = warp;
+                for (; r + 3 * LW < s; r += 4 * LW) {
+                    v0 = fma(As[(size_t)r * a.lda + c], z[r], v0);
+                    v1 = fma(As[(size_t)(r + LW) * a.lda + c], z[r + LW], v1);
+                    v2 = fma(As[(size_t)(r + 2 * LW) * a.lda + c], z[r + 2 * LW], v2);
+                    v3 = fma(As[(size_t)(r + 3 * LW) * a.lda + c], z[r + 3 * LW], v3);
+                }
+                for (; r < s; r += LW) v0 = fma(As[(size_t)r * a.lda + c], z[r], v0);
+            }
+            s_red[warp][lane] = (v0 + v1) + (v2 + v3);
             __syncthreads();
             if (warp == 0 && c < c1) {
                 double t = 0.0;
@@ -252,6 +281,22 @@ __global__ void __launch_bounds__(LT, 1) lsqr_kernel(const LsqrArgs a) {
         const int64_t j = a.proj_only ? a.proj_j : (int64_t)draw_block(a.seed, t, a.sys, (int32_t)a.nb);
         const double *As = a.A + (size_t)j * s * a.lda;
         const double *Lj = a.Linv + (size_t)j * s * s;
+        const double *LjT = a.LinvT + (size_t)j * s * s;
+        // the next step's block: my columns of its rows and my rows of its L^{-1}, L^{-T} go to L2
+        if (!a.proj_only && q + 1 < steps) {
+            const int64_t jn = draw_block(a.seed, t + 1, a.sys, (int32_t)a.nb);
+            const double *An = a.A + (size_t)jn * s * a.lda;
+            for (int r = warp; r < s; r += LW)
+                for (int64_t c = c0 + lane * 4; c < c1; c += 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(An + (size_t)r * a.lda + c));
+            for (int i = g; i < s; i += G) {
+                const double *l1 = a.Linv + ((size_t)jn * s + i) * s, *l2 = a.LinvT + ((size_t)jn * s + i) * s;
+                for (int k = threadIdx.x * 4; k < s; k += LT * 4) {
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(l1 + k));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(l2 + k));
+                }
+            }
+        }
 
         // ---- r = A_S x - b_S (or the given residual) ----
         double rn2 = 0.0;
@@ -272,7 +317,7 @@ __global__ void __launch_bounds__(LT, 1) lsqr_kernel(const LsqrArgs a) {
             for (int r = threadIdx.x; r < s; r += LT) s_u[r] /= beta;
             __syncthreads();
             // v = M^T u = [A_S^T z; sqrt(lam) z], z = L^{-T} u
-            if (!(ok = product_Linv(Lj, s_u, s_z, true))) break;
+            if (!(ok = product_Linv(LjT, s_u, s_z, true))) break;
             product_AST(As, s_z, vw, nullptr, 0.0);
             for (int r = threadIdx.x; r < s; r += LT) s_vv[r] = sl * s_z[r];
             __syncthreads();
@@ -302,7 +347,7 @@ __global__ void __launch_bounds__(LT, 1) lsqr_kernel(const LsqrArgs a) {
                         __syncthreads();
                     }
                     // M^T u - beta v
-                    if (!(ok = product_Linv(Lj, s_u, s_z, true))) break;
+                    if (!(ok = product_Linv(LjT, s_u, s_z, true))) break;
                     product_AST(As, s_z, vw, vw, beta);  // vw <- A_S^T z - beta vw (my columns)
                     for (int r = threadIdx.x; r < s; r += LT) s_vv[r] = sl * s_z[r] - beta * s_vv[r];
                     __syncthreads();
@@ -500,6 +545,20 @@ extern "C" kpp_status kpp_factor_lsqr(const kpp_matrix *A, kpp_partition_t P, do
             F.bad_block = bad;
             set_error("kpp_factor_lsqr: block %lld: sketched Gram not positive definite", (long long)bad);
         }
+        if (rc == KPP_OK) {
+            if (dev_malloc((void **)&F.LinvT, nb * blk * sizeof(double)) != cudaSuccess) {
+                rc = KPP_ERR_OOM;
+                set_error("kpp_factor_lsqr: out of device memory");
+            } else {
+                note_launch();
+                transpose_blocks_kernel<<<(unsigned)std::min<int64_t>(nb, 4 * (int64_t)sm_count()), 256, 0, st>>>(
+                    F.Linv, F.LinvT, nb, s);
+                if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+                    rc = KPP_ERR_CUDA;
+                    set_error("kpp_factor_lsqr: transpose failed");
+                }
+            }
+        }
     }
     if (dT) cudaFreeAsync(dT, st);
     if (Ahat) cudaFreeAsync(Ahat, st);
@@ -530,6 +589,7 @@ kpp_status lsqr_launch(const kpp_matrix &A, const double *b, double *x, const Fa
     a.b = b;
     a.x = x;
     a.Linv = F.Linv;
+    a.LinvT = F.LinvT;
     a.m = A.rows;
     a.n = n;
     a.nb = F.nb;
@@ -590,6 +650,7 @@ cleanup:
 
 bool lsqr_factors_ok(const kpp_matrix *A, kpp_partition_t P, kpp_factors_t F) {
     return A && A->data && P && F && A->dtype == KPP_F64 && A->ld >= A->cols && F->f.mode == 2 && F->f.Linv &&
+           F->f.LinvT &&
            F->f.rows == A->rows && P->rows == A->rows && P->s == F->f.s && F->f.memo_cols == A->cols &&
            F->f.bad_block < 0;
 }

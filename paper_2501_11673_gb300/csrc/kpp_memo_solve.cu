@@ -45,7 +45,6 @@ namespace {
 constexpr int MT = 256;            // threads per CTA
 constexpr int MW = MT / 32;
 constexpr int MEMO_SMAX = 1024;    // block size at most (r and y in shared memory)
-constexpr int RB = 8;              // rows a warp handles at a time (their loads in flight together)
 
 struct MemoScalars {  // the stopping rule's state (Alg. 3), one system
     double E0, E1, rhat, rho, bn2, res_est, res_true;
@@ -111,27 +110,17 @@ __global__ void __launch_bounds__(MT, 1) memo_kernel(const MemoArgs a) {
         const double *__restrict__ Gj = a.Ginv + (size_t)j * s * s;
         double *part = a.part + (size_t)(t & 1) * a.G * s;
 
-        // a. my partial of r: warp per row (RB rows of a warp at a time, their loads issued together),
-        // lanes over my columns
-        for (int r0 = warp; r0 < s; r0 += MW * RB) {
-            double v[RB];
-#pragma unroll
-            for (int k = 0; k < RB; ++k) v[k] = 0.0;
-            for (int64_t c = c0 + lane; c < c1; c += 32) {
-                const double xc = x[c];
-#pragma unroll
-                for (int k = 0; k < RB; ++k) {
-                    const int r = r0 + k * MW;
-                    if (r < s) v[k] = fma(As[(size_t)r * n + c], xc, v[k]);
-                }
+        // a. my partial of r: a thread per row (the row's entries on my columns share a few cache lines)
+        for (int r = threadIdx.x; r < s; r += MT) {
+            const double *row = As + (size_t)r * n;
+            double v0 = 0.0, v1 = 0.0;
+            int64_t c = c0;
+            for (; c + 1 < c1; c += 2) {
+                v0 = fma(row[c], x[c], v0);
+                v1 = fma(row[c + 1], x[c + 1], v1);
             }
-#pragma unroll
-            for (int k = 0; k < RB; ++k) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-                const int r = r0 + k * MW;
-                if (lane == 0 && r < s) part[(size_t)g * s + r] = v[k];
-            }
+            if (c < c1) v0 = fma(row[c], x[c], v0);
+            part[(size_t)g * s + r] = v0 + v1;
         }
         if (!group_barrier(gs)) break;
 

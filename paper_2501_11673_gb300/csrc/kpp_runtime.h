@@ -27,6 +27,7 @@ struct FactorSet {
     float *W32 = nullptr;     // K++ with FP32/BF16 storage, large-block kernel only: G_j^{-1} A_{S_j} in FP32
     int64_t memo_cols = 0;    // columns of W / W32 (the matrix's columns)
     double *Linv = nullptr;   // mode 2 (sketch preconditioners of the LSQR projection): nb x s x s L_j^{-1}
+    double *LinvT = nullptr;  // mode 2: L_j^{-T} (so that both products read rows)
     // Device time of the factor phase's stages (kpp_factors_stage_ms): events recorded on the stream
     // before the Grams / principal blocks, then after the Cholesky, the inverses and the W memo.
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
