@@ -582,7 +582,9 @@ kpp_status lsqr_launch(const kpp_matrix &A, const double *b, double *x, const Fa
     kpp_status rc = KPP_OK;
     Scratch scr(st);
     const int64_t n = A.cols;
-    const int G = auto_grid(n, 1);
+    // every SM: a step's products with A_S and A_S^T are FP64 FMAs on the columns, and GB300's FP64 pipe
+    // is narrow, so they are spread as widely as the columns allow (at least 8 per CTA)
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(), (n + 7) / 8));
     const int s = F.s;
     a.A = (const double *)A.data;
     a.lda = A.ld;
