@@ -1200,9 +1200,9 @@ def run_reference(args, rank: int):
         what = "FP64 oracle block iterations of the workload"
         dtype = "f64"
     else:
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-system workloads "
-                          "(mixed262144, cdpp4096, kpp2000); the batched and serving workloads report it as "
-                          "cpu_baseline"}), flush=True)
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the fixed-partition single-system "
+                          "workloads (mixed262144, cdpp4096, kpp2000); the memo, LSQR, batched and serving "
+                          "workloads report their oracle as cpu_baseline"}), flush=True)
         return
     v1, _, _ = _oracle_iter_rate(A, b, L, s, cd, lam, seed, 8.0, it0=it0)
     times, iters, cores, model = [], 0, 1, ""
