@@ -82,6 +82,11 @@ FP64_PEAK_SOURCE = ("derived: 152 SMs x 1.68 FP64 FMA lanes/clk/SM (measured by 
                     "pool's GB300) x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)")
 
 
+def fp32_peak_gflops(peaks):
+    """FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x the maximum SM clock."""
+    return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+
+
 def fp64_peak_nominal(peaks):
     return {"peak": fp64_peak_gflops(peaks, FP64_LANES_NOMINAL),
             "source": "nominal: 152 SMs x 2 FP64 FMA/clk x 2 flop x sm_max_mhz"}
@@ -730,7 +735,8 @@ class MixedLS(Workload):
                  if noisy else "b = A_stored x* (noise-free headline)")
         self.desc = (f"K++ mixed precision, {m}x{n} LS A=Z D V^T stored {storage.upper()} (Z~N(0,1/m), V Haar, "
                      f"100 outliers log-spaced 10..1000 + U[0.5,1]), {noise}, s={s}, lambda=1e-3, "
-                     "tensor-core block Grams, FP64 Cholesky, FP32 iterations + FP64 refinement (inner tol 1e-3), "
+                     "tensor-core block Grams, FP32 Cholesky (FP64 for blocks it finds ill-conditioned), "
+                     "FP32 iterations + FP64 refinement (inner tol 1e-3), "
                      "tol 1e-8 on the FP64 residual, x0=0")
 
     def setup(self, kpp, torch, rank):
@@ -749,10 +755,12 @@ class MixedLS(Workload):
         F = kpp.Factors(self.A, self.P, self.lam, 0)
         rep = kpp.kpp_solve(self.A, self.b, self.x, self.P, F, self.prm, allow_no_conv=self.noisy)
         stages = F.stage_ms()
+        fp64_blocks = F.fp64_blocks
         del F
         ok = rep.rel_res_true <= self.tol if not self.noisy else math.isfinite(rep.rel_res_true)
         return {"units": rep.iters, "ok": ok, "kernel_ms": rep.kernel_ms, "kernel_launches": rep.launches,
-                "iters": rep.iters, "outer": rep.outer, "rel_res": rep.rel_res_true, "stages": stages}
+                "iters": rep.iters, "outer": rep.outer, "rel_res": rep.rel_res_true, "stages": stages,
+                "fp64_blocks": fp64_blocks}
 
     def per_iter_bytes(self):
         esz = 2 if self.storage == "bf16" else 4
@@ -783,8 +791,9 @@ class MixedLS(Workload):
         return out
 
     def roofline(self, steps, peaks):
-        """The dominant kernel of the step: the FP64 Cholesky of every block, or the block-step kernel,
-        whichever took more device time (events on the launching stream for both)."""
+        """The dominant kernel of the step: the Cholesky of every block (FP32, with FP64 for the blocks it
+        flags), or the block-step kernel, whichever took more device time (events on the launching stream
+        for both)."""
         st = steps[-1]["stages"]
         chol_ms = statistics.mean(x["stages"]["cholesky"] for x in steps)
         kms = statistics.mean(x["kernel_ms"] for x in steps)
@@ -794,23 +803,23 @@ class MixedLS(Workload):
         nb = -(-self.m // self.s)
         flops = nb * self.s ** 3 / 3.0
         ach = flops / (chol_ms / 1e3) / 1e9
-        pk = fp64_peak_gflops(peaks)
-        nom = fp64_peak_nominal(peaks)
-        return {"kernel": "cholesky_kernel", "bound": "alu", "achieved": ach, "peak": pk, "unit": "GFLOP/s",
-                "frac": ach / pk, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(f"cholesky_kernel/{self.name}"),
+        pk = fp32_peak_gflops(peaks)
+        return {"kernel": "cholesky_f32_kernel", "bound": "alu", "achieved": ach, "peak": pk, "unit": "GFLOP/s",
+                "frac": ach / pk, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(f"cholesky_f32_kernel/{self.name}"),
                 "launch_ms": chol_ms, "per_launch": {"flops": flops, "blocks": nb, "s": self.s,
                                                      "count": "s^3/3 per block (the paper's Cholesky count)"},
-                "launches": "cholesky_kernel over the whole rounds of blocks (one CTA per block, 3 per SM), then "
-                            "cholesky_pair_kernel over the last round (nb mod SMs blocks, a 2-CTA cluster each); "
-                            "the time is the stage's events around both",
-                "peak_source": FP64_PEAK_SOURCE, "nominal_peak": {**nom, "frac": ach / nom["peak"]},
+                "launches": "cholesky_f32_kernel over every block (one CTA per block), then cholesky_kernel "
+                            "(FP64) over the blocks it flagged (the others return at once); the time is the "
+                            "stage's events around both",
+                "fp64_blocks": steps[-1].get("fp64_blocks"),
+                "peak_source": "nominal: 152 SMs x 128 FP32 FMA/clk x 2 flop x sm_max_mhz",
                 "factor_stages_ms": st}
 
     def extra(self, steps):
         x_err = float(((self.x - self.x_star).norm() / self.x_star.norm()).item())
         stages = {k: statistics.mean(x["stages"][k] for x in steps) for k in steps[-1]["stages"]}
         out = {"outer_steps": steps[-1]["outer"], "x_rel_err_vs_x_star": x_err, "factor_stages_ms": stages,
-               "block_step": self._block}
+               "fp64_cholesky_blocks": steps[-1].get("fp64_blocks"), "block_step": self._block}
         if self.noisy:
             out["attained_rel_res"] = steps[-1]["rel_res"]
         if self.run_fp64_reference and not self.noisy:

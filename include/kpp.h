@@ -122,8 +122,9 @@ int64_t kpp_partition_blocks(kpp_partition_t p);
  *   mode 0 (K++):  G_j = A_{S_j} A_{S_j}^T + lambda I  (the block Gram; for F32/BF16 storage it is
  *                  built on the tensor cores with FP32 accumulation, then widened to FP64);
  *   mode 1 (CD++): G_j = A_{S_j S_j} + lambda I  (the principal block; A must be square and symmetric).
- * For every block the library stores the FP64 lower Cholesky factor L_j (G_j = L_j L_j^T) and the
- * inverse G_j^{-1} = L_j^{-T} L_j^{-1} formed from it.  The inverse turns each per-step projection
+ * For every block the library stores the lower Cholesky factor L_j (G_j = L_j L_j^T; held in FP64,
+ * computed in FP32 for F32/BF16 storage unless the block is ill-conditioned, see
+ * kpp_factors_fp64_blocks) and the inverse G_j^{-1} = L_j^{-T} L_j^{-1} formed from it.  The inverse turns each per-step projection
  * into a parallel s x s matrix-vector product instead of two depth-s substitutions.  With F32/BF16
  * storage it also keeps an FP32 copy of G_j^{-1} for the inner solves.
  * A: device matrix, rows x cols (K++), or n x n symmetric (CD++).  Its rows must equal the
@@ -136,6 +137,14 @@ kpp_status kpp_factor_blocks(const kpp_matrix *A, kpp_partition_t P, double lamb
 void kpp_factors_destroy(kpp_factors_t f);
 /* First block whose factorisation failed, or -1. */
 int64_t kpp_factors_bad_block(kpp_factors_t f);
+/* Number of blocks whose Cholesky factor was computed in FP64.  FP64 storage: every block.  FP32/BF16
+ * storage: the Cholesky runs in FP32 (the Gram carries FP32 accuracy and the inner solves use an FP32
+ * inverse), and a block is refactored in FP64 only when the FP32 pass finds it too ill-conditioned
+ * for FP32 elimination: a non-positive or non-finite FP32 pivot, or a ratio of largest to smallest
+ * pivot L_cc^2 (a lower bound on kappa(G_j)) above 2^24 / (s + 1), where the smallest pivot reaches the
+ * FP32 factor's rounding floor.  Below that the FP32 factor's backward error, (s + 1) 2^-24
+ * componentwise, is no larger than the FP32-accumulated Gram's own.  -1 for a null handle. */
+int64_t kpp_factors_fp64_blocks(kpp_factors_t f);
 /* Copy rows row0 .. row0+nrows-1 of the FP32 memo W (block j's rows: W_j = G_j^{-1} A_{S_j}, Sec. 4's
  * projection folded into one operator; rows x cols, row-major) to host memory out_host (nrows * cols
  * floats).  The memo exists for BF16 / FP32 storage where the large-block K++ kernel or the

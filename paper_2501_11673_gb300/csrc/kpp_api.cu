@@ -770,6 +770,7 @@ void kpp_factors_destroy(kpp_factors_t f) {
 }
 
 int64_t kpp_factors_bad_block(kpp_factors_t f) { return f ? f->f.bad_block : -1; }
+int64_t kpp_factors_fp64_blocks(kpp_factors_t f) { return f ? f->f.fp64_blocks : -1; }
 
 kpp_status kpp_factors_get_memo(kpp_factors_t f, int64_t row0, int64_t nrows, float *out_host) {
     clear_error();

@@ -97,8 +97,10 @@ constexpr int CHOL_PB = 8;
 constexpr int CHOL_NT = 512;
 
 __global__ void __launch_bounds__(CHOL_NT) cholesky_kernel(int64_t rows, int s, double *__restrict__ G,
-                                                          double *__restrict__ L, int *__restrict__ bad, int j0) {
+                                                          double *__restrict__ L, int *__restrict__ bad, int j0,
+                                                          const int *__restrict__ only) {
     const int j = j0 + (int)blockIdx.x;  // blocks j0 .. j0 + gridDim.x - 1
+    if (only && !only[j]) return;        // refactoring only the blocks flagged by the FP32 pass
     const int len = (int)min64(s, rows - (int64_t)j * s);
     double *Gj = G + (size_t)j * s * s;
     double *Lj = L + (size_t)j * s * s;
@@ -279,6 +281,185 @@ static cudaError_t launch_cholesky_pairs(int64_t rows, int s, double *G, double 
     note_launch();
     cholesky_pair_kernel<<<(unsigned)(2 * count), CHOL_NT, smem, st>>>(rows, s, G, L, bad, j0);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP32 Cholesky for the mixed-precision forms (FP32/BF16 storage), where G_j itself carries only FP32
+// accuracy (tensor-core Gram, FP32 accumulation) and only the FP32 inverse feeds the inner solves.
+// One CTA per block on an FP32 working copy of G_j's lower triangle (global memory, ld = ws), right-
+// looking with 32-column panels:
+//   (a) the panel's rows are copied, transposed, into shared memory (PT[c][i - jb]);
+//   (b) one warp factors the 32 x 32 diagonal tile in registers (lane a holds row a);
+//   (c) every row below it solves L21 L11^T = P21 by forward substitution (a thread per row);
+//   (d) the panel's columns of L go out widened to FP64, with the zeros right of the diagonal tile;
+//   (e) the trailing lower triangle takes the rank-32 update in 128 x 64 tiles, each thread an 8 x 4
+//       register tile fed by 16-byte shared-memory loads.
+// 256 threads and two CTAs per SM: the serial parts of one block's panel ((b), (c)) and the global
+// read-modify-write of its tiles overlap with the other block's tile products.
+// The pivots L_cc^2 are Schur-complement diagonals, so they lie in [lambda_min(G), lambda_max(G)] and
+// their ratio is a lower bound on kappa(G).  The FP32 factor's backward error is at most (s + 1) 2^-24
+// |L||L^T| componentwise; for a K++ Gram (n >= s columns, FP32 accumulation) that is no more than the
+// Gram's own error, so the FP32 factor loses nothing as long as elimination stays clear of breakdown.
+// A block whose FP32 pivot fails, or whose smallest pivot falls to the FP32 factor's rounding floor
+// (ratio above kappa_max = 2^24 / (s + 1)), is flagged in need64[j] (and counted in *n64): the caller
+// refactors it in FP64 from the untouched G.
+// ---------------------------------------------------------------------------------------------
+constexpr int C32_NT = 256;
+constexpr int C32_TM = 128;  // trailing tile rows (16 row groups of 8)
+constexpr int C32_TN = 64;   // trailing tile columns (16 column groups of 4)
+static __host__ __device__ __forceinline__ int c32_ws(int s) { return (s + 3) & ~3; }
+// PT row length: the trailing tiles read up to 158 entries past the block's last row, and 4 mod 32
+// spreads the transposed accesses over banks while keeping 16-byte alignment.
+static __host__ __device__ __forceinline__ int c32_ldp(int s) { return ((s + 160 + 31) / 32) * 32 + 4; }
+
+__global__ void __launch_bounds__(C32_NT, 2)
+    cholesky_f32_kernel(int64_t rows, int s, const double *__restrict__ G, float *__restrict__ Wk,
+                        double *__restrict__ L, int *__restrict__ need64, int *__restrict__ n64, float kappa_max) {
+    const int j = (int)blockIdx.x;
+    const int len = (int)min64(s, rows - (int64_t)j * s);
+    const int ws = c32_ws(s), ldp = c32_ldp(s);
+    const double *Gj = G + (size_t)j * s * s;
+    float *Wj = Wk + (size_t)j * ws * ws;
+    double *Lj = L + (size_t)j * s * s;
+    extern __shared__ __align__(16) float PT[];  // 32 x ldp
+    __shared__ float sRd[32];
+    __shared__ int s_fail;
+    __shared__ float s_pmin, s_pmax;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = C32_NT / 32;
+    if (tid == 0) {
+        s_fail = 0;
+        s_pmin = INFINITY;
+        s_pmax = 0.f;
+    }
+    for (int e = tid; e < 32 * ldp; e += C32_NT) PT[e] = 0.f;
+    for (int i = warp; i < len; i += nw)
+        for (int k = lane; k <= i; k += 32) Wj[(size_t)i * ws + k] = (float)Gj[(size_t)i * len + k];
+    __syncthreads();
+    for (int jb = 0; jb < len; jb += 32) {
+        const int pw = min(32, len - jb), T = len - jb;
+        // (a)
+        for (int e = tid; e < T * 32; e += C32_NT) {
+            const int i = e >> 5, c = e & 31;
+            PT[c * ldp + i] = (c < pw && c <= i) ? Wj[(size_t)(jb + i) * ws + jb + c] : 0.f;
+        }
+        __syncthreads();
+        // (b)
+        if (warp == 0) {
+            float d[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) d[c] = (lane < pw) ? (c < pw ? PT[c * ldp + lane] : 0.f) : (lane == c ? 1.f : 0.f);
+            bool bad = false;
+            float pmin = INFINITY, pmax = 0.f;
+#pragma unroll 32
+            for (int c = 0; c < 32; ++c) {
+                const float piv = __shfl_sync(0xffffffffu, d[c], c);
+                if (c < pw) {
+                    bad |= !(piv > 0.f) || !isfinite(piv);
+                    pmin = fminf(pmin, piv);
+                    pmax = fmaxf(pmax, piv);
+                }
+                const float l = sqrtf(piv), rl = 1.f / l;
+                if (lane == c) {
+                    d[c] = l;
+                    sRd[c] = rl;
+                } else if (lane > c) {
+                    d[c] *= rl;
+                }
+#pragma unroll 31
+                for (int c2 = c + 1; c2 < 32; ++c2) {
+                    const float lc2 = __shfl_sync(0xffffffffu, d[c], c2);
+                    if (lane >= c2) d[c2] = fmaf(-d[c], lc2, d[c2]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) PT[c * ldp + lane] = (c <= lane) ? d[c] : 0.f;
+            if (lane == 0) {
+                if (bad) s_fail = 1;
+                s_pmin = fminf(s_pmin, pmin);
+                s_pmax = fmaxf(s_pmax, pmax);
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        // (c) rows below the diagonal tile (pw == 32 whenever there are any)
+        for (int i = 32 + tid; i < T; i += C32_NT) {
+            float p[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) p[c] = PT[c * ldp + i];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const float x = p[c] * sRd[c];
+                p[c] = x;
+#pragma unroll
+                for (int c2 = c + 1; c2 < 32; ++c2) p[c2] = fmaf(-PT[c * ldp + c2], x, p[c2]);
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) PT[c * ldp + i] = p[c];
+        }
+        __syncthreads();
+        // (d)
+        for (int e = tid; e < T * 32; e += C32_NT) {
+            const int i = e >> 5, c = e & 31;
+            if (c < pw) Lj[(size_t)(jb + i) * len + jb + c] = (double)PT[c * ldp + i];
+        }
+        const int right = len - jb - pw;
+        for (int e = tid; e < pw * right; e += C32_NT) {
+            const int r = e / right, c = e % right;
+            Lj[(size_t)(jb + r) * len + jb + pw + c] = 0.0;
+        }
+        // (e)
+        const int t0 = jb + 32, Tt = len - t0;
+        const int tr = tid >> 4, tc = tid & 15;
+        for (int ti = 0; ti < Tt; ti += C32_TM) {
+            for (int tk = 0; tk < ti + C32_TM && tk < Tt; tk += C32_TN) {
+                float acc[8][4];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+                const float *pa = PT + 32 + ti + tr * 8;
+                const float *pb = PT + 32 + tk + tc * 4;
+#pragma unroll 8
+                for (int c = 0; c < 32; ++c) {
+                    const float4 a0 = *reinterpret_cast<const float4 *>(pa + c * ldp);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(pa + c * ldp + 4);
+                    const float4 b = *reinterpret_cast<const float4 *>(pb + c * ldp);
+                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+                }
+                const int k0 = t0 + tk + tc * 4;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = t0 + ti + tr * 8 + u;
+                    if (i < len && k0 <= i) {
+                        float *w = Wj + (size_t)i * ws + k0;
+                        if (k0 + 3 <= i) {
+                            float4 x = *reinterpret_cast<float4 *>(w);
+                            x.x -= acc[u][0];
+                            x.y -= acc[u][1];
+                            x.z -= acc[u][2];
+                            x.w -= acc[u][3];
+                            *reinterpret_cast<float4 *>(w) = x;
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                if (k0 + v <= i) w[v] -= acc[u][v];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const bool ill = s_fail || !(s_pmax <= kappa_max * s_pmin);
+        need64[j] = ill ? 1 : 0;
+        if (ill) atomicAdd(n64, 1);
+    }
 }
 
 // G^{-1} = L^{-T} L^{-1} from the FP64 factor, in the arithmetic TI: FP64 for FP64 storage; FP32 for the
@@ -542,7 +723,7 @@ kpp_status factor_grams(double *G, int64_t nblk, int s, double *Ginv, int64_t *b
         rc = KPP_ERR_CUDA;
     if (rc == KPP_OK) {
         note_launch();
-        cholesky_kernel<<<(unsigned)nblk, CHOL_NT, chol_smem, st>>>(rows, s, G, L, bad, 0);
+        cholesky_kernel<<<(unsigned)nblk, CHOL_NT, chol_smem, st>>>(rows, s, G, L, bad, 0, nullptr);
         note_launch();
         inverse_kernel<double><<<(unsigned)nblk, INV_NT, sm64, st>>>(rows, s, L, Linv, Ginv, 0);
         if (cudaGetLastError() != cudaSuccess ||
@@ -573,8 +754,10 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     F.dtype = A.dtype;
     F.bad_block = -1;
     double *G = nullptr, *Linv = nullptr;
-    int *bad = nullptr;
+    float *Wk = nullptr;
+    int *bad = nullptr, *need64 = nullptr;
     kpp_status rc = KPP_OK;
+    F.fp64_blocks = A.dtype == KPP_F64 ? nb : 0;
 #define KPP_TRY(call)                                                        \
     do {                                                                     \
         cudaError_t e_ = (call);                                             \
@@ -611,7 +794,25 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     }
     KPP_TRY(cudaGetLastError());
     KPP_TRY(cudaEventRecord(F.ev[1], st));
-    {
+    if (A.dtype != KPP_F64) {
+        // FP32/BF16 storage: the Cholesky runs in FP32, and only the blocks it flags as ill-conditioned
+        // (or failed) are refactored in FP64 from the untouched G.
+        const int ws = c32_ws(s);
+        const size_t c32_smem = (size_t)32 * c32_ldp(s) * sizeof(float);
+        const size_t chol_smem = CHOL_PB * s * sizeof(double);
+        const float kappa_max = (float)(16777216.0 / (s + 1));  // smallest pivot above (s + 1) 2^-24 x largest
+        KPP_TRY(dev_malloc((void **)&Wk, (size_t)nb * ws * ws * sizeof(float)));
+        KPP_TRY(dev_malloc((void **)&need64, (size_t)(nb + 1) * sizeof(int)));
+        KPP_TRY(cudaMemsetAsync(need64 + nb, 0, sizeof(int), st));
+        KPP_TRY(cudaFuncSetAttribute(cholesky_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c32_smem));
+        note_launch();
+        cholesky_f32_kernel<<<(unsigned)nb, C32_NT, c32_smem, st>>>(rows, s, G, Wk, F.L, need64, need64 + nb, kappa_max);
+        KPP_TRY(cudaGetLastError());
+        KPP_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem));
+        note_launch();
+        cholesky_kernel<<<(unsigned)nb, CHOL_NT, chol_smem, st>>>(rows, s, G, F.L, bad, 0, need64);
+        KPP_TRY(cudaGetLastError());
+    } else {
         // The Cholesky is one CTA per block on the FP64 pipe.  nb blocks over the SMs end in a last
         // round of nb mod SMs blocks, during which the other SMs would idle; when there are few enough,
         // that round runs as its own launch with each block split over a pair of CTAs (a cluster) on
@@ -624,7 +825,7 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
         const size_t chol_smem = CHOL_PB * s * sizeof(double);
         KPP_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem));
         note_launch();
-        cholesky_kernel<<<(unsigned)head, CHOL_NT, chol_smem, st>>>(rows, s, G, F.L, bad, 0);
+        cholesky_kernel<<<(unsigned)head, CHOL_NT, chol_smem, st>>>(rows, s, G, F.L, bad, 0, nullptr);
         KPP_TRY(cudaGetLastError());
         if (pair) KPP_TRY(launch_cholesky_pairs(rows, s, G, F.L, bad, (int)head, (int)tail, st));
     }
@@ -643,9 +844,11 @@ kpp_status factor_blocks_impl(const kpp_matrix &A, int s, double lam, int mode, 
     KPP_TRY(cudaGetLastError());
     KPP_TRY(cudaEventRecord(F.ev[3], st));
     {
-        int hb = 0;
+        int hb = 0, h64 = 0;
         KPP_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (need64) KPP_TRY(cudaMemcpyAsync(&h64, need64 + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
         KPP_TRY(cudaStreamSynchronize(st));
+        if (need64) F.fp64_blocks = h64;
         if (hb != 0x7fffffff) {
             F.bad_block = hb;
             rc = KPP_ERR_NOT_SPD;
@@ -678,6 +881,8 @@ done:
 #undef KPP_TRY
     dev_free(G);
     dev_free(Linv);
+    dev_free(Wk);
+    dev_free(need64);
     dev_free(bad);
     return rc;
 }

@@ -20,6 +20,7 @@ struct FactorSet {
     int dtype = 0;       // storage dtype of the matrix the factors came from
     double lambda = 0.0;
     int64_t bad_block = -1;
+    int64_t fp64_blocks = 0;  // blocks whose Cholesky ran in FP64 (all of them for FP64 storage)
     double *L = nullptr;      // nb x s x s, FP64 lower Cholesky factors (block j: len x len, ld len)
     double *Ginv = nullptr;   // nb x s x s, FP64 (G_j)^{-1}
     float *Ginv32 = nullptr;  // nb x s x s, FP32 copy (FP32/BF16 storage only)

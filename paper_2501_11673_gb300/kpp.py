@@ -29,7 +29,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NUMERIC, ERR_NO_CONVERGENCE, ER
 
 # Every symbol include/kpp.h declares (checked by the CPU test suite against the built library).
 EXPORTS = ["kpp_params_default", "kpp_status_string", "kpp_last_error", "kpp_partition", "kpp_partition_destroy",
-           "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block", "kpp_factors_stage_ms", "kpp_factors_get_memo",
+           "kpp_partition_blocks", "kpp_factor_blocks", "kpp_factors_destroy", "kpp_factors_bad_block", "kpp_factors_fp64_blocks", "kpp_factors_stage_ms", "kpp_factors_get_memo",
            "kpp_factors_get_block", "kpp_solve", "cdpp_solve", "kpp_solve_host", "kpp_rel_residual",
            "kpp_solve_batched", "kpp_sample_blocks", "cdpp_solve_noalloc", "kpp_set_kernel_variant", "kpp_set_wait_test", "kpp_block_gram", "kpp_server_create", "kpp_server_add_matrix",
            "kpp_server_submit", "kpp_server_poll", "kpp_server_wait_all", "kpp_server_stats", "kpp_server_reset_stats", "kpp_server_destroy",
@@ -108,6 +108,8 @@ def load(path: str | None = None):
         lib.kpp_factors_destroy.argtypes = [vp]
         lib.kpp_factors_bad_block.argtypes = [vp]
         lib.kpp_factors_bad_block.restype = i64
+        lib.kpp_factors_fp64_blocks.argtypes = [vp]
+        lib.kpp_factors_fp64_blocks.restype = i64
         lib.kpp_factors_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         lib.kpp_factors_stage_ms.restype = ctypes.c_int
         lib.kpp_factors_get_memo.argtypes = [vp, i64, i64, ctypes.POINTER(ctypes.c_float)]
@@ -311,6 +313,11 @@ class Factors:
     @property
     def bad_block(self) -> int:
         return int(self._lib.kpp_factors_bad_block(self.handle))
+
+    @property
+    def fp64_blocks(self) -> int:
+        """Blocks whose Cholesky ran in FP64 (all for FP64 storage; the ill-conditioned ones otherwise)."""
+        return int(self._lib.kpp_factors_fp64_blocks(self.handle))
 
     def stage_ms(self) -> dict:
         """Device time (ms) of the factor phase's stages: Grams (or principal blocks), Cholesky,

@@ -13,12 +13,12 @@ to FP64 and runs K++ (Eq. 1.3 - 1.4, Alg. 5) to a residual well below the GPU's.
   leave a small component in the null space of A, which no residual sees; it is bounded separately
   by the FP32 drift of the whole run, 4 * T * (2 + sqrt(n)) * 2^-24 relative (T its steps);
 * FP32 iterations in lockstep with the FP64 oracle (same Philox block sequence, T steps, no
-  refinement) on systems with well-conditioned blocks.  The FP32 Gram, inverse and residual carry a
-  relative error of about u_n = (2 + sqrt(n)) 2^-24 (a rounding per operation plus the random-walk
-  growth of an FP32 sum over n columns); the block solve turns it into a perturbation of the step of
-  at most kappa(G_j + lambda I) u_n relative; a projection does not expand the error it inherits and
-  the momentum at most doubles it; so after T steps
-      |x_32 - x_64| / |x_64| <= 4 * T * max_j kappa(G_j + lambda I) * (2 + sqrt(n)) * 2^-24.
+  refinement) on systems with well-conditioned blocks.  The FP32 Gram, Cholesky factor, inverse and
+  residual carry a relative error of about u = (2 + sqrt(n) + sqrt(s)) 2^-24 (a rounding per operation
+  plus the random-walk growth of FP32 sums over n columns and over the s terms of the factor); the
+  block solve turns it into a perturbation of the step of at most kappa(G_j + lambda I) u relative; a
+  projection does not expand the error it inherits and the momentum at most doubles it; so after T steps
+      |x_32 - x_64| / |x_64| <= 4 * T * max_j kappa(G_j + lambda I) * (2 + sqrt(n) + sqrt(s)) * 2^-24.
 Each test reports its measured error beside the bound (record_property).
 The kernel a solve runs is read from a plan of the same solve (kpp_plan_info: 2 small-block,
 4 streaming, 6 large-block with the W memo).
@@ -155,7 +155,7 @@ def test_streaming_kernel_s256_k8_two_systems_match_oracle(K, record_property):
 @pytest.mark.parametrize("form", ["large_block", "general", "streaming"])
 def test_fp32_iterations_lockstep_with_fp64_oracle(K, record_property, form):
     """T FP32 steps (no refinement) against T FP64 oracle steps on the same stored matrix and block
-    sequence, within 4 T kappa_block (2 + sqrt(n)) 2^-24 (module docstring)."""
+    sequence, within 4 T kappa_block (2 + sqrt(n) + sqrt(s)) 2^-24 (module docstring)."""
     rng_seed = {"large_block": 610, "general": 620, "streaming": 630}[form]
     if form == "streaming":
         nsys, m, n, s, k = 2, 512, 16384, 256, 3
@@ -186,7 +186,7 @@ def test_fp32_iterations_lockstep_with_fp64_oracle(K, record_property, form):
     for i in range(nsys):
         X = Xd[i].cpu().numpy().reshape(n, k)
         L = oracle.kpp_factor(As[i], s, lam)
-        bound = 4.0 * T * block_kappa(As[i], s, lam) * (2.0 + np.sqrt(n)) * EPS32
+        bound = 4.0 * T * block_kappa(As[i], s, lam) * (2.0 + np.sqrt(n) + np.sqrt(s)) * EPS32
         for c in range(k):
             res = oracle.run(As[i], Bs[i][:, c], L, s, lam=lam, tol=0.0, max_iters=T, seed=11, sys=40 + i)
             err = rel(X[:, c], res.x)
