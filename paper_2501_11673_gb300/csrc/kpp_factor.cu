@@ -469,19 +469,55 @@ __global__ void __launch_bounds__(C32_NT, 2)
 //   1. Linv block row by block row: D = (L_II)^{-1} by substitution in shared memory, then
 //      Linv_IJ = -D (sum_{K=J}^{I-1} L_IK Linv_KJ) for J < I (tile products);
 //   2. Ginv_AB = sum_{C >= max(A,B)} Linv_CA^T Linv_CB for A <= B, mirrored.
-// Blocks whose factor failed (NaN) give NaN.
+// Every tile product has the form acc[r][c] += X^T[k][r] Y[k][c] with both operands stored k-major, so a
+// thread's 4 x 4 register tile takes two 16-byte shared loads per 16 FMAs.  Left operands that are not
+// already transposed (L_IK, D) are stored transposed: each thread reads four rows of one column
+// (coalesced across the warp) and writes them as one 16-byte vector.  Blocks whose factor failed (NaN)
+// give NaN.
 constexpr int IT = 64;          // tile
-constexpr int ITP = IT + 1;     // padded leading dimension in shared memory
+constexpr int ITP = 68;         // leading dimension in shared memory (16-byte rows)
 constexpr int INV_NT = 256;
 
 template <typename TI>
-__device__ __forceinline__ void tile_load_f64(TI *dst, const double *src, int ld, int r0, int c0, int len) {
-    for (int e = threadIdx.x; e < IT * IT; e += INV_NT) {
-        const int r = e / IT, c = e % IT;
-        const int gr = r0 + r, gc = c0 + c;
-        dst[r * ITP + c] = (gr < len && gc < len) ? (TI)src[(size_t)gr * ld + gc] : (TI)0;
+struct Vec4 {
+    TI v[4];
+};
+template <typename TI>
+__device__ __forceinline__ Vec4<TI> lds4(const TI *p) {
+    Vec4<TI> r;
+    if constexpr (sizeof(TI) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        r.v[0] = q.x, r.v[1] = q.y, r.v[2] = q.z, r.v[3] = q.w;
+    } else {
+        const double2 q0 = *reinterpret_cast<const double2 *>(p), q1 = *reinterpret_cast<const double2 *>(p + 2);
+        r.v[0] = q0.x, r.v[1] = q0.y, r.v[2] = q1.x, r.v[3] = q1.y;
+    }
+    return r;
+}
+template <typename TI>
+__device__ __forceinline__ void sts4(TI *p, const Vec4<TI> &r) {
+    if constexpr (sizeof(TI) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    } else {
+        *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
+        *reinterpret_cast<double2 *>(p + 2) = make_double2(r.v[2], r.v[3]);
     }
 }
+// dst[c][r] = src[r0 + r][c0 + c] (transposed), zero outside len x len
+template <typename TI, typename TS>
+__device__ __forceinline__ void tile_load_T(TI *dst, const TS *src, int ld, int r0, int c0, int len) {
+    for (int e = threadIdx.x; e < IT * (IT / 4); e += INV_NT) {
+        const int c = e % IT, r4 = (e / IT) * 4, gc = c0 + c;
+        Vec4<TI> q;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int gr = r0 + r4 + u;
+            q.v[u] = (gr < len && gc < len) ? (TI)src[(size_t)gr * ld + gc] : (TI)0;
+        }
+        sts4(dst + c * ITP + r4, q);
+    }
+}
+// dst[r][c] = src[r0 + r][c0 + c], zero outside len x len
 template <typename TI>
 __device__ __forceinline__ void tile_load(TI *dst, const TI *src, int ld, int r0, int c0, int len) {
     for (int e = threadIdx.x; e < IT * IT; e += INV_NT) {
@@ -490,37 +526,34 @@ __device__ __forceinline__ void tile_load(TI *dst, const TI *src, int ld, int r0
         dst[r * ITP + c] = (gr < len && gc < len) ? src[(size_t)gr * ld + gc] : (TI)0;
     }
 }
-// acc += op(A) B with op(A) = A or A^T; thread (ty, tx) owns rows ty*4.., columns tx*4..
-template <typename TI, bool TRANS_A>
-__device__ __forceinline__ void tile_mma(TI (&acc)[4][4], const TI *A, const TI *B) {
+// acc[u][v] += sum_k XT[k][ty*4 + u] Y[k][tx*4 + v]
+template <typename TI>
+__device__ __forceinline__ void tile_mma(TI (&acc)[4][4], const TI *XT, const TI *Y) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll 4
+#pragma unroll 8
     for (int k = 0; k < IT; ++k) {
-        TI a[4], bv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = TRANS_A ? A[k * ITP + ty * 4 + u] : A[(ty * 4 + u) * ITP + k];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) bv[v] = B[k * ITP + tx * 4 + v];
+        const Vec4<TI> a = lds4(XT + k * ITP + ty * 4);
+        const Vec4<TI> b = lds4(Y + k * ITP + tx * 4);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * bv[v];
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a.v[u], b.v[v], acc[u][v]);
     }
 }
 
 template <typename TI>
-__global__ void __launch_bounds__(INV_NT) inverse_kernel(int64_t rows, int s, const double *__restrict__ L,
-                                                         TI *__restrict__ Linv, TI *__restrict__ Ginv, int j0) {
+__global__ void __launch_bounds__(INV_NT, 2) inverse_kernel(int64_t rows, int s, const double *__restrict__ L,
+                                                            TI *__restrict__ Linv, TI *__restrict__ Ginv, int j0) {
     const int j = j0 + (int)blockIdx.x;  // blocks j0 .. j0 + gridDim.x - 1
     const int len = (int)min64(s, rows - (int64_t)j * s);
     const double *Lj = L + (size_t)j * s * s;
     TI *Xj = Linv + (size_t)j * s * s;
     TI *Vj = Ginv + (size_t)j * s * s;
     extern __shared__ __align__(16) unsigned char inv_smem[];
-    TI *sA = (TI *)inv_smem;       // IT x ITP each
-    TI *sB = sA + IT * ITP;
-    TI *sD = sB + IT * ITP;
-    TI *sT = sD + IT * ITP;
+    TI *sA = (TI *)inv_smem;  // IT x ITP each: left operand (k-major)
+    TI *sB = sA + IT * ITP;   // right operand (k-major)
+    TI *sD = sB + IT * ITP;   // D^T: sD[k][r] = D[r][k]
+    TI *sT = sD + IT * ITP;   // sum_K L_IK Linv_KJ, row-major (the right operand of D T)
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     if (isnan(Lj[0])) {
         for (int e = threadIdx.x; e < len * len; e += INV_NT) Vj[e] = (TI)NAN;
@@ -528,45 +561,49 @@ __global__ void __launch_bounds__(INV_NT) inverse_kernel(int64_t rows, int s, co
     }
     const int nt = (len + IT - 1) / IT;
     for (int I = 0; I < nt; ++I) {
-        // D = inverse of the diagonal tile (lower triangular), by columns in shared memory
-        tile_load_f64<TI>(sA, Lj, len, I * IT, I * IT, len);
+        // D = inverse of the diagonal tile (lower triangular), by columns; thread c owns column c of D,
+        // stored as row c of sD
+        tile_load_T<TI, double>(sA, Lj, len, I * IT, I * IT, len);  // sA[k][i] = L_II[i][k]
+        for (int e = threadIdx.x; e < IT * ITP; e += INV_NT) sD[e] = (TI)0;
         __syncthreads();
         const int tl = min(IT, len - I * IT);
-        for (int e = threadIdx.x; e < IT * IT; e += INV_NT) sD[(e / IT) * ITP + e % IT] = (TI)0;
-        __syncthreads();
         if (threadIdx.x < tl) {
             const int c = threadIdx.x;
-            sD[c * ITP + c] = (TI)1 / sA[c * ITP + c];
+            TI *dc = sD + c * ITP;
+            dc[c] = (TI)1 / sA[c * ITP + c];
             for (int i = c + 1; i < tl; ++i) {
                 TI v = (TI)0;
-                for (int k = c; k < i; ++k) v += sA[i * ITP + k] * sD[k * ITP + c];
-                sD[i * ITP + c] = -v / sA[i * ITP + i];
+                for (int k = c; k < i; ++k) v = fma(sA[k * ITP + i], dc[k], v);
+                dc[i] = -v / sA[i * ITP + i];
             }
         }
         __syncthreads();
         // Linv_II = D
         for (int e = threadIdx.x; e < IT * IT; e += INV_NT) {
             const int r = e / IT, c = e % IT;
-            if (r < tl && c < tl) Xj[(size_t)(I * IT + r) * len + I * IT + c] = sD[r * ITP + c];
+            if (r < tl && c < tl) Xj[(size_t)(I * IT + r) * len + I * IT + c] = sD[c * ITP + r];
         }
         // Linv_IJ = -D sum_K L_IK Linv_KJ
         for (int J = 0; J < I; ++J) {
             TI acc[4][4] = {};
             for (int Kt = J; Kt < I; ++Kt) {
                 __syncthreads();
-                tile_load_f64<TI>(sA, Lj, len, I * IT, Kt * IT, len);
+                tile_load_T<TI, double>(sA, Lj, len, I * IT, Kt * IT, len);
                 tile_load<TI>(sB, Xj, len, Kt * IT, J * IT, len);
                 __syncthreads();
-                tile_mma<TI, false>(acc, sA, sB);
+                tile_mma<TI>(acc, sA, sB);
             }
             __syncthreads();
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                Vec4<TI> q;
 #pragma unroll
-                for (int v = 0; v < 4; ++v) sT[(ty * 4 + u) * ITP + tx * 4 + v] = acc[u][v];
+                for (int v = 0; v < 4; ++v) q.v[v] = acc[u][v];
+                sts4(sT + (ty * 4 + u) * ITP + tx * 4, q);
+            }
             __syncthreads();
             TI out[4][4] = {};
-            tile_mma<TI, false>(out, sD, sT);
+            tile_mma<TI>(out, sD, sT);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -593,7 +630,7 @@ __global__ void __launch_bounds__(INV_NT) inverse_kernel(int64_t rows, int s, co
                 tile_load<TI>(sA, Xj, len, C * IT, A * IT, len);
                 tile_load<TI>(sB, Xj, len, C * IT, B * IT, len);
                 __syncthreads();
-                tile_mma<TI, true>(acc, sA, sB);
+                tile_mma<TI>(acc, sA, sB);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
