@@ -1042,17 +1042,18 @@ class Serving(Workload):
 
     unit = "solves/s"
     metric = SERVING_METRIC
-    kernel = "cd3_kernel"
+    kernel = "serve_kernel"
 
-    def __init__(self, n_req=1024, n_mats=32, budget=120 << 30, max_concurrent=16, grid_per_solve=0):
+    def __init__(self, n_req=1024, n_mats=32, budget=120 << 30, max_concurrent=64, grid_per_solve=0):
         self.n_req, self.n_mats, self.budget = n_req, n_mats, budget
         self.max_concurrent, self.grid = max_concurrent, grid_per_solve
         self.dtype = "f32"
         self.desc = (f"{n_req} CD++ requests, Poisson arrivals (mean gap 2 ms), catalog of {n_mats} dense SPD "
                      "matrices built as the n=4096 workload (n log-uniform in [512,8192], even ids BF16, odd FP32), "
                      "k ~ U{1..32} right-hand sides ~N(0,I), s=64, lambda=1e-4, FP32 iterations + FP64 "
-                     f"refinement, tol 1e-8, HBM budget {budget >> 30} GiB, up to {max_concurrent} concurrent solves "
-                     "(CTAs per solve chosen per request, admitted launches never exceed the SM count), factors "
+                     f"refinement, tol 1e-8, HBM budget {budget >> 30} GiB, device-resident request loop (one "
+                     "persistent kernel; as many slots of 8 CTAs as fit, at most "
+                     f"{max_concurrent}; jobs of <= 8 columns, shortest expected work first), factors "
                      "memoised per matrix across requests")
 
     def setup(self, kpp, torch, rank):
@@ -1096,12 +1097,15 @@ class Serving(Workload):
             n = self.sizes[mid]
             done, rc, _, reps = self.sv.poll(rid, n, k)
             esz = 2 if self.mats[mid][1] == "bf16" else 4
-            it = reps[0].iters
-            iters += it
             worst = max(worst, max(r.rel_res_true for r in reps))
-            byts += it * (64 * n * esz + 64 * 64 * 4 + 4 * n * k * 4)
+            # the server runs a request as jobs of at most 8 columns, each its own block sequence of steps
+            for c0 in range(0, k, 8):
+                it, kc = reps[c0].iters, min(8, k - c0)
+                iters += it
+                byts += it * (64 * n * esz + 64 * 64 * 4 + 4 * n * kc * 4)
         return {"units": st["completed"], "ok": st["failed"] == 0 and st["completed"] == self.n_req,
                 "span_s": st["span_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                "loop_launches": st["loop_launches"], "loop_slots": st["loop_slots"],
                 "solves_per_s": st["solves_per_s"], "peak_bytes": st["peak_bytes"], "alg_bytes": byts,
                 "iters": iters, "rel_res": worst}
 
@@ -1118,6 +1122,8 @@ class Serving(Workload):
         last = steps[-1]
         return {"p50_ms": last["p50_ms"], "p99_ms": last["p99_ms"], "max_ms": last["max_ms"],
                 "server_solves_per_s": last["solves_per_s"], "peak_bytes": last["peak_bytes"],
+                "loop_launches": last["loop_launches"], "loop_slots": last["loop_slots"],
+                "block_iters_per_s": last["iters"] / last["span_s"] if last["span_s"] > 0 else None,
                 "block_iters": last["iters"], "requests": self.n_req,
                 "bf16_not_spd_stored_f32": [(i, self.sizes[i]) for i in self.bf16_to_f32]}
 

@@ -432,13 +432,20 @@ kpp_status kpp_set_kernel_variant(int32_t variant);
 kpp_status kpp_set_wait_test(uint64_t wait_ns, int32_t hold_cta);
 
 /* ------------------------------------------------------------------------------------------------
- * Serving: a continuous-batching request loop over registered matrices (host runtime in the library).
- * Requests arrive at any time and are admitted FIFO as soon as device memory under the budget allows:
- * a request's panels and scratch and, on a matrix's first use, its memoised block factors (Sec. 4,
- * Sec. 5.2), which then stay resident for later requests on that matrix (idle factors are evicted when
- * the budget needs the room).  Admitted requests run concurrently, each on its own CUDA stream, so work
- * that arrives while other solves run overlaps with them on the GPU.  Solves are deterministic: a
- * request's result does not depend on the other requests in flight.
+ * Serving: a continuous-batching request loop over registered matrices, resident on the device.
+ * Requests arrive at any time and are admitted FIFO as soon as device memory under the budget allows: a
+ * request's panels and scratch next to the memoised block factors (Sec. 4, Sec. 5.2) of the matrices in
+ * use, which stay resident for later requests on the same matrix (idle factors are evicted when the
+ * budget needs the room).  An admitted request becomes jobs of at most 8 right-hand-side columns.  One
+ * persistent kernel holds `max_concurrent` slots of `grid_per_solve` CTAs; each slot claims the next
+ * job from a queue in mapped host memory and runs its whole solve (the FP64 refinement loop of the
+ * mixed-precision form around FP32 inner solves, or one FP64 solve) with its own CTAs, then claims the
+ * next.  Jobs are queued shortest expected work first (iterations seen on the matrix x n x columns),
+ * at most two per slot ahead of the running ones, so work that arrives while other solves run is taken
+ * up as slots free up and overlaps with them.  The host launches no kernel per request; a library
+ * thread publishes jobs, collects completions, and relaunches the loop after it has gone idle.  Factor
+ * phases drain the loop first (they run on the whole GPU).  Solves are deterministic: a request's
+ * result does not depend on the other requests in flight.
  * ------------------------------------------------------------------------------------------------ */
 typedef struct kpp_server_s *kpp_server_t;
 
@@ -450,16 +457,21 @@ typedef struct {
     double span_s;
     size_t peak_bytes;      /* largest device memory charged to the budget */
     size_t budget_bytes;
-    int64_t reserved[4];
+    int64_t loop_launches;  /* launches of the device-resident request loop so far */
+    int64_t loop_slots;     /* slots of its last launch */
+    int64_t reserved[2];
 } kpp_serving_stats;
 
-/* Create a server with a device-memory budget (bytes), `max_concurrent` solves in flight (1..64) and
- * `grid_per_solve` CTAs per solve (0: automatic).  Uses the current CUDA device.  Errors: KPP_ERR_ARG. */
+/* Create a server with a device-memory budget (bytes), `max_concurrent` slots of the request loop (jobs
+ * in flight, 1..64; fewer when the GPU cannot hold that many at once) and `grid_per_solve` CTAs per slot
+ * (0: 8; at most 64).  Uses the current CUDA device.  Errors: KPP_ERR_ARG; KPP_ERR_CUDA when the mapped
+ * queue cannot be allocated. */
 kpp_status kpp_server_create(size_t hbm_budget_bytes, int32_t max_concurrent, int32_t grid_per_solve,
                              kpp_server_t *out);
 /* Register a device matrix (caller-owned, must outlive the server) for mode 0 (K++) or 1 (CD++; square
- * symmetric), block size s and regulariser lambda.  Factors are built on first use.  *matrix_id
- * receives its index.  Errors: KPP_ERR_ARG. */
+ * symmetric), block size s and regulariser lambda.  Factors are built on first use (with those of the
+ * other registered matrices that fit half the budget).  *matrix_id receives its index.  Errors:
+ * KPP_ERR_ARG, also when the block size and column chunk do not fit the loop's shared memory. */
 kpp_status kpp_server_add_matrix(kpp_server_t sv, const kpp_matrix *A, int32_t s, double lambda, int32_t mode,
                                  int32_t *matrix_id);
 /* Submit a request: B_host is rows x k (row-major FP64, copied before return), 1 <= k <= 32; p gives

@@ -99,6 +99,8 @@ template <typename TC> __device__ __forceinline__ TC conv(__nv_bfloat16 v) { ret
 // ---------------------------------------------------------------------------------------------
 constexpr unsigned ERR_BIAS = 0x40000000u;
 
+// Bring the 128-byte line holding p into L2 (no register result, no fault on the hint itself).
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -26,328 +26,15 @@
 #include "kpp_runtime.h"
 #include "kpp_solve.h"
 #include "kpp_solve_device.cuh"
+#include "kpp_solve_group.cuh"
 
 namespace kpp {
 
 template <typename TA, typename TC, int KP, bool CD>
 __global__ void __launch_bounds__(NT, 1) solve_kernel(const SysArgs *__restrict__ systems, Common cm) {
     const SysArgs sa = systems[blockIdx.x / cm.G];
-    const int g = blockIdx.x % cm.G;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int k = cm.k, s = cm.s, nb = cm.nb;
-    const int64_t rows = cm.rows, cols = cm.cols;
-    const TA *__restrict__ A = (const TA *)sa.A;
-    const int64_t lda = sa.lda;
-    const TC *__restrict__ b = (const TC *)sa.b;
-    TC *__restrict__ x = (TC *)sa.x;
-    TC *__restrict__ mv = (TC *)sa.m;
-    TC *__restrict__ Rx = (TC *)sa.Rx;
-    TC *__restrict__ Rm = (TC *)sa.Rm;
-    const TC *__restrict__ Ginv = (const TC *)sa.Ginv;
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TC *s_r = (TC *)smem_raw;                 // s x KP
-    TC *s_y = s_r + (size_t)s * KP;           // s x KP
-    TC *s_red = s_y + (size_t)s * KP;         // NW x 32 x KP
-    TC *s_x = s_red + (size_t)NW * 32 * KP;   // CW x KP (K++ chunk of x)
-    __shared__ ColState st[KP];
-    __shared__ double s_part[NW * KP];
-    __shared__ double s_rn2[KP];
-    __shared__ int s_stop, s_need;
-
     GroupSync gs{sa.bar, sa.err, 0u, (unsigned)cm.G, cm.timeout_ns};
-    // first and end step (read before the first group barrier: CTA 0 rewrites sc at the end)
-    const int64_t t_begin = cm.t0_state ? sa.sc[0].t : sa.t0;
-    int64_t t_end = cm.t0_state ? t_begin + cm.max_iters : cm.max_iters;
-    if (cm.t0_state) {  // a system whose columns are all done does not iterate (t stays put)
-        int any = 0;
-        for (int c = 0; c < k; ++c) any |= sa.sc[c].active;
-        if (!any) t_end = t_begin;
-    }
-
-    // my column chunk (aligned to 32-byte sectors of A)
-    const int64_t c0 = min64((int64_t)g * cm.CW, cols);
-    const int64_t c1 = min64(c0 + cm.CW, cols);
-
-    // ---- set-up: column state, |b|^2, (CD++) R_x = A x0 - b ----
-    if (threadIdx.x < KP) {
-        const int c = threadIdx.x;
-        ColState cs = {};
-        if (c < k) {
-            const SolveScalars &in = sa.sc[c];
-            cs.E0 = in.E0; cs.E1 = in.E1; cs.rhat = in.rhat; cs.rho = in.rho; cs.ci = in.ci;
-            cs.active = in.active; cs.status = in.status;
-        }
-        cs.res_true = NAN;
-        cs.res_est = NAN;
-        st[c] = cs;
-    }
-    {
-        double acc[KP];
-#pragma unroll
-        for (int c = 0; c < KP; ++c) acc[c] = 0.0;
-        for (int64_t i = (int64_t)g * NT + threadIdx.x; i < rows; i += (int64_t)cm.G * NT)
-#pragma unroll
-            for (int c = 0; c < KP; ++c)
-                if (c < k) acc[c] += (double)b[i * k + c] * (double)b[i * k + c];
-        __syncthreads();
-#pragma unroll
-        for (int c = 0; c < KP; ++c) {
-            double v = block_sum<NT>(acc[c], s_part);
-            if (threadIdx.x == 0) sa.rpart[(size_t)g * KP + c] = v;
-        }
-        if (g == cm.test_hold_cta) goto finish;  // wait test: leave without arriving
-        if (!group_barrier(gs)) goto finish;
-        if (threadIdx.x < KP) {
-            double t = 0.0;
-            for (int h = 0; h < cm.G; ++h) t += __ldcg(sa.rpart + (size_t)h * KP + threadIdx.x);
-            st[threadIdx.x].bn2 = t;
-        }
-        __syncthreads();
-        if (!group_barrier(gs)) goto finish;
-    }
-    if (CD && cm.init_residual) {
-        if (!true_residual_phase<TA, TC, KP>(sa, cm, g, gs, st, s_part, Rx)) goto finish;
-    }
-
-    {
-        const int zeta = nb;
-        int64_t t = t_begin;
-        while (t < t_end) {
-            // ---- sample the block (every CTA draws the same j) ----
-            const int j = draw_block(cm.seed, t, sa.sys_id, nb);
-            const int64_t S0 = (int64_t)j * s;
-            const int len = (int)min64(s, rows - S0);
-            const TC *__restrict__ Gj = Ginv + (size_t)j * s * s;
-
-            // ---- block residual r (s_r) ----
-            if (!CD) {
-                // partial r over my column chunk: warps over rows, lanes over columns
-                for (int e = threadIdx.x; e < (int)(c1 - c0) * KP; e += NT) {
-                    const int cc = e / KP, c = e % KP;
-                    s_x[e] = (c < k) ? __ldcg(x + (c0 + cc) * k + c) : (TC)0;
-                }
-                __syncthreads();
-                TC *part = (TC *)sa.part;  // G x s x KP
-                for (int a = warp; a < len; a += NW) {
-                    TC acc[KP];
-#pragma unroll
-                    for (int c = 0; c < KP; ++c) acc[c] = (TC)0;
-                    const TA *row = A + (S0 + a) * lda;
-#pragma unroll 4
-                    for (int64_t col = c0 + lane; col < c1; col += 32) {
-                        const TC av = conv<TC>(row[col]);
-                        const TC *xs = s_x + (col - c0) * KP;
-#pragma unroll
-                        for (int c = 0; c < KP; ++c) acc[c] = tfma<TC>(av, xs[c], acc[c]);
-                    }
-                    warp_reduce<TC, KP>(acc);
-                    if (lane == 0)
-#pragma unroll
-                        for (int c = 0; c < KP; ++c) part[((size_t)g * s + a) * KP + c] = acc[c];
-                }
-                if (!group_barrier(gs)) break;
-                if (cm.reduce_redundant) {
-                    for (int e = threadIdx.x; e < len * KP; e += NT) {
-                        const int a = e / KP, c = e % KP;
-                        TC v = (TC)0;
-                        if (c < k) {
-                            for (int h = 0; h < cm.G; ++h) v += __ldcg(part + ((size_t)h * s + a) * KP + c);
-                            v -= b[(S0 + a) * k + c];
-                        }
-                        s_r[e] = v;
-                    }
-                } else {
-                    // one warp per entry: lanes sum strided partials, then a fixed shuffle tree
-                    TC *rbuf = (TC *)sa.rbuf;
-                    for (int e = g * NW + warp; e < len * KP; e += cm.G * NW) {
-                        const int a = e / KP, c = e % KP;
-                        TC v = (TC)0;
-                        if (c < k)
-                            for (int h = lane; h < cm.G; h += 32) v += __ldcg(part + ((size_t)h * s + a) * KP + c);
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        if (lane == 0) rbuf[e] = (c < k) ? v - b[(S0 + a) * k + c] : (TC)0;
-                    }
-                    if (!group_barrier(gs)) break;
-                    for (int e = threadIdx.x; e < len * KP; e += NT) s_r[e] = __ldcg(rbuf + e);
-                }
-            } else {
-                for (int e = threadIdx.x; e < len * KP; e += NT) {
-                    const int a = e / KP, c = e % KP;
-                    s_r[e] = (c < k) ? __ldcg(Rx + (S0 + a) * k + c) : (TC)0;
-                }
-            }
-            __syncthreads();
-            // |r|^2 per column: warp c % NW, lanes over rows, fixed tree
-            for (int c = warp; c < k; c += NW) {
-                double v = 0.0;
-                for (int a = lane; a < len; a += 32) {
-                    const double r = (double)s_r[a * KP + c];
-                    v += r * r;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) s_rn2[c] = v;
-            }
-            // ---- projection y = G_j^{-1} r: rows spread over all CTAs (warp per row) ----
-            {
-                TC *ybuf = (TC *)sa.ybuf;
-                for (int a = g + cm.G * warp; a < len; a += cm.G * NW) {
-                    TC acc[KP];
-#pragma unroll
-                    for (int c = 0; c < KP; ++c) acc[c] = (TC)0;
-                    const TC *grow = Gj + (size_t)a * len;
-                    for (int d = lane; d < len; d += 32) {
-                        const TC gv = grow[d];
-#pragma unroll
-                        for (int c = 0; c < KP; ++c) acc[c] = tfma<TC>(gv, s_r[d * KP + c], acc[c]);
-                    }
-                    warp_reduce<TC, KP>(acc);
-                    if (lane == 0)
-#pragma unroll
-                        for (int c = 0; c < KP; ++c) ybuf[(size_t)a * KP + c] = acc[c];
-                }
-                if (!group_barrier(gs)) break;
-                for (int e = threadIdx.x; e < len * KP; e += NT) s_y[e] = __ldcg(ybuf + e);
-            }
-            __syncthreads();
-
-            // ---- back-projection and update on my column chunk ----
-            __shared__ TC s_beta[KP], s_keep[KP];  // read with a runtime rhs index below
-            if (threadIdx.x < KP) {
-                const double rho = st[threadIdx.x].rho;
-                s_beta[threadIdx.x] = (TC)((1.0 - rho) / (1.0 + rho));
-                s_keep[threadIdx.x] = (TC)((threadIdx.x < k && st[threadIdx.x].active) ? 1 : 0);
-            }
-            __syncthreads();
-            const TC eta = (TC)cm.eta;
-            for (int64_t cb = c0; cb < c1; cb += 32) {
-                const int64_t col = cb + lane;
-                const bool valid = col < c1;
-                TC acc[KP];
-#pragma unroll
-                for (int c = 0; c < KP; ++c) acc[c] = (TC)0;
-                if (valid) {
-#pragma unroll 4
-                    for (int a = warp; a < len; a += NW) {
-                        const TC av = conv<TC>(A[(S0 + a) * lda + col]);
-#pragma unroll
-                        for (int c = 0; c < KP; ++c) acc[c] = tfma<TC>(av, s_y[a * KP + c], acc[c]);
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < KP; ++c) s_red[(warp * 32 + lane) * KP + c] = acc[c];
-                __syncthreads();
-                // combine the warps' partial sums; threads take (column, rhs) pairs
-                for (int e = threadIdx.x; e < 32 * KP; e += NT) {
-                    const int ln = e / KP, c = e % KP;
-                    const int64_t cl = cb + ln;
-                    if (cl < c1 && c < k && s_keep[c] != (TC)0) {
-                        TC u = (TC)0;
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) u += s_red[(w * 32 + ln) * KP + c];
-                        const size_t idx = (size_t)cl * k + c;
-                        if (!CD) {
-                            const TC mm = s_beta[c] * (__ldcg(mv + idx) - u);
-                            mv[idx] = mm;
-                            x[idx] = __ldcg(x + idx) - u + eta * mm;
-                        } else {
-                            const TC rm = s_beta[c] * (__ldcg(Rm + idx) - u);
-                            Rm[idx] = rm;
-                            Rx[idx] = __ldcg(Rx + idx) - u + eta * rm;
-                            const TC wv = (cl >= S0 && cl < S0 + len) ? s_y[(cl - S0) * KP + c] : (TC)0;
-                            const TC mm = s_beta[c] * (__ldcg(mv + idx) - wv);
-                            mv[idx] = mm;
-                            x[idx] = __ldcg(x + idx) - wv + eta * mm;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            if (CD) {
-                if (!group_barrier(gs)) break;
-            }
-
-            // ---- residual estimate, checkpoint, adaptive rho (identical in every CTA) ----
-            const int64_t ph = t % (2 * (int64_t)zeta);
-            if (threadIdx.x == 0) {
-                s_need = 0;
-                s_stop = 0;
-            }
-            __syncthreads();
-            if (threadIdx.x < k) {
-                ColState &cs = st[threadIdx.x];
-                if (cs.active) {
-                    if (ph < zeta) cs.E0 += s_rn2[threadIdx.x];
-                    else cs.E1 += s_rn2[threadIdx.x];
-                    if (ph == 2 * zeta - 1) {
-                        cs.res_est = cs.bn2 > 0.0 ? sqrt(cs.E1 / cs.bn2) : sqrt(cs.E1);
-                        if (cm.tol > 0.0 && cs.E1 <= cm.tol * cm.tol * cs.bn2 && cm.confirm) atomicOr(&s_need, 1);
-                    }
-                }
-            }
-            __syncthreads();
-            t += 1;
-            if (ph == 2 * zeta - 1) {
-                if (s_need) {
-                    // x must be complete in every chunk before the true residual (K++ has no barrier yet)
-                    if (!CD && !group_barrier(gs)) break;
-                    if (!true_residual_phase<TA, TC, KP>(sa, cm, g, gs, st, s_part, CD ? Rx : (TC *)nullptr)) break;
-                }
-                if (threadIdx.x < k) {
-                    ColState &cs = st[threadIdx.x];
-                    if (cs.active) {
-                        cs.ci += 1;
-                        bool stop = false;
-                        if (cm.tol > 0.0 && cs.E1 <= cm.tol * cm.tol * cs.bn2) stop = cm.confirm ? (cs.res_true <= cm.tol) : true;
-                        if (!isfinite(cs.E1) || !isfinite(cs.E0)) {
-                            cs.status = KPP_ERR_NUMERIC;
-                            cs.active = 0;
-                        } else if (stop) {
-                            cs.status = KPP_OK;
-                            cs.active = 0;
-                        } else {
-                            if (cm.adaptive) {
-                                const double q = cs.E0 > 0.0 ? cs.E1 / cs.E0 : 0.0;
-                                if (cs.ci == 1) {
-                                    cs.rhat = q;
-                                } else {
-                                    const double li = log((double)cs.ci), li1 = log((double)cs.ci + 1.0);
-                                    const double wgt = exp(li * li - li1 * li1);
-                                    cs.rhat = wgt * cs.rhat + (1.0 - wgt) * q;
-                                }
-                                double rho = 1.0 - pow(cs.rhat, 1.0 / (double)zeta);
-                                if (!(rho > 0.0)) rho = 0.0;
-                                if (rho > 1.0 - 1e-12) rho = 1.0 - 1e-12;
-                                cs.rho = rho;
-                            }
-                        }
-                        cs.E0 = 0.0;
-                        cs.E1 = 0.0;
-                    }
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int any = 0;
-                    for (int c = 0; c < k; ++c) any |= st[c].active;
-                    s_stop = !any;
-                }
-                __syncthreads();
-                if (s_stop) break;
-            }
-        }
-        // ---- write back (CTA 0 of the group) ----
-        if (g == 0 && threadIdx.x < k) {
-            const ColState &cs = st[threadIdx.x];
-            SolveScalars &out = sa.sc[threadIdx.x];
-            out.E0 = cs.E0; out.E1 = cs.E1; out.rhat = cs.rhat; out.rho = cs.rho; out.ci = cs.ci;
-            out.active = cs.active; out.status = cs.status; out.res_est = cs.res_est; out.bn2 = cs.bn2;
-            out.t = t;
-        }
-    }
-finish:
-    return;
+    solve_group<TA, TC, KP, CD>(sa, cm, (int)(blockIdx.x % cm.G), gs);
 }
 
 // ---------------------------------------------------------------------------------------------

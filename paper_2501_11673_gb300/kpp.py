@@ -64,7 +64,7 @@ class ServingStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("solves_per_s", ctypes.c_double),
                 ("span_s", ctypes.c_double), ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("loop_launches", ctypes.c_int64), ("loop_slots", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -695,7 +695,8 @@ def rht_inverse(d, xbar, stream=None):
 
 class Server:
     """Continuous-batching solve server (kpp_server_*): admission by a device-memory budget, memoised
-    factors kept resident per registered matrix, concurrent solves on separate streams."""
+    factors kept resident per registered matrix, and a device-resident request loop whose slots
+    (max_concurrent of them, grid_per_solve CTAs each) claim and run the queued jobs."""
 
     def __init__(self, hbm_budget_bytes: int, max_concurrent: int = 8, grid_per_solve: int = 0):
         self._lib = load()

@@ -1,8 +1,9 @@
-"""Serving runtime (kpp_server_*): continuous batching under a memory budget.
+"""Serving runtime (kpp_server_*): continuous batching under a memory budget, run by the device-resident
+request loop (a persistent kernel whose slots claim queued jobs).
 
 Each result must be bitwise the same whether the request ran alone or in a mix of concurrent requests
-(the solves are deterministic: fixed reduction orders, no floating-point atomics), every column must
-reach its tolerance, and the peak device memory charged to admitted work must stay within the budget.
+(a job runs on one slot's CTAs with fixed reduction orders and no floating-point atomics), every column
+must reach its tolerance, and the peak device memory charged to admitted work must stay within the budget.
 """
 import numpy as np
 import pytest
@@ -101,10 +102,43 @@ def test_budget_admission_and_refusal(K):
     small = 24 << 20
     res, st = _run(K, mats[:1], [(0, 1, 1), (0, 3, 2), (0, 1, 3)], max_concurrent=3, budget=small)
     assert st["completed"] == 3 and st["failed"] == 0 and st["peak_bytes"] <= small
-    # a budget no request fits: refused at submission
-    sv = K.Server(1 << 20, max_concurrent=1)
+    # a budget no request fits (the matrix's factors alone take about 0.7 MB): refused at submission
+    sv = K.Server(1 << 18, max_concurrent=1)
     mid = sv.add_matrix(mats[0][2], 32, 1e-4, 1)
     rid = sv.submit(mid, np.ones(256), K.params(tol=1e-8))
     done, rc, _, _ = sv.poll(rid, 256, 1)
     assert done and rc == K.ERR_BUDGET
+    sv.close()
+
+
+def test_loop_goes_idle_and_relaunches_and_splits_wide_requests(K):
+    """A request of 20 columns runs as jobs of 8, 8 and 4 columns; after the loop has gone idle (its
+    slots leave after 50 ms without work), a second batch relaunches it; every column meets 1e-8 in the
+    FP64 residual of the stored matrix."""
+    import time
+    mats = _catalog()
+    sv = K.Server(8 << 30, max_concurrent=4, grid_per_solve=8)
+    ids = [sv.add_matrix(A, 32, 1e-4, 1) for (_, _, A, _) in mats]
+    def batch(seeds):
+        rids = []
+        for mid, k, seed in seeds:
+            n = mats[mid][0]
+            B = np.random.default_rng(seed).standard_normal((n, k))
+            prm = K.params(tol=1e-8, refine=1 if mats[mid][1] != "f64" else 0, inner_tol=1e-3, seed=seed,
+                           sys_id=seed)
+            rids.append((sv.submit(ids[mid], B, prm), mid, k, B))
+        sv.wait_all(300.0)
+        for rid, mid, k, B in rids:
+            done, rc, X, reps = sv.poll(rid, mats[mid][0], k)
+            assert done and rc == K.OK, (rid, rc)
+            Ar = mats[mid][3]
+            for c in range(k):
+                assert reps[c].status == K.OK
+                assert np.linalg.norm(Ar @ X[:, c] - B[:, c]) <= 1e-8 * np.linalg.norm(B[:, c]) * 1.0001
+    batch([(2, 20, 11), (1, 1, 12)])
+    first = sv.stats()["loop_launches"]
+    time.sleep(0.5)
+    batch([(0, 2, 13), (2, 9, 14)])
+    st = sv.stats()
+    assert first >= 1 and st["loop_launches"] > first and st["loop_slots"] >= 1
     sv.close()

@@ -219,7 +219,7 @@ def test_binding_structs_match_the_c_header_layout(tmp_path):
                                            "bad_block", "device_ms", "kernel_ms", "launches", "reserved"]),
                "kpp_serving_stats": (kpp.ServingStats, ["completed", "failed", "p50_ms", "p99_ms", "max_ms",
                                                         "solves_per_s", "span_s", "peak_bytes", "budget_bytes",
-                                                        "reserved"])}
+                                                        "loop_launches", "loop_slots", "reserved"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kpp.h"', "int main(void) {"]
     for cname, (_, fields) in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
