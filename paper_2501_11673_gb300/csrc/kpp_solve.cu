@@ -1,22 +1,7 @@
-// kpp_solve.cu -- the block-step iteration of Kaczmarz++ and CD++ as one persistent kernel.
-//
-// Paper: arXiv 2501.11673.  One launch runs every iteration of one or more systems:
-//   K++  (Alg. 1; Alg. 5, exact projection through the memoised factor):
-//        r = A_S x - b_S;  y = (A_S A_S^T + lam I)^{-1} r;  w = A_S^T y;
-//        m <- beta (m - w);  x <- x - w + eta m;   beta = (1 - rho)/(1 + rho)          (Eq. 1.3, 1.4)
-//   CD++ (Eq. 5.1; Alg. 3) with the residual kept up to date:
-//        r = R_x[S];  y = (A_SS + lam I)^{-1} r;  u = A_{:,S} y  (= A_S^T y, A symmetric);
-//        R_m <- beta (R_m - u);  R_x <- R_x - u + eta R_m;  m <- beta (m - I_S^T y);  x <- x - I_S^T y + eta m
-//   then, every step, E0 / E1 += |r|^2 and every 2 zeta steps the checkpoint of Alg. 3:
-//   stop test on E1 (confirmed by the true residual), weighted ratio (Eq. 5.3), rho = 1 - rhat^(1/zeta).
-//
-// Work split inside a system (G CTAs, one group barrier counter):
-//   * column chunks: CTA g owns columns [c0, c1) of x, m (and R_x, R_m) and streams the block rows
-//     A_S[:, c0:c1] -- warps take rows, lanes take columns (coalesced row segments);
-//   * the s x s projection y = G^{-1} r is split by rows across all CTAs (warp per row);
-//   * the K++ residual is reduced from per-CTA partial sums in a fixed order (deterministic).
-// Every CTA recomputes the scalars (|r|^2, E0, E1, rho) from identical data in an identical order,
-// so all CTAs agree on rho and on the stop decision without another exchange.
+// kpp_solve.cu -- the general persistent solve kernel of Kaczmarz++ and CD++ (Alg. 1, Alg. 3, Alg. 5;
+// Eq. 1.3 - 1.4, Eq. 5.1 - 5.3), the standalone FP64 residual and the small elementwise kernels of the
+// refinement loop.  One launch runs every iteration of one or more systems, G CTAs per system; the body
+// of a system's solve is solve_group (kpp_solve_group.cuh), which the serving loop's slots run as well.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
