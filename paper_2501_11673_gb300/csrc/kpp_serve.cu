@@ -167,7 +167,7 @@ __device__ void serve_mixed(const ServeJob &J, ServeDone *D, int g, GroupSync &g
             ok = false;
             break;
         }
-        solve_group<TA, float, KP, CD>(J.sa, J.cm, g, gs);
+        solve_group<TA, float, KP, CD, false>(J.sa, J.cm, g, gs);
         if (!group_barrier(gs)) {
             ok = false;
             break;
@@ -220,7 +220,7 @@ __device__ void serve_fp64(const ServeJob &J, ServeDone *D, int g, GroupSync &gs
     constexpr int KP = SERVE_KP;
     __shared__ double s_part[NW * 2 * KP];
     __shared__ double s_rn2[KP], s_bn2[KP];
-    solve_group<TA, double, KP, CD>(J.sa, J.cm, g, gs);
+    solve_group<TA, double, KP, CD, false>(J.sa, J.cm, g, gs);
     bool ok = group_barrier(gs);
     // the reported residual: |B - A X| / |B| in FP64 over the slot
     if (ok) ok = serve_residual<TA, CD, false>(J, g, gs, s_part, s_rn2, s_bn2, true);

@@ -260,7 +260,7 @@ bool prepare_chunk(kpp_server_s *sv, Request &r, Matrix &m, Chunk &ch) {
     const bool refine = !f64 && r.p.refine;
     cm.tol = f64 ? r.p.tol : (refine ? r.p.inner_tol : r.p.tol);
     cm.adaptive = r.p.adaptive_rho;
-    cm.confirm = 1;
+    cm.confirm = f64 ? 1 : 0;  // inner solves stop on the window estimate; the FP64 outer residual decides
     cm.reduce_redundant = ((int64_t)G * m.s * KP <= 8192) ? 1 : 0;
     cm.init_residual = (f64 && m.mode == 1) ? 1 : 0;
     cm.max_iters = r.p.max_iters;

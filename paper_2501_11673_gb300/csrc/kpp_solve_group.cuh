@@ -30,7 +30,10 @@ namespace kpp {
 
 // g: this CTA's rank in the group; gs: the group's barrier (its target carried by the caller).
 // Returns when the system's iteration ends (every column stopped, the step cap, or a group error).
-template <typename TA, typename TC, int KP, bool CD>
+// CRMW: the back-projection's read-modify-write goes through shared memory so that it is coalesced (the
+// batched kernel); without it each lane updates the k entries of its own column directly, which needs
+// fewer registers (the serving loop, which holds six instantiations of this body in one kernel).
+template <typename TA, typename TC, int KP, bool CD, bool CRMW = true>
 __device__ void solve_group(const SysArgs &sa, const Common &cm, int g, GroupSync &gs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = cm.k, s = cm.s, nb = cm.nb;
@@ -221,12 +224,13 @@ __device__ void solve_group(const SysArgs &sa, const Common &cm, int g, GroupSyn
             __syncthreads();
             const TC eta = (TC)cm.eta;
             // a warp takes whole 32-column groups of my chunk: each lane sums the len rows of A_S for its
-            // column in row order (16 row loads in flight at a time), then updates its own entries, so
-            // the phase needs no cross-warp reduction and no barrier
+            // column in row order (16 or 32 row loads in flight at a time); the sums then go through the
+            // warp's slice of shared memory to the updates, so the phase needs no cross-warp reduction
+            // and no block barrier
             for (int64_t cb = c0 + (int64_t)warp * 32; cb < c1; cb += (int64_t)NW * 32) {
-                const int64_t col = cb + lane;
-                if (col >= c1) continue;
-                TC acc[KP];
+                if (!CRMW && cb + lane >= c1) continue;
+                const int64_t col = cb + lane < c1 ? cb + lane : c1 - 1;  // lanes past the chunk repeat
+                TC acc[KP];                                                 // its last column (unused)
 #pragma unroll
                 for (int c = 0; c < KP; ++c) acc[c] = (TC)0;
                 const TA *ap = A + S0 * lda + col;
@@ -246,23 +250,54 @@ __device__ void solve_group(const SysArgs &sa, const Common &cm, int g, GroupSyn
 #pragma unroll
                     for (int c = 0; c < KP; ++c) acc[c] = tfma<TC>(av, s_y[a * KP + c], acc[c]);
                 }
+                if (CRMW) {
+                    // the lanes then take consecutive (column, right-hand side) entries, so that every
+                    // read-modify-write below is coalesced
+                    TC *red = s_red + (size_t)warp * 32 * KP;
 #pragma unroll
-                for (int c = 0; c < KP; ++c) {
-                    if (c < k && s_keep[c] != (TC)0) {
-                        const TC u = acc[c];
-                        const size_t idx = (size_t)col * k + c;
-                        if (!CD) {
-                            const TC mm = s_beta[c] * (__ldcg(mv + idx) - u);
-                            mv[idx] = mm;
-                            x[idx] = __ldcg(x + idx) - u + eta * mm;
-                        } else {
-                            const TC rm = s_beta[c] * (__ldcg(Rm + idx) - u);
-                            Rm[idx] = rm;
-                            Rx[idx] = __ldcg(Rx + idx) - u + eta * rm;
-                            const TC wv = (col >= S0 && col < S0 + len) ? s_y[(col - S0) * KP + c] : (TC)0;
-                            const TC mm = s_beta[c] * (__ldcg(mv + idx) - wv);
-                            mv[idx] = mm;
-                            x[idx] = __ldcg(x + idx) - wv + eta * mm;
+                    for (int c = 0; c < KP; ++c) red[lane * KP + c] = acc[c];
+                    __syncwarp();
+                    for (int e = lane; e < 32 * k; e += 32) {
+                        const int ln = e / k, c = e % k;
+                        const int64_t cl = cb + ln;
+                        if (cl < c1 && s_keep[c] != (TC)0) {
+                            const TC u = red[ln * KP + c];
+                            const size_t idx = (size_t)cl * k + c;
+                            if (!CD) {
+                                const TC mm = s_beta[c] * (__ldcg(mv + idx) - u);
+                                mv[idx] = mm;
+                                x[idx] = __ldcg(x + idx) - u + eta * mm;
+                            } else {
+                                const TC rm = s_beta[c] * (__ldcg(Rm + idx) - u);
+                                Rm[idx] = rm;
+                                Rx[idx] = __ldcg(Rx + idx) - u + eta * rm;
+                                const TC wv = (cl >= S0 && cl < S0 + len) ? s_y[(cl - S0) * KP + c] : (TC)0;
+                                const TC mm = s_beta[c] * (__ldcg(mv + idx) - wv);
+                                mv[idx] = mm;
+                                x[idx] = __ldcg(x + idx) - wv + eta * mm;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                } else if (cb + lane < c1) {
+#pragma unroll
+                    for (int c = 0; c < KP; ++c) {
+                        if (c < k && s_keep[c] != (TC)0) {
+                            const TC u = acc[c];
+                            const size_t idx = (size_t)col * k + c;
+                            if (!CD) {
+                                const TC mm = s_beta[c] * (__ldcg(mv + idx) - u);
+                                mv[idx] = mm;
+                                x[idx] = __ldcg(x + idx) - u + eta * mm;
+                            } else {
+                                const TC rm = s_beta[c] * (__ldcg(Rm + idx) - u);
+                                Rm[idx] = rm;
+                                Rx[idx] = __ldcg(Rx + idx) - u + eta * rm;
+                                const TC wv = (col >= S0 && col < S0 + len) ? s_y[(col - S0) * KP + c] : (TC)0;
+                                const TC mm = s_beta[c] * (__ldcg(mv + idx) - wv);
+                                mv[idx] = mm;
+                                x[idx] = __ldcg(x + idx) - wv + eta * mm;
+                            }
                         }
                     }
                 }
