@@ -185,6 +185,7 @@ def test_solver_entry_points_refuse_bad_arguments_on_the_host(lib):
     assert lib.kpp_server_create(0, 4, 0, ctypes.byref(out)) == kpp.ERR_ARG                    # no budget
     assert lib.kpp_server_create(1 << 30, 0, 0, ctypes.byref(out)) == kpp.ERR_ARG              # no slots
     assert lib.kpp_server_create(1 << 30, 65, 0, ctypes.byref(out)) == kpp.ERR_ARG
+    assert lib.kpp_server_create(1 << 30, 4, 65, ctypes.byref(out)) == kpp.ERR_ARG             # slot width
     assert lib.kpp_sample_blocks(1, 0, 0, 10, 0, dev, None) == kpp.ERR_ARG                     # nb < 1
     assert lib.kpp_sample_blocks(1, 0, 0, -1, 4, dev, None) == kpp.ERR_ARG
     assert lib.kpp_sample_blocks(1, 0, 0, 10, 4, None, None) == kpp.ERR_ARG
