@@ -489,7 +489,8 @@ kpp_status kpp_server_stats(kpp_server_t sv, kpp_serving_stats *out);
 /* Start a new statistics window: latencies, completed / failed counts, the first-submission time and
  * the peak are reset (requests already submitted stay pollable).  Errors: KPP_ERR_ARG (null server). */
 kpp_status kpp_server_reset_stats(kpp_server_t sv);
-/* Stop the workers (after the running requests finish) and free the factors. */
+/* Stop the server: requests already submitted finish first, then the request loop is drained, its
+ * thread joined, and the factors, the mapped queue and the device buffers freed. */
 void kpp_server_destroy(kpp_server_t sv);
 
 /* Batched CD++ (Eq. 5.1, Alg. 3): as kpp_solve_batched, for square symmetric systems whose factors
