@@ -471,7 +471,8 @@ kpp_status kpp_server_create(size_t hbm_budget_bytes, int32_t max_concurrent, in
 /* Register a device matrix (caller-owned, must outlive the server) for mode 0 (K++) or 1 (CD++; square
  * symmetric), block size s and regulariser lambda.  Factors are built on first use (with those of the
  * other registered matrices that fit half the budget).  *matrix_id receives its index.  Errors:
- * KPP_ERR_ARG, also when the block size and column chunk do not fit the loop's shared memory. */
+ * KPP_ERR_ARG, also when the block size and column chunk do not fit the loop's shared memory, or when
+ * the server already holds 4096 matrices. */
 kpp_status kpp_server_add_matrix(kpp_server_t sv, const kpp_matrix *A, int32_t s, double lambda, int32_t mode,
                                  int32_t *matrix_id);
 /* Submit a request: B_host is rows x k (row-major FP64, copied before return), 1 <= k <= 32; p gives

@@ -84,6 +84,8 @@ struct Request {
     kpp_status status = KPP_OK;
 };
 
+constexpr size_t kMaxMatrices = 4096;  // registered matrices per server
+
 size_t dsize(int dt) { return kpp::dtype_size(dt); }
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -641,6 +643,8 @@ kpp_status kpp_server_create(size_t hbm_budget_bytes, int32_t max_concurrent, in
         delete sv;
         return KPP_ERR_CUDA;
     }
+    // the dispatcher thread reads registered entries without the lock: the table never reallocates
+    sv->mats.reserve(kMaxMatrices);
     memset(sv->ctl_h, 0, sizeof(ServeCtl));
     memset(sv->done_h, 0, sizeof(ServeDone) * sv->R);
     sv->ring.assign(sv->R, {});
@@ -672,6 +676,11 @@ kpp_status kpp_server_add_matrix(kpp_server_t sv, const kpp_matrix *A, int32_t s
     kpp_status rc = kpp_partition(A->rows, s, &m->P);
     if (rc != KPP_OK) return rc;
     std::lock_guard<std::mutex> g(sv->mu);
+    if (sv->mats.size() >= kMaxMatrices) {
+        kpp_partition_destroy(m->P);
+        set_error("kpp_server_add_matrix: at most %d matrices per server", (int)kMaxMatrices);
+        return KPP_ERR_ARG;
+    }
     *matrix_id = (int32_t)sv->mats.size();
     sv->mats.push_back(std::move(m));
     return KPP_OK;
@@ -684,6 +693,7 @@ kpp_status kpp_server_submit(kpp_server_t sv, int32_t matrix_id, const double *B
         set_error("kpp_server_submit: invalid argument");
         return KPP_ERR_ARG;
     }
+    const clk::time_point t_call = clk::now();  // latency counts any wait for the server's lock
     std::lock_guard<std::mutex> g(sv->mu);
     if (matrix_id < 0 || matrix_id >= (int32_t)sv->mats.size()) {
         set_error("kpp_server_submit: unknown matrix %d", matrix_id);
@@ -698,7 +708,7 @@ kpp_status kpp_server_submit(kpp_server_t sv, int32_t matrix_id, const double *B
     r->B.assign(B_host, B_host + (size_t)m.A.rows * k);
     r->bytes = 0;
     for (int c0 = 0; c0 < k; c0 += SERVE_KP) r->bytes += chunk_bytes(m, std::min(SERVE_KP, k - c0), sv->G);
-    r->t_submit = clk::now();
+    r->t_submit = t_call;
     if (!sv->have_first) {
         sv->t_first = r->t_submit;
         sv->have_first = true;
